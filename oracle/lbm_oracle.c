@@ -1,0 +1,437 @@
+/*
+ * Oracle: plain, slow, FP64 CPU statement of one time step of the coupled
+ * double-distribution-function (DDF) thermal lattice Boltzmann method on D2Q9
+ * (Li, Luo, He, Gao & Tao, arXiv:1109.6672), BGK scheme of Sec. III.C.1.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; only the tests, the smoke check and the benchmark's CPU
+ * baseline do.  It shares no code, header, table or constant with the CUDA
+ * library: every constant below is written out here from the paper.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared [-fopenmp] (no FMA
+ * contraction, so every product and sum is rounded as written).
+ *
+ * State: the canonical pre-collision distributions fbar_a(x,t), hbar_a(x,t)
+ * (Eqs. 33-36 variable change), stored as f[a][y*nx+x], h[a][y*nx+x].
+ *
+ * One step, in the order the paper defines it:
+ *   phase 1, every node: rho, u (Eq. 35 with the force shift under Eq. 51),
+ *            T from Eq. 37 (total energy) or from the internal-energy form
+ *            under Eq. 38, theta = T/T0, Q = rho u (1 - theta) (Eq. 48);
+ *   phase 2, every node: dQx/dx, dQy/dy by Eq. 50, phi (Eq. 48), C_a
+ *            (Eq. 49), Guo force F_a (text above Eq. 51) added to C_a,
+ *            equilibria (Eq. 18a/18b), collision (Eq. 34 with the sign of the
+ *            C term read as +, Eq. 36 or Eq. 38), then push-streaming to
+ *            x + e_a with periodic wrap or the wall rules below.
+ *
+ * Readings where the paper is silent (the wall rules are not in the paper,
+ * which uses non-equilibrium extrapolation):
+ *   - halfway bounce-back for f with the odd part of Eq. 18a at the wall
+ *     state (moving wall);
+ *   - f wall state: rho and theta of the boundary node itself and the wall
+ *     velocity (the linear Couette profile is then reproduced exactly);
+ *   - h on isothermal walls: non-equilibrium extrapolation (the paper's wall
+ *     method, ref. [45]) from a ghost node one spacing outside the node, with
+ *     u_g = 2 u_w - u, theta_g = 2 theta_w - theta (linear through the wall
+ *     value at the halfway point) and rho_g = rho theta / theta_g (equal
+ *     pressure across the wall): h_in = h^eq(ghost) + (h* - h^eq)(node);
+ *   - h on adiabatic walls: bounce-back plus twice the odd part of h^eq at
+ *     (rho, u_w, theta) of the node (zero total-energy flux through a wall at
+ *     rest);
+ *   - a population leaving through a corner across two walls takes the
+ *     x-side wall's rule;
+ *   - Eq. 50 across a wall uses the mirror ghost Q_g = 2 Q_w - Q(node),
+ *     Q_w = rho(node) u_w (1 - theta_w).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* D2Q9 velocities and weights, Eq. 6 with c = 1 and the weights under Eq. 8. */
+static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+static const double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                            1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+static const double DIM = 2.0; /* D */
+
+enum { ORC_PERIODIC = 0, ORC_WALL_ISOTHERMAL = 1, ORC_WALL_ADIABATIC = 2 };
+enum { ORC_E_TOTAL = 0, ORC_E_INTERNAL = 1 };
+
+typedef struct {
+  int32_t nx, ny;
+  int32_t bc[4]; /* sides x-, x+, y-, y+ */
+  double tau_f, tau_h;
+  double R, T0, b;
+  double u_wall[4][2];
+  double T_wall[4];
+  double g; /* gravity; force density a = (0, -rho g) */
+  int32_t energy_model;
+  int32_t correction;
+  int32_t z_full;
+} orc_params;
+
+typedef struct {
+  orc_params p;
+  long n;
+  double *f[9], *h[9];   /* current state, pre-collision */
+  double *fn[9], *hn[9]; /* next state */
+  double *rho, *ux, *uy, *theta, *Qx, *Qy;
+} orc_state;
+
+/* ---- pointwise pieces (exported so the tests can pin them one by one) ---- */
+
+/* Eq. 18a: f^eq with the theta terms, third-order velocity term dropped. */
+void orc_feq(double RT0, double rho, double ux, double uy, double theta, double out[9]) {
+  double usq = ux * ux + uy * uy;
+  for (int a = 0; a < 9; ++a) {
+    double eu = EX[a] * ux + EY[a] * uy;
+    double esq = (double)(EX[a] * EX[a] + EY[a] * EY[a]);
+    double second = (eu / RT0) * (eu / RT0) - usq / RT0 + (theta - 1.0) * (esq / RT0 - DIM);
+    double third = eu / (2.0 * RT0) * (theta - 1.0) * (esq / RT0 - DIM - 2.0);
+    out[a] = rho * W[a] * (1.0 + eu / RT0 + 0.5 * second + third);
+  }
+}
+
+/* Eq. 18b: h^eq = E f^eq + w p [...], p = rho R T = rho RT0 theta. */
+void orc_heq(double RT0, double rho, double ux, double uy, double theta, double E,
+             const double feq[9], double out[9]) {
+  double usq = ux * ux + uy * uy;
+  double p = rho * RT0 * theta;
+  for (int a = 0; a < 9; ++a) {
+    double eu = EX[a] * ux + EY[a] * uy;
+    double esq = (double)(EX[a] * EX[a] + EY[a] * EY[a]);
+    double br = eu / RT0 + (eu / RT0) * (eu / RT0) - usq / RT0 + 0.5 * theta * (esq / RT0 - DIM);
+    out[a] = E * feq[a] + W[a] * p * br;
+  }
+}
+
+/* Text under Eq. 38: internal-energy equilibrium h^eq = b R T f^eq / 2. */
+void orc_heq_internal(double RT0, double b, double theta, const double feq[9], double out[9]) {
+  double bRT = b * RT0 * theta;
+  for (int a = 0; a < 9; ++a) out[a] = 0.5 * bRT * feq[a];
+}
+
+/* Eq. 48 and Eq. 49: C_a from the two divergence pieces of Q. */
+void orc_correction(double dQx_dx, double dQy_dy, double out[9]) {
+  double phx = 3.0 * (dQx_dx + dQy_dy);
+  double phy = dQx_dx - dQy_dy;
+  out[0] = -phx / 9.0;
+  out[1] = -phx / 36.0 + phy / 4.0;
+  out[2] = -phx / 36.0 - phy / 4.0;
+  out[3] = out[1];
+  out[4] = out[2];
+  out[5] = phx / 18.0;
+  out[6] = phx / 18.0;
+  out[7] = phx / 18.0;
+  out[8] = phx / 18.0;
+}
+
+/* Guo forcing term (the text above Eq. 51):
+ * F_a = w_a [ (e.a)/RT0 + u a : (e e - RT0 I) / RT0^2 ]. */
+void orc_force(double RT0, double ux, double uy, double ax, double ay, double out[9]) {
+  for (int a = 0; a < 9; ++a) {
+    double ea = EX[a] * ax + EY[a] * ay;
+    double ua_ee = (EX[a] * ux + EY[a] * uy) * ea; /* (u.e)(e.a) */
+    double ua = ux * ax + uy * ay;
+    out[a] = W[a] * (ea / RT0 + (ua_ee - RT0 * ua) / (RT0 * RT0));
+  }
+}
+
+/* ---- state ---- */
+
+static long nodes(const orc_params* p) { return (long)p->nx * (long)p->ny; }
+
+orc_state* orc_new(const orc_params* p) {
+  orc_state* s = (orc_state*)calloc(1, sizeof(orc_state));
+  if (!s) return NULL;
+  s->p = *p;
+  s->n = nodes(p);
+  for (int a = 0; a < 9; ++a) {
+    s->f[a] = (double*)calloc(s->n, sizeof(double));
+    s->h[a] = (double*)calloc(s->n, sizeof(double));
+    s->fn[a] = (double*)calloc(s->n, sizeof(double));
+    s->hn[a] = (double*)calloc(s->n, sizeof(double));
+  }
+  s->rho = (double*)calloc(s->n, sizeof(double));
+  s->ux = (double*)calloc(s->n, sizeof(double));
+  s->uy = (double*)calloc(s->n, sizeof(double));
+  s->theta = (double*)calloc(s->n, sizeof(double));
+  s->Qx = (double*)calloc(s->n, sizeof(double));
+  s->Qy = (double*)calloc(s->n, sizeof(double));
+  return s;
+}
+
+void orc_free(orc_state* s) {
+  if (!s) return;
+  for (int a = 0; a < 9; ++a) {
+    free(s->f[a]);
+    free(s->h[a]);
+    free(s->fn[a]);
+    free(s->hn[a]);
+  }
+  free(s->rho);
+  free(s->ux);
+  free(s->uy);
+  free(s->theta);
+  free(s->Qx);
+  free(s->Qy);
+  free(s);
+}
+
+/* Initial state (the paper is silent): fbar = f^eq(rho, u, T), hbar = h^eq. */
+void orc_init(orc_state* s, const double* rho, const double* ux, const double* uy,
+              const double* T) {
+  const orc_params* p = &s->p;
+  double RT0 = p->R * p->T0;
+  for (long i = 0; i < s->n; ++i) {
+    double th = T[i] / p->T0;
+    double feq[9], heq[9];
+    orc_feq(RT0, rho[i], ux[i], uy[i], th, feq);
+    if (p->energy_model == ORC_E_TOTAL) {
+      double E = 0.5 * (p->b * p->R * T[i] + ux[i] * ux[i] + uy[i] * uy[i]);
+      orc_heq(RT0, rho[i], ux[i], uy[i], th, E, feq, heq);
+    } else {
+      orc_heq_internal(RT0, p->b, th, feq, heq);
+    }
+    for (int a = 0; a < 9; ++a) {
+      s->f[a][i] = feq[a];
+      s->h[a][i] = heq[a];
+    }
+  }
+}
+
+/* Moments of the pre-collision state at node i: Eq. 35 with the force shift
+ * (rho u = sum e fbar + a/2, a = (0, -rho g)), Eq. 37 or the internal-energy
+ * temperature under Eq. 38. */
+static void node_moments(const orc_state* s, long i, double* rho, double* ux, double* uy,
+                         double* theta) {
+  const orc_params* p = &s->p;
+  double r = 0, jx = 0, jy = 0, sh = 0;
+  for (int a = 0; a < 9; ++a) {
+    r += s->f[a][i];
+    jx += EX[a] * s->f[a][i];
+    jy += EY[a] * s->f[a][i];
+    sh += s->h[a][i];
+  }
+  double ax = 0.0, ay = -r * p->g;
+  double vx = (jx + 0.5 * ax) / r;
+  double vy = (jy + 0.5 * ay) / r;
+  double T;
+  if (p->energy_model == ORC_E_TOTAL)
+    T = 2.0 / (p->b * p->R) * (sh / r - 0.5 * (vx * vx + vy * vy));
+  else
+    T = 2.0 * sh / (r * p->b * p->R);
+  *rho = r;
+  *ux = vx;
+  *uy = vy;
+  *theta = T / p->T0;
+}
+
+/* Wall temperature ratio for side `side` seen from node i. */
+static double wall_theta(const orc_state* s, int side, long i) {
+  const orc_params* p = &s->p;
+  if (p->bc[side] == ORC_WALL_ISOTHERMAL) return p->T_wall[side] / p->T0;
+  return s->theta[i];
+}
+
+/* Q of the neighbour across one side of node i (Eq. 50 stencil). */
+static double neighbour_Q(const orc_state* s, int x, int y, int side, int comp) {
+  const orc_params* p = &s->p;
+  int nx = p->nx, ny = p->ny;
+  int xx = x + (side == 0 ? -1 : side == 1 ? 1 : 0);
+  int yy = y + (side == 2 ? -1 : side == 3 ? 1 : 0);
+  const double* Q = comp == 0 ? s->Qx : s->Qy;
+  long i = (long)y * nx + x;
+  int outside = xx < 0 || xx >= nx || yy < 0 || yy >= ny;
+  if (!outside) return Q[(long)yy * nx + xx];
+  if (p->bc[side] == ORC_PERIODIC) {
+    xx = (xx + nx) % nx;
+    yy = (yy + ny) % ny;
+    return Q[(long)yy * nx + xx];
+  }
+  /* mirror ghost across the wall: Q_g = 2 Q_w - Q(node) */
+  double Qw = s->rho[i] * p->u_wall[side][comp] * (1.0 - wall_theta(s, side, i));
+  return 2.0 * Qw - Q[i];
+}
+
+static void phase1(orc_state* s, int nthreads) {
+  const orc_params* p = &s->p;
+  (void)nthreads;
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+  for (int y = 0; y < p->ny; ++y) {
+    for (int x = 0; x < p->nx; ++x) {
+      long i = (long)y * p->nx + x;
+      node_moments(s, i, &s->rho[i], &s->ux[i], &s->uy[i], &s->theta[i]);
+      s->Qx[i] = s->rho[i] * s->ux[i] * (1.0 - s->theta[i]);
+      s->Qy[i] = s->rho[i] * s->uy[i] * (1.0 - s->theta[i]);
+    }
+  }
+}
+
+static void phase2(orc_state* s, int nthreads) {
+  const orc_params* p = &s->p;
+  const int nx = p->nx, ny = p->ny;
+  const double RT0 = p->R * p->T0;
+  const double wf = 2.0 / (2.0 * p->tau_f + 1.0); /* omega_f below Eq. 34, dt = 1 */
+  const double wh = 2.0 / (2.0 * p->tau_h + 1.0); /* omega_h below Eq. 36 */
+  (void)nthreads;
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+  for (int y = 0; y < ny; ++y) {
+    for (int x = 0; x < nx; ++x) {
+      long i = (long)y * nx + x;
+      double rho = s->rho[i], ux = s->ux[i], uy = s->uy[i], th = s->theta[i];
+      double usq = ux * ux + uy * uy;
+
+      /* Eq. 50: central differences of Q; Eq. 48-49: C_a. */
+      double C[9] = {0};
+      if (p->correction) {
+        double dQx = 0.5 * (neighbour_Q(s, x, y, 1, 0) - neighbour_Q(s, x, y, 0, 0));
+        double dQy = 0.5 * (neighbour_Q(s, x, y, 3, 1) - neighbour_Q(s, x, y, 2, 1));
+        orc_correction(dQx, dQy, C);
+      }
+      /* Force absorbed into C (text under Eq. 51). */
+      double F[9];
+      orc_force(RT0, ux, uy, 0.0, -rho * p->g, F);
+      for (int a = 0; a < 9; ++a) C[a] += F[a];
+
+      double feq[9], heq[9];
+      orc_feq(RT0, rho, ux, uy, th, feq);
+      if (p->energy_model == ORC_E_TOTAL) {
+        double E = 0.5 * (p->b * RT0 * th + usq); /* E = (bRT + u^2)/2 */
+        orc_heq(RT0, rho, ux, uy, th, E, feq, heq);
+      } else {
+        orc_heq_internal(RT0, p->b, th, feq, heq);
+      }
+
+      /* Collision: Eq. 34 (f, "+(1 - w_f/2) C" from Eqs. 32-33) and Eq. 36 or
+       * Eq. 38 (h). */
+      double fs[9], hs[9];
+      for (int a = 0; a < 9; ++a) {
+        double fa = s->f[a][i], ha = s->h[a][i];
+        fs[a] = fa - wf * (fa - feq[a]) + (1.0 - 0.5 * wf) * C[a];
+        hs[a] = ha - wh * (ha - heq[a]);
+        if (p->energy_model == ORC_E_TOTAL) {
+          double eu = EX[a] * ux + EY[a] * uy;
+          double Z = p->z_full ? eu - 0.5 * usq : eu;
+          hs[a] += (wh - wf) * Z * (fa - feq[a] + 0.5 * C[a]);
+        }
+      }
+
+      /* Wall (f, adiabatic h) and ghost (isothermal h) equilibria for the up
+       * to two sides this node touches. */
+      double fw[4][9], hw[4][9];
+      int have[4] = {0, 0, 0, 0};
+
+      /* Streaming (LHS of Eqs. 34 and 36: x + e_a at t + 1). */
+      for (int a = 0; a < 9; ++a) {
+        int dx = x + EX[a], dy = y + EY[a];
+        int ox = dx < 0 ? 0 : (dx >= nx ? 1 : -1);
+        int oy = dy < 0 ? 2 : (dy >= ny ? 3 : -1);
+        int side = -1;
+        if (ox >= 0 && p->bc[ox] != ORC_PERIODIC)
+          side = ox;
+        else if (oy >= 0 && p->bc[oy] != ORC_PERIODIC)
+          side = oy;
+        if (side < 0) {
+          long j = (long)((dy + ny) % ny) * nx + (long)((dx + nx) % nx);
+          s->fn[a][j] = fs[a];
+          s->hn[a][j] = hs[a];
+          continue;
+        }
+        double uwx = p->u_wall[side][0], uwy = p->u_wall[side][1];
+        int iso = p->bc[side] == ORC_WALL_ISOTHERMAL;
+        if (!have[side]) {
+          double thw = wall_theta(s, side, i);
+          orc_feq(RT0, rho, uwx, uwy, th, fw[side]);
+          /* h: ghost state for isothermal walls, wall state for adiabatic. */
+          double thg = iso ? 2.0 * thw - th : th;
+          double rg = iso ? rho * th / thg : rho;
+          double ugx = iso ? 2.0 * uwx - ux : uwx;
+          double ugy = iso ? 2.0 * uwy - uy : uwy;
+          double fg[9];
+          orc_feq(RT0, rg, ugx, ugy, thg, fg);
+          if (p->energy_model == ORC_E_TOTAL) {
+            double Eg = 0.5 * (p->b * RT0 * thg + ugx * ugx + ugy * ugy);
+            orc_heq(RT0, rg, ugx, ugy, thg, Eg, fg, hw[side]);
+          } else {
+            orc_heq_internal(RT0, p->b, thg, fg, hw[side]);
+          }
+          have[side] = 1;
+        }
+        int b = OPP[a]; /* reflected direction, points back into the fluid */
+        double A = 0.5 * (fw[side][b] - fw[side][a]);   /* odd part of f^eq along e_b */
+        s->fn[b][i] = fs[a] + 2.0 * A;
+        if (iso) {
+          s->hn[b][i] = hw[side][b] + (hs[b] - heq[b]);
+        } else {
+          double B = 0.5 * (hw[side][b] - hw[side][a]); /* odd part of h^eq */
+          s->hn[b][i] = hs[a] + 2.0 * B;
+        }
+      }
+    }
+  }
+}
+
+void orc_step(orc_state* s, long nsteps, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  for (long t = 0; t < nsteps; ++t) {
+    phase1(s, nthreads);
+    phase2(s, nthreads);
+    for (int a = 0; a < 9; ++a) {
+      double* tf = s->f[a];
+      s->f[a] = s->fn[a];
+      s->fn[a] = tf;
+      double* th = s->h[a];
+      s->h[a] = s->hn[a];
+      s->hn[a] = th;
+    }
+  }
+}
+
+/* Macroscopic output of the current state: rho, u, T (T = theta T0). */
+void orc_moments(const orc_state* s, double* rho, double* ux, double* uy, double* T) {
+  for (long i = 0; i < s->n; ++i) {
+    double r, vx, vy, th;
+    node_moments(s, i, &r, &vx, &vy, &th);
+    rho[i] = r;
+    ux[i] = vx;
+    uy[i] = vy;
+    T[i] = th * s->p.T0;
+  }
+}
+
+/* Sums of rho, rho u (with the force shift), and of hbar (= sum rho E). */
+void orc_conserved(const orc_state* s, double out[4]) {
+  double m = 0, px = 0, py = 0, e = 0;
+  for (long i = 0; i < s->n; ++i) {
+    double r, vx, vy, th;
+    node_moments(s, i, &r, &vx, &vy, &th);
+    m += r;
+    px += r * vx;
+    py += r * vy;
+    for (int a = 0; a < 9; ++a) e += s->h[a][i];
+  }
+  out[0] = m;
+  out[1] = px;
+  out[2] = py;
+  out[3] = e;
+}
+
+/* Populations as [18][ny][nx]: f_0..f_8 then h_0..h_8. */
+void orc_get_pops(const orc_state* s, double* out) {
+  for (int a = 0; a < 9; ++a) {
+    memcpy(out + (long)a * s->n, s->f[a], sizeof(double) * s->n);
+    memcpy(out + (long)(9 + a) * s->n, s->h[a], sizeof(double) * s->n);
+  }
+}
+
+void orc_set_pops(orc_state* s, const double* in) {
+  for (int a = 0; a < 9; ++a) {
+    memcpy(s->f[a], in + (long)a * s->n, sizeof(double) * s->n);
+    memcpy(s->h[a], in + (long)(9 + a) * s->n, sizeof(double) * s->n);
+  }
+}
+
+int orc_param_size(void) { return (int)sizeof(orc_params); }

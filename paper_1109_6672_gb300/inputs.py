@@ -1,0 +1,131 @@
+"""Seeded synthetic inputs and workload recipes.
+
+This module holds no step arithmetic of the method: it draws the initial
+macroscopic fields (rho, u, T) from a seeded generator and fills the parameter
+dictionaries of the named workloads.  Both the CUDA path and the CPU oracle
+receive exactly these arrays and parameters.
+
+Sides are ordered x-, x+, y-, y+ everywhere.  Lattice units: dx = dt = 1,
+c = sqrt(3 R T0) = 1, so R T0 = 1/3 (Eq. 6 and Eq. 28 of arXiv:1109.6672).
+
+Parameter mapping used by the recipes (BGK scheme, Eq. 30 and text around it):
+the shear viscosity is mu = tau_f p, so nu = tau_f R T; the thermal
+diffusivity is chi = tau_h R T; Pr = tau_f / tau_h.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+PERIODIC, WALL_ISOTHERMAL, WALL_ADIABATIC = 0, 1, 2
+E_TOTAL, E_INTERNAL = 0, 1
+P_FP64, P_FP32, P_FP32_FP16, P_FP32_BF16 = 0, 1, 2, 3
+RT0 = 1.0 / 3.0
+
+
+def base_params(nx: int, ny: int, **kw) -> dict:
+    p = dict(
+        nx=int(nx), ny=int(ny), bc=[PERIODIC] * 4, tau_f=0.3, tau_h=0.3 / 0.71, Pr=0.0,
+        R=1.0 / 3.0, T0=1.0, b=3.0, u_wall=[[0.0, 0.0] for _ in range(4)],
+        T_wall=[1.0] * 4, g=0.0, energy_model=E_TOTAL, correction=1, z_full=1,
+        precision=P_FP64,
+    )
+    p.update(kw)
+    return p
+
+
+def uniform_fields(nx: int, ny: int, seed: int, rho0: float = 1.0, u_amp: float = 0.0,
+                   T0: float = 1.0, T_amp: float = 0.0, rho_amp: float = 0.0):
+    """rho, ux, uy, T as [ny, nx] float64: constant means plus independent
+    uniform noise U(-amp, amp) from numpy's PCG64 seeded with ``seed``.
+    T_amp is relative to T0."""
+    rng = np.random.default_rng(seed)
+    shape = (ny, nx)
+    rho = rho0 + rho_amp * rng.uniform(-1.0, 1.0, shape) if rho_amp else np.full(shape, rho0)
+    ux = u_amp * rng.uniform(-1.0, 1.0, shape) if u_amp else np.zeros(shape)
+    uy = u_amp * rng.uniform(-1.0, 1.0, shape) if u_amp else np.zeros(shape)
+    T = T0 * (1.0 + T_amp * rng.uniform(-1.0, 1.0, shape)) if T_amp else np.full(shape, T0)
+    return rho, ux, uy, T
+
+
+# ---- named workloads -------------------------------------------------------
+
+def couette(ny: int = 33, nx: int = 4, U: float = 0.05, nu: float = 0.1, Pr: float = 0.71,
+            b: float = 3.0, **kw):
+    """Thermal Couette flow: periodic in x, halfway walls at y = -1/2 and
+    y = ny - 1/2 (H = ny); bottom at rest, top moving at (U, 0); both walls at
+    T = T0 = 1.  Starts from uniform rest."""
+    tau_f = nu / RT0
+    p = base_params(nx, ny, tau_f=tau_f, tau_h=tau_f / Pr, b=b,
+                    bc=[PERIODIC, PERIODIC, WALL_ISOTHERMAL, WALL_ISOTHERMAL],
+                    u_wall=[[0.0, 0.0], [0.0, 0.0], [0.0, 0.0], [U, 0.0]], **kw)
+    return p, uniform_fields(nx, ny, seed=0)
+
+
+def couette_b(ny: int = 33, nx: int = 4, **kw):
+    """Couette variant with a 5 % viscous-heating rise: Pr = 3, b = 3
+    (gamma = 5/3), U = 1/3 (Ma = U / sqrt(gamma R T0) = 0.447), nu = 0.2.
+    The peak rise of the constant-property solution is
+    Pr U^2 / (4 (b + 2) R T0) = 0.05.  (Pr = 5 with tau_h = tau_f / 5 is
+    outside the stable range of the BGK scheme, so Pr = 3 is used.)"""
+    return couette(ny=ny, nx=nx, U=1.0 / 3.0, nu=0.2, Pr=3.0, b=3.0, **kw)
+
+
+def periodic_box(n: int = 4096, seed: int = 2, precision: int = P_FP32, nx: int | None = None,
+                 ny: int | None = None, **kw):
+    """Fully periodic box: rho = 1, u ~ U(-1e-3, 1e-3), T = T0 (1 + U(-1e-2, 1e-2)),
+    tau_f = 0.3 (nu = 0.1), Pr = 0.71, b = 3, total-energy model, correction on."""
+    nx = n if nx is None else nx
+    ny = n if ny is None else ny
+    p = base_params(nx, ny, precision=precision, **kw)
+    return p, uniform_fields(nx, ny, seed=seed, u_amp=1e-3, T_amp=1e-2)
+
+
+def cavity_gravity(H: int, dT_over_T0: float, Ma: float = 0.1, strat: float = 0.05) -> float:
+    """Gravity for a cavity of height H: the smaller of the value that keeps the
+    hydrostatic stratification g H / (R T0) at ``strat`` and the value whose
+    free-fall velocity sqrt(g beta dT H) equals Ma * sqrt(gamma R T0) with
+    gamma = 1.4 (beta = 1/T_r, T_r = T0)."""
+    g_strat = strat * RT0 / H
+    U = Ma * math.sqrt(1.4 * RT0)
+    g_ma = U * U / (dT_over_T0 * H)
+    return min(g_strat, g_ma)
+
+
+def cavity(n: int = 256, Ra: float = 1e5, Pr: float = 0.71, dT_over_T0: float = 0.01,
+           seed: int = 1, noise: float = 1e-4, b: float = 5.0, precision: int = P_FP64,
+           nu_min: float = 0.0, **kw):
+    """Differentially heated square cavity (natural convection): hot wall at
+    x-, cold wall at x+ (isothermal, T0 (1 +- dT/2)), adiabatic top and bottom,
+    internal-energy model (Eq. 38), gravity a = (0, -rho g), b = 5
+    (gamma = 1.4).  Ra = g beta dT H^3 Pr / nu^2 with beta = 1/T0 (Eq. 57-58),
+    hence nu = sqrt(g (dT/T0) H^3 Pr / Ra).  ``nu_min`` floors nu (lowering the
+    effective Ra) for under-resolved members of a batch."""
+    H = n
+    g = cavity_gravity(H, dT_over_T0)
+    nu = math.sqrt(g * dT_over_T0 * H ** 3 * Pr / Ra)
+    nu = max(nu, nu_min)
+    tau_f = nu / RT0
+    Th, Tl = 1.0 + 0.5 * dT_over_T0, 1.0 - 0.5 * dT_over_T0
+    p = base_params(n, n, tau_f=tau_f, tau_h=tau_f / Pr, b=b, g=g, energy_model=E_INTERNAL,
+                    bc=[WALL_ISOTHERMAL, WALL_ISOTHERMAL, WALL_ADIABATIC, WALL_ADIABATIC],
+                    T_wall=[Th, Tl, 1.0, 1.0], precision=precision, **kw)
+    p["Ra_effective"] = g * dT_over_T0 * H ** 3 * Pr / (nu * nu)
+    return p, uniform_fields(n, n, seed=seed, u_amp=noise)
+
+
+def batch_cavities(count: int = 256, seed: int = 4, sides=tuple(range(64, 513, 32)),
+                   precision: int = P_FP32_BF16, nu_min: float = 0.01):
+    """Batch of independent cavities: side uniform over ``sides``, dT/T0 ~
+    U[0.01, 0.6], Ra log-uniform in [1e4, 1e6], Pr = 0.71."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(rng.choice(sides))
+        dT = float(rng.uniform(0.01, 0.6))
+        Ra = float(10.0 ** rng.uniform(4.0, 6.0))
+        p, fields = cavity(n=n, Ra=Ra, dT_over_T0=dT, seed=seed * 100003 + k, precision=precision,
+                           nu_min=nu_min)
+        out.append((p, fields))
+    return out

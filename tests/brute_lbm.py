@@ -1,0 +1,192 @@
+"""Independent NumPy restatement of one step of the BGK coupled DDF scheme
+(arXiv:1109.6672, Sec. III.C), used only to cross-check the C oracle on tiny
+grids.  It is written from the paper separately from the oracle and takes
+different routes to the same quantities:
+
+* Eq. 18a is expanded per speed shell (rest, axis, diagonal) by hand instead of
+  being evaluated from the generic Hermite form;
+* moments use array contractions;
+* streaming is pull-based (``np.roll``), and the wall rules are applied from the
+  receiving node's side instead of the sending node's side.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+OPP = np.array([0, 3, 4, 1, 2, 7, 8, 5, 6])
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+PERIODIC, ISO, ADIA = 0, 1, 2
+
+
+def feq_shells(rho, ux, uy, th):
+    """Eq. 18a with R T0 = 1/3, D = 2, expanded per shell:
+    rest:     rho 4/9  [1 - 3/2 u^2 - (th - 1)]
+    axis:     rho 1/9  [1 + 3 eu (1 - (th-1)/2) + 9/2 eu^2 - 3/2 u^2 + (th-1)/2]
+    diagonal: rho 1/36 [1 + 3 th eu + 9/2 eu^2 - 3/2 u^2 + 2 (th-1)]"""
+    usq = ux * ux + uy * uy
+    out = []
+    for a in range(9):
+        eu = EX[a] * ux + EY[a] * uy
+        if a == 0:
+            v = rho * (4 / 9) * (1 - 1.5 * usq - (th - 1))
+        elif a <= 4:
+            v = rho / 9 * (1 + 3 * eu * (1 - 0.5 * (th - 1)) + 4.5 * eu * eu - 1.5 * usq + 0.5 * (th - 1))
+        else:
+            v = rho / 36 * (1 + 3 * th * eu + 4.5 * eu * eu - 1.5 * usq + 2 * (th - 1))
+        out.append(v)
+    return np.array(out)
+
+
+def heq_total(rho, ux, uy, th, b, feq):
+    """Eq. 18b with E = (b R T + u^2)/2, p = rho R T, R T = th/3."""
+    usq = ux * ux + uy * uy
+    E = 0.5 * (b * th / 3 + usq)
+    p = rho * th / 3
+    out = []
+    for a in range(9):
+        eu = EX[a] * ux + EY[a] * uy
+        e2 = EX[a] ** 2 + EY[a] ** 2
+        out.append(E * feq[a] + W[a] * p * (3 * eu + 9 * eu * eu - 3 * usq + 0.5 * th * (3 * e2 - 2)))
+    return np.array(out)
+
+
+def heq_internal(th, b, feq):
+    return 0.5 * b * (th / 3) * feq
+
+
+class Brute:
+    def __init__(self, p: dict):
+        self.p = p
+        self.nx, self.ny = p["nx"], p["ny"]
+        assert abs(p["R"] * p["T0"] - 1 / 3) < 1e-14
+
+    def init(self, rho, ux, uy, T):
+        p = self.p
+        th = T / p["T0"]
+        self.F = feq_shells(rho, ux, uy, th)
+        self.H = (heq_total(rho, ux, uy, th, p["b"], self.F) if p["energy_model"] == 0
+                  else heq_internal(th, p["b"], self.F))
+        return self
+
+    def moments(self):
+        p = self.p
+        rho = self.F.sum(0)
+        jx = np.tensordot(EX, self.F, 1)
+        jy = np.tensordot(EY, self.F, 1) - 0.5 * rho * p["g"]
+        ux, uy = jx / rho, jy / rho
+        sh = self.H.sum(0)
+        if p["energy_model"] == 0:
+            th = 6 / p["b"] * (sh / rho - 0.5 * (ux * ux + uy * uy))
+        else:
+            th = 6 * sh / (rho * p["b"])
+        return rho, ux, uy, th
+
+    def _wall_theta(self, side, th_node):
+        if self.p["bc"][side] == ISO:
+            return self.p["T_wall"][side] / self.p["T0"] + 0 * th_node
+        return th_node
+
+    def _grad(self, Q, axis, rho, th, comp):
+        """Eq. 50 with periodic wrap or a mirror ghost across a wall."""
+        lo_side, hi_side = (0, 1) if axis == 1 else (2, 3)
+        n = Q.shape[axis]
+        plus = np.roll(Q, -1, axis=axis)
+        minus = np.roll(Q, 1, axis=axis)
+        for side, arr, idx in ((hi_side, plus, n - 1), (lo_side, minus, 0)):
+            if self.p["bc"][side] == PERIODIC:
+                continue
+            sl = [slice(None), slice(None)]
+            sl[axis] = idx
+            sl = tuple(sl)
+            thw = self._wall_theta(side, th[sl])
+            Qw = rho[sl] * self.p["u_wall"][side][comp] * (1 - thw)
+            arr[sl] = 2 * Qw - Q[sl]
+        return 0.5 * (plus - minus)
+
+    def step(self, n=1):
+        for _ in range(n):
+            self._step()
+        return self
+
+    def _step(self):
+        p = self.p
+        rho, ux, uy, th = self.moments()
+        usq = ux * ux + uy * uy
+        Qx, Qy = rho * ux * (1 - th), rho * uy * (1 - th)
+        C = np.zeros_like(self.F)
+        if p["correction"]:
+            dqx = self._grad(Qx, 1, rho, th, 0)
+            dqy = self._grad(Qy, 0, rho, th, 1)
+            phx, phy = 3 * (dqx + dqy), dqx - dqy
+            C[0] = -phx / 9
+            C[1] = C[3] = -phx / 36 + phy / 4
+            C[2] = C[4] = -phx / 36 - phy / 4
+            C[5:] = phx / 18
+        ay = -rho * p["g"]
+        for a in range(9):  # Guo force, R T0 = 1/3
+            ea = EY[a] * ay
+            eu = EX[a] * ux + EY[a] * uy
+            C[a] += W[a] * (3 * ea + 9 * (eu * ea - (uy * ay) / 3))
+        feq = feq_shells(rho, ux, uy, th)
+        if p["energy_model"] == 0:
+            heq = heq_total(rho, ux, uy, th, p["b"], feq)
+        else:
+            heq = heq_internal(th, p["b"], feq)
+        wf = 1 / (p["tau_f"] + 0.5)
+        wh = 1 / (p["tau_h"] + 0.5)
+        fs = self.F + wf * (feq - self.F) + (1 - wf / 2) * C
+        hs = self.H + wh * (heq - self.H)
+        if p["energy_model"] == 0:
+            for a in range(9):
+                eu = EX[a] * ux + EY[a] * uy
+                Z = eu - 0.5 * usq if p["z_full"] else eu
+                hs[a] += (wh - wf) * Z * (self.F[a] - feq[a] + 0.5 * C[a])
+        # pull streaming with wrap, then overwrite wall-crossing pulls
+        Fn = np.empty_like(fs)
+        Hn = np.empty_like(hs)
+        for a in range(9):
+            Fn[a] = np.roll(fs[a], (EY[a], EX[a]), axis=(0, 1))
+            Hn[a] = np.roll(hs[a], (EY[a], EX[a]), axis=(0, 1))
+        nx, ny = self.nx, self.ny
+        for y in range(ny):
+            for x in range(nx):
+                if 0 < x < nx - 1 and 0 < y < ny - 1:
+                    continue
+                for a in range(1, 9):
+                    sx, sy = x - EX[a], y - EY[a]
+                    out_x = 0 if sx < 0 else (1 if sx >= nx else -1)
+                    out_y = 2 if sy < 0 else (3 if sy >= ny else -1)
+                    side = -1
+                    if out_x >= 0 and p["bc"][out_x] != PERIODIC:
+                        side = out_x
+                    elif out_y >= 0 and p["bc"][out_y] != PERIODIC:
+                        side = out_y
+                    if side < 0:
+                        continue
+                    r, t = rho[y, x], th[y, x]
+                    uw = p["u_wall"][side]
+                    iso = p["bc"][side] == ISO
+                    thw = p["T_wall"][side] / p["T0"] if iso else t
+                    fw = feq_shells(r, uw[0], uw[1], t)
+                    o = OPP[a]
+                    Fn[a, y, x] = fs[o, y, x] + (fw[a] - fw[o])
+                    if iso:
+                        # ghost node one spacing outside: linear in u and theta
+                        # through the wall, equal pressure
+                        tg = 2 * thw - t
+                        rg, ugx, ugy = r * t / tg, 2 * uw[0] - ux[y, x], 2 * uw[1] - uy[y, x]
+                        fg = feq_shells(rg, ugx, ugy, tg)
+                        hg = (heq_total(rg, ugx, ugy, tg, p["b"], fg) if p["energy_model"] == 0
+                              else heq_internal(tg, p["b"], fg))
+                        Hn[a, y, x] = hg[a] + hs[a, y, x] - heq[a, y, x]
+                    else:
+                        fa = feq_shells(r, uw[0], uw[1], t)
+                        ha = (heq_total(r, uw[0], uw[1], t, p["b"], fa) if p["energy_model"] == 0
+                              else heq_internal(t, p["b"], fa))
+                        Hn[a, y, x] = hs[o, y, x] + (ha[a] - ha[o])
+        self.F, self.H = Fn, Hn
+
+    def pops(self):
+        return np.concatenate([self.F, self.H], 0)
