@@ -1,0 +1,318 @@
+"""Benchmark of the fused coupled f+h D2Q9 step on GB300.
+
+Workload (one "step" = one time step of the whole hot path over one grid):
+periodic box 4096 x 4096, rho = 1, u ~ U(-1e-3, 1e-3), T = T0 (1 + U(-1e-2,
+1e-2)) (seed 2), tau_f = 0.3, Pr = 0.71, b = 3, total-energy model,
+correction on, FP32 storage and arithmetic.  The state (2.4 GB) is far larger
+than L2 (129 MB), so no L2 flush is needed between steps.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the
+host cores on a bounded sample of the same workload instead.
+Multi-GPU (torchrun): every rank runs an independent replica (the single grid
+is not sharded; weak scaling), max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled f+h D2Q9 GLUPS and % HBM roofline; served p50/p99 latency"
+UNIT = "GLUPS"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"lbm_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [s.strip() for s in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        mine = [r for r in rows if r[0] == str(self.gpu)]
+        if mine and len({r[0] for r in rows}) > 1:
+            rows = mine
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_glups(n_side: int, steps: int, threads: int):
+    """Time the FP64 oracle on an n_side^2 sample of the box workload."""
+    from oracle import oracle
+    from paper_1109_6672_gb300 import inputs
+
+    p, fields = inputs.periodic_box(n=n_side, precision=inputs.P_FP64)
+    o = oracle.Oracle(p).init(*fields)
+    o.step(1, threads)
+    t0 = time.perf_counter()
+    o.step(steps, threads)
+    dt = time.perf_counter() - t0
+    return n_side * n_side * steps / dt / 1e9, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cores = cpu_cores()
+    side = args.ref_side
+    glups_per_step = []
+    for _ in range(args.warmup):
+        oracle_glups(side, 1, cores)
+    total_t = 0.0
+    for _ in range(args.steps):
+        g, dt = oracle_glups(side, 1, cores)
+        glups_per_step.append(g)
+        total_t += dt
+    value = side * side * args.steps / total_t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"periodic box {side}x{side} sample of the 4096x4096 box "
+                               "(FP64 CPU oracle, OpenMP over rows)",
+                   "nx": side, "ny": side},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{side}x{side} periodic box, {args.steps} timed steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def time_steps(torch, lbm_mod, g, stream, steps):
+    """CUDA-event time of `steps` back-to-back step launches on `stream`."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    g.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1109_6672_gb300 import build as cuda_build
+    from paper_1109_6672_gb300 import inputs, lbm
+
+    cuda_build.build()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    prec = {"f64": lbm.LBM_P_FP64, "f32": lbm.LBM_P_FP32, "f16": lbm.LBM_P_FP32_FP16,
+            "bf16": lbm.LBM_P_FP32_BF16}[args.precision]
+    n = args.n
+    p, fields = inputs.periodic_box(n=n, precision=prec)
+    stream = torch.cuda.Stream()
+    g = lbm.Lbm(p, stream=stream.cuda_stream)
+    if args.threads:
+        g.set_launch(args.threads, args.rows)
+    # inputs resident in HBM before the timed region
+    dev_fields = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in fields]
+    with torch.cuda.stream(stream):
+        lbm.lbm_init_device(g.h, *[t.data_ptr() for t in dev_fields])
+    stream.synchronize()
+    g.step(args.warmup)
+    g.sync()
+
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local_rank
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_index) as clk:
+        elapsed = time_steps(torch, lbm, g, stream, args.steps)
+    torch.cuda.synchronize()
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        dist.barrier()
+    nodes = n * n
+    value = world * nodes * args.steps / elapsed / 1e9
+    per_launch = elapsed / args.steps
+    bpn = lbm.BYTES_PER_NODE_UPDATE[prec]
+    hbm, peak_kind = peaks()
+    achieved = nodes * bpn / per_launch / 1e9
+
+    # e2e through the C ABI with host buffers: H2D of the fields from pinned
+    # memory, `steps` steps, D2H of the moments, all inside the timed region
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in fields]
+    out = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in range(4)]
+    e2e_steps = args.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbm.lbm_init(g.h, *[t.numpy() for t in pinned])
+    g.step(e2e_steps)
+    rc = lbm.load().lbm_moments(g.h, *[lbm._dp(t.numpy()) for t in out])
+    if rc != 0:
+        raise lbm.LbmError(rc, lbm.lbm_last_error(g.h))
+    e2e_t = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_t], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e_value = world * nodes * e2e_steps / e2e_t / 1e9
+
+    variants = {}
+    if args.variants and world == 1:
+        for name, pv in (("f64", lbm.LBM_P_FP64), ("f16dev", lbm.LBM_P_FP32_FP16),
+                         ("bf16dev", lbm.LBM_P_FP32_BF16)):
+            if pv == prec:
+                continue
+            g.close()
+            pp = dict(p, precision=pv)
+            gv = lbm.Lbm(pp, stream=stream.cuda_stream)
+            with torch.cuda.stream(stream):
+                lbm.lbm_init_device(gv.h, *[t.data_ptr() for t in dev_fields])
+            ksteps = max(3, args.steps // (8 if pv == lbm.LBM_P_FP64 else 1))
+            gv.step(args.warmup)
+            gv.sync()
+            tv = time_steps(torch, lbm, gv, stream, ksteps)
+            gl = nodes * ksteps / tv / 1e9
+            variants[name] = {"glups": gl, "bytes_per_node_update": lbm.BYTES_PER_NODE_UPDATE[pv],
+                              "achieved_gbs": gl * lbm.BYTES_PER_NODE_UPDATE[pv],
+                              "hbm_frac": gl * lbm.BYTES_PER_NODE_UPDATE[pv] / hbm,
+                              "steps": ksteps}
+            gv.close()
+    else:
+        g.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cores = cpu_cores()
+        side = args.ref_side
+        gl, dt = oracle_glups(side, args.ref_steps, cores)
+        cpu = {"value": gl, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{side}x{side} periodic box of the same workload, {args.ref_steps} steps "
+                         f"({dt:.1f} s), FP64, OpenMP over rows"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"f64": "f64", "f32": "f32", "f16": "f32 (f16 storage)",
+                      "bf16": "f32 (bf16 storage)"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": f"periodic box {n}x{n}, coupled f+h D2Q9 BGK, total energy, "
+                                   f"correction on, {lbm.PRECISION_NAMES[prec]} storage",
+                       "nx": n, "ny": n, "precision": args.precision,
+                       "bytes_per_node_update": bpn,
+                       "l2": "state 2x18 populations per node >> 129 MB L2; no flush",
+                       "replicas": world},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "step_kernel", "algorithmic_bytes_per_launch": nodes * bpn},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(4 * nodes * 8 / e2e_steps),
+                    "d2h_bytes_per_step": int(4 * nodes * 8 / e2e_steps)},
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+            "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f64", "f32", "f16", "bf16"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--rows", type=int, default=0)
+    ap.add_argument("--ref-side", type=int, default=1024)
+    ap.add_argument("--ref-steps", type=int, default=60)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-variants", dest="variants", action="store_false")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

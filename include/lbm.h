@@ -1,0 +1,177 @@
+/*
+ * lbm.h -- C ABI of the GB300 library for the coupled double-distribution-
+ * function (DDF) thermal lattice Boltzmann method on D2Q9 of Li, Luo, He, Gao
+ * and Tao, "Coupling lattice Boltzmann model for simulation of thermal flows
+ * on standard lattices" (arXiv:1109.6672), BGK scheme of Sec. III.C.1.
+ *
+ * One time step advances, for every node x, the density distribution f
+ * (Eq. 34, equilibrium Eq. 18a with p = rho R T) and the total-energy
+ * distribution h (Eq. 36, equilibrium Eq. 18b; or the internal-energy form of
+ * Eq. 38), with the third-moment correction C_a (Eqs. 48-50) and the Guo
+ * gravity force (text around Eq. 51), followed by streaming and the wall rules.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an int status: LBM_OK (0) or a negative LBM_ERR_*
+ *    code; no C++ exception crosses this boundary.  lbm_last_error() gives a
+ *    one-line message for the last failure on a handle.
+ *  - Host arrays are caller-owned, row-major [ny][nx] doubles (node (x, y) at
+ *    index y * nx + x), unless stated otherwise.  The library never keeps a
+ *    pointer to a caller array after the call returns.
+ *  - Device memory for the state is owned by the handle unless it was created
+ *    with lbm_create_in(), in which case the caller owns the buffer and must
+ *    keep it alive until lbm_destroy().
+ *  - Work is enqueued on the CUDA stream given at creation (NULL: the legacy
+ *    default stream).  Calls that return host data synchronise that stream.
+ *    lbm_step() is asynchronous: a kernel failure is reported by the next
+ *    call that synchronises.
+ *  - Lattice units: dx = dt = 1, c = sqrt(3 R T0) = 1 (Eq. 6 and Eq. 28), so
+ *    R * T0 must equal 1/3.  Sides are ordered x-, x+, y-, y+.
+ *  - Walls sit halfway between the boundary node and the first node outside
+ *    (at x = -1/2, x = nx - 1/2, y = -1/2, y = ny - 1/2).  The paper uses
+ *    non-equilibrium extrapolation walls; this library uses:
+ *      f: halfway bounce-back plus twice the odd part of Eq. 18a evaluated at
+ *         the boundary node's rho and theta and the wall velocity;
+ *      h, isothermal wall: non-equilibrium extrapolation from a ghost node one
+ *         spacing outside, with u_g = 2 u_w - u, theta_g = 2 theta_w - theta,
+ *         rho_g = rho theta / theta_g;
+ *      h, adiabatic wall: bounce-back plus twice the odd part of h^eq at the
+ *         boundary node's (rho, theta) and the wall velocity;
+ *      corners: a population leaving across two walls uses the x-side wall;
+ *      Eq. 50 across a wall: mirror ghost Q_g = 2 rho u_w (1 - theta_w) - Q.
+ */
+#ifndef LBM_H_
+#define LBM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  LBM_OK = 0,
+  LBM_ERR_PARAM = -1,     /* invalid argument; the handle is unchanged        */
+  LBM_ERR_OOM = -2,       /* device or host allocation failed / does not fit  */
+  LBM_ERR_CUDA = -3,      /* a CUDA call or kernel failed                     */
+  LBM_ERR_NONFINITE = -4, /* a moment or population is NaN/Inf (state kept)   */
+  LBM_ERR_TIMEOUT = -5,   /* a bounded device-side wait ran out               */
+  LBM_ERR_STATE = -6      /* call out of order (e.g. lbm_step before lbm_init) */
+};
+
+enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL_ISOTHERMAL = 1, LBM_BC_WALL_ADIABATIC = 2 };
+/* LBM_E_TOTAL: total-energy h, Eq. 18b and Eq. 36 (viscous heating and
+ * compression work, Z = e.u - u^2/2 or e.u).  LBM_E_INTERNAL: internal-energy
+ * h of Eq. 38 with h^eq = b R T f^eq / 2 and T = 2 sum h / (rho b R). */
+enum { LBM_E_TOTAL = 0, LBM_E_INTERNAL = 1 };
+/* Storage / arithmetic: FP64 everywhere; FP32 everywhere; FP32 arithmetic with
+ * populations stored as FP16 or BF16 deviations from the rest equilibrium
+ * (rho = 1, u = 0, T = T0), T recovered and reductions accumulated in FP64. */
+enum { LBM_P_FP64 = 0, LBM_P_FP32 = 1, LBM_P_FP32_FP16 = 2, LBM_P_FP32_BF16 = 3 };
+
+typedef struct {
+  int32_t nx, ny;           /* fluid nodes per axis, >= 1 (>= 3 on a walled axis)  */
+  int32_t bc[4];            /* LBM_BC_* per side x-, x+, y-, y+; a periodic side
+                               needs its opposite side periodic too             */
+  double tau_f, tau_h;      /* continuous relaxation times (Eq. 30: mu = tau_f p,
+                               lambda = tau_h (b+2)/2 p R); omega = 2/(2 tau + 1),
+                               text below Eqs. 34 and 36; both > 0             */
+  double Pr;                /* <= 0: ignored; > 0: must equal tau_f / tau_h     */
+  double R, T0;             /* gas constant and reference temperature, R T0 = 1/3 */
+  double b;                 /* degrees of freedom, gamma = (b + 2)/b (Eq. 37), b >= 2 */
+  double u_wall[4][2];      /* wall velocity per side (tangential in practice)  */
+  double T_wall[4];         /* wall temperature per isothermal side, > 0        */
+  double g;                 /* gravity; force density a = (0, -rho g), text under
+                               Eq. 51; needs energy_model = LBM_E_INTERNAL      */
+  int32_t energy_model;     /* LBM_E_TOTAL or LBM_E_INTERNAL                    */
+  int32_t correction;       /* 1: C_a of Eqs. 48-50; 0: omitted                 */
+  int32_t z_full;           /* 1: Z = e.u - u^2/2 (Eq. 7b); 0: Z = e.u           */
+  int32_t precision;        /* LBM_P_*                                          */
+} lbm_params;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Bytes of device memory the state of one grid occupies (two population
+ * buffers in the layout described in lbm_create_in()).  Returns a negative
+ * LBM_ERR_* code for invalid parameters. */
+int64_t lbm_state_bytes(const lbm_params* p);
+
+/* Validates *p, allocates the device state and creates a handle bound to the
+ * current CUDA device and to cuda_stream (a cudaStream_t; NULL = default).
+ * On error *out is NULL.  Errors: LBM_ERR_PARAM (see lbm_params), LBM_ERR_OOM,
+ * LBM_ERR_CUDA. */
+int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out);
+
+/* Same as lbm_create() but places the state in caller-owned device memory
+ * (for example a buffer from a caching allocator): device_buffer must be
+ * 256-byte aligned and at least lbm_state_bytes(p) long.  Layout (opaque to
+ * callers): two buffers, each 18 planes per row, row-interleaved
+ * [y + 1][population][x + 1] with a one-node ghost ring. */
+int lbm_create_in(const lbm_params* p, void* cuda_stream, void* device_buffer, int64_t bytes,
+                  lbm_handle** out);
+
+/* Sets the state to equilibrium (Eq. 18a, Eq. 18b or the Eq. 38 form) at the
+ * given host fields (nx*ny doubles each; T in the units of T0; the paper
+ * leaves the initial state free).  Resets the step counter.  Synchronous. */
+int lbm_init(lbm_handle* h, const double* rho, const double* ux, const double* uy,
+             const double* T);
+
+/* Same as lbm_init() with device pointers (nx*ny doubles each, on the handle's
+ * device); asynchronous on the handle's stream. */
+int lbm_init_device(lbm_handle* h, const double* d_rho, const double* d_ux, const double* d_uy,
+                    const double* d_T);
+
+/* Advances n >= 0 time steps (one fused stream-and-collide kernel per step).
+ * Asynchronous; returns LBM_ERR_CUDA if a launch fails, LBM_ERR_STATE before
+ * lbm_init(). */
+int lbm_step(lbm_handle* h, int64_t n);
+
+/* Macroscopic fields of the current state: rho, u = (sum e fbar + a/2)/rho
+ * (Eq. 35 and text under Eq. 51) and T (Eq. 37, or 2 sum hbar/(rho b R)),
+ * computed in FP64 from the stored populations.  Host outputs, nx*ny each;
+ * synchronous.  LBM_ERR_NONFINITE if any value is NaN/Inf (arrays still
+ * filled). */
+int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy, double* T);
+
+/* Same as lbm_moments() into device arrays, asynchronous, no finite check. */
+int lbm_moments_device(lbm_handle* h, double* d_rho, double* d_ux, double* d_uy, double* d_T);
+
+/* FP64 sums over all nodes of rho, rho u_x, rho u_y and hbar (sum rho E for
+ * LBM_E_TOTAL, internal energy for LBM_E_INTERNAL), reduced in a fixed order
+ * (bitwise reproducible).  out: host, 4 doubles; synchronous. */
+int lbm_conserved(lbm_handle* h, double out[4]);
+
+/* Canonical pre-collision populations fbar_a(x, t), hbar_a(x, t) as
+ * host [18][ny][nx] doubles (f_0..f_8 then h_0..h_8, velocities
+ * e = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1)).
+ * Synchronous.  lbm_set_state() writes them back (rounded to the storage
+ * precision); together they checkpoint and resume a run. */
+int lbm_get_state(lbm_handle* h, double* pops);
+int lbm_set_state(lbm_handle* h, const double* pops);
+
+/* Waits for all work enqueued on the handle's stream; reports a pending
+ * kernel error as LBM_ERR_CUDA. */
+int lbm_sync(lbm_handle* h);
+
+/* Time steps taken since the last lbm_init() / lbm_set_state(). */
+int64_t lbm_steps_done(const lbm_handle* h);
+
+/* Launch shape of the step kernel: threads per block (a multiple of 32 in
+ * 64..256; each block owns threads - 2 columns, default 128) and rows per
+ * block (>= 1; 0 = about one wave of blocks, the default). */
+int lbm_set_launch(lbm_handle* h, int32_t threads, int32_t rows_per_block);
+
+/* Frees the handle and the device memory it owns.  NULL-safe. */
+void lbm_destroy(lbm_handle* h);
+
+/* Message of the last failure on h (or of the last failed lbm_create on this
+ * thread when h is NULL).  Never NULL; valid until the next call on h. */
+const char* lbm_last_error(const lbm_handle* h);
+
+/* Static name of a status code. */
+const char* lbm_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H_ */

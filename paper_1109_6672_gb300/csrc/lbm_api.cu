@@ -1,0 +1,548 @@
+// Host side of the single-grid C ABI declared in include/lbm.h: parameter
+// validation, device state, launches of the kernels in lbm_device.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_device.cuh"
+#include "lbm_host.h"
+
+using namespace lbm;
+
+struct lbm_handle {
+  lbm_params p{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  void* base = nullptr;  // start of the two state buffers
+  bool owns = false;
+  size_t buf_bytes = 0;
+  int cur = 0;  // buffer holding the state at the current time
+  int64_t steps = 0;
+  bool ready = false;
+  Grid grid{};
+  int threads = 128, rows = 0;
+  double* partial = nullptr;  // reduction scratch: RED_BLOCKS x 4
+  double* out4 = nullptr;     // reduction result
+  double* staging = nullptr;  // device staging for host transfers
+  size_t staging_bytes = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(lbm_handle* h, int code, const std::string& msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(lbm_handle* h, cudaError_t e, const char* what) {
+  return fail(h, LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+constexpr int RED_BLOCKS = 1024;
+
+size_t elem_size(int precision) {
+  switch (precision) {
+    case LBM_P_FP64: return 8;
+    case LBM_P_FP32: return 4;
+    default: return 2;
+  }
+}
+
+}  // namespace
+
+namespace lbm_host {
+
+int validate(const lbm_params* p, std::string& why) {
+  if (!p) {
+    why = "params is NULL";
+    return LBM_ERR_PARAM;
+  }
+  if (p->nx < 1 || p->ny < 1) {
+    why = "nx and ny must be >= 1";
+    return LBM_ERR_PARAM;
+  }
+  for (int s = 0; s < 4; ++s) {
+    if (p->bc[s] < 0 || p->bc[s] > 2) {
+      why = "bc values must be LBM_BC_PERIODIC, LBM_BC_WALL_ISOTHERMAL or LBM_BC_WALL_ADIABATIC";
+      return LBM_ERR_PARAM;
+    }
+  }
+  if ((p->bc[0] == LBM_BC_PERIODIC) != (p->bc[1] == LBM_BC_PERIODIC) ||
+      (p->bc[2] == LBM_BC_PERIODIC) != (p->bc[3] == LBM_BC_PERIODIC)) {
+    why = "a periodic side needs its opposite side periodic";
+    return LBM_ERR_PARAM;
+  }
+  if ((p->bc[0] != LBM_BC_PERIODIC && p->nx < 3) || (p->bc[2] != LBM_BC_PERIODIC && p->ny < 3)) {
+    why = "a walled axis needs at least 3 nodes";
+    return LBM_ERR_PARAM;
+  }
+  if ((int64_t)p->nx * (int64_t)p->ny > (int64_t)1 << 31 || p->nx > (1 << 20) ||
+      p->ny > (1 << 20)) {
+    why = "grid too large (nx * ny must be <= 2^31)";
+    return LBM_ERR_PARAM;
+  }
+  if (!(p->tau_f > 0.0) || !(p->tau_h > 0.0) || !std::isfinite(p->tau_f) ||
+      !std::isfinite(p->tau_h)) {
+    why = "tau_f and tau_h must be finite and > 0 (omega in (0, 2))";
+    return LBM_ERR_PARAM;
+  }
+  if (p->Pr > 0.0 && std::fabs(p->Pr - p->tau_f / p->tau_h) > 1e-9 * p->Pr) {
+    why = "Pr must equal tau_f / tau_h (or be <= 0)";
+    return LBM_ERR_PARAM;
+  }
+  if (!(p->R > 0.0) || !(p->T0 > 0.0) || std::fabs(p->R * p->T0 * 3.0 - 1.0) > 1e-12) {
+    why = "R * T0 must equal 1/3 (lattice speed c = sqrt(3 R T0) = 1)";
+    return LBM_ERR_PARAM;
+  }
+  if (!(p->b >= 2.0) || !std::isfinite(p->b)) {
+    why = "b (degrees of freedom) must be >= 2";
+    return LBM_ERR_PARAM;
+  }
+  for (int s = 0; s < 4; ++s) {
+    if (p->bc[s] == LBM_BC_WALL_ISOTHERMAL && !(p->T_wall[s] > 0.0)) {
+      why = "T_wall must be > 0 on isothermal walls";
+      return LBM_ERR_PARAM;
+    }
+    if (!std::isfinite(p->u_wall[s][0]) || !std::isfinite(p->u_wall[s][1])) {
+      why = "u_wall must be finite";
+      return LBM_ERR_PARAM;
+    }
+  }
+  if (p->energy_model != LBM_E_TOTAL && p->energy_model != LBM_E_INTERNAL) {
+    why = "energy_model must be LBM_E_TOTAL or LBM_E_INTERNAL";
+    return LBM_ERR_PARAM;
+  }
+  if (p->g != 0.0 && p->energy_model == LBM_E_TOTAL) {
+    why = "gravity needs energy_model = LBM_E_INTERNAL (the paper gives no work term for h)";
+    return LBM_ERR_PARAM;
+  }
+  if (!std::isfinite(p->g)) {
+    why = "g must be finite";
+    return LBM_ERR_PARAM;
+  }
+  if (p->correction != 0 && p->correction != 1) {
+    why = "correction must be 0 or 1";
+    return LBM_ERR_PARAM;
+  }
+  if (p->z_full != 0 && p->z_full != 1) {
+    why = "z_full must be 0 or 1";
+    return LBM_ERR_PARAM;
+  }
+  if (p->precision < LBM_P_FP64 || p->precision > LBM_P_FP32_BF16) {
+    why = "precision must be one of LBM_P_*";
+    return LBM_ERR_PARAM;
+  }
+  return LBM_OK;
+}
+
+int pitch_of(int nx) { return ((nx + 2 + 31) / 32) * 32; }
+
+size_t buffer_elems(const lbm_params* p) {
+  const size_t pitch = (size_t)pitch_of(p->nx);
+  size_t n = (size_t)R0 + (size_t)(p->ny + 2) * NPOP * pitch + 32;
+  return (n + 127) / 128 * 128;
+}
+
+size_t buffer_bytes(const lbm_params* p) { return buffer_elems(p) * elem_size(p->precision); }
+
+void fill_grid(const lbm_params* p, Grid& g) {
+  std::memset(&g, 0, sizeof(g));
+  g.nx = p->nx;
+  g.ny = p->ny;
+  g.pitch = pitch_of(p->nx);
+  g.rp = NPOP * g.pitch;
+  for (int s = 0; s < 4; ++s) {
+    g.bc[s] = p->bc[s];
+    g.uw[s][0] = p->u_wall[s][0];
+    g.uw[s][1] = p->u_wall[s][1];
+    g.thw[s] = p->T_wall[s] / p->T0;
+  }
+  g.energy_model = p->energy_model;
+  g.correction = p->correction;
+  g.z_full = p->z_full;
+  g.omega_f = 2.0 / (2.0 * p->tau_f + 1.0);
+  g.omega_h = 2.0 / (2.0 * p->tau_h + 1.0);
+  g.g = p->g;
+  g.b = p->b;
+  g.b6 = p->b / 6.0;
+  g.six_b = 6.0 / p->b;
+  // rest equilibria rho = 1, u = 0, theta = 1: f = w, h = w (b + 3 e^2 - 2)/6
+  // (total energy) or w b / 6 (internal energy)
+  double hs = 0.0;
+  for (int a = 0; a < 9; ++a) {
+    const double w = wgt<double>(a);
+    const double e2 = (double)(ex(a) * ex(a) + ey(a) * ey(a));
+    const double h = p->energy_model == LBM_E_TOTAL ? w * (p->b + 3.0 * e2 - 2.0) / 6.0
+                                                    : w * p->b / 6.0;
+    g.fref[a] = (float)w;
+    g.href[a] = (float)h;
+    hs += (double)g.href[a];
+  }
+  g.href_sum = hs;
+}
+
+}  // namespace lbm_host
+
+using namespace lbm_host;
+
+namespace {
+
+template <class F>
+int dispatch(int precision, F&& f) {
+  switch (precision) {
+    case LBM_P_FP64: return f((double*)nullptr);
+    case LBM_P_FP32: return f((float*)nullptr);
+    case LBM_P_FP32_FP16: return f((__half*)nullptr);
+    default: return f((__nv_bfloat16*)nullptr);
+  }
+}
+
+void* buf_ptr(lbm_handle* h, int which) {
+  return static_cast<unsigned char*>(h->base) + (size_t)which * h->buf_bytes;
+}
+
+int ensure_staging(lbm_handle* h, size_t bytes) {
+  if (h->staging_bytes >= bytes) return LBM_OK;
+  if (h->staging) cudaFree(h->staging);
+  h->staging = nullptr;
+  h->staging_bytes = 0;
+  cudaError_t e = cudaMalloc(&h->staging, bytes);
+  if (e != cudaSuccess) return fail(h, LBM_ERR_OOM, "device staging allocation failed");
+  h->staging_bytes = bytes;
+  return LBM_OK;
+}
+
+int grid_blocks(long long n) { return (int)std::max(1LL, std::min(4096LL, (n + 255) / 256)); }
+
+int create_impl(const lbm_params* p, void* stream, void* ext, int64_t ext_bytes, lbm_handle** out) {
+  if (!out) return fail(nullptr, LBM_ERR_PARAM, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  int rc = validate(p, why);
+  if (rc != LBM_OK) return fail(nullptr, rc, why);
+  lbm_handle* h = new lbm_handle();
+  h->p = *p;
+  h->stream = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(nullptr, LBM_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  }
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  h->buf_bytes = buffer_bytes(p);
+  const size_t need = 2 * h->buf_bytes;
+  if (ext) {
+    if ((int64_t)need > ext_bytes || (reinterpret_cast<uintptr_t>(ext) & 255u)) {
+      delete h;
+      return fail(nullptr, LBM_ERR_PARAM,
+                  "device_buffer too small or not 256-byte aligned (need lbm_state_bytes)");
+    }
+    h->base = ext;
+    h->owns = false;
+  } else {
+    e = cudaMalloc(&h->base, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return fail(nullptr, LBM_ERR_OOM, "cudaMalloc of the state failed");
+    }
+    h->owns = true;
+  }
+  e = cudaMalloc(&h->partial, sizeof(double) * (RED_BLOCKS * 4 + 4));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (h->owns) cudaFree(h->base);
+    delete h;
+    return fail(nullptr, LBM_ERR_OOM, "cudaMalloc of the reduction scratch failed");
+  }
+  h->out4 = h->partial + RED_BLOCKS * 4;
+  // ghost slots that no rule writes are never read; zero everything once so
+  // the buffers hold defined values
+  e = cudaMemsetAsync(h->base, 0, need, h->stream);
+  if (e != cudaSuccess) {
+    lbm_destroy(h);
+    return fail(nullptr, LBM_ERR_CUDA, std::string("memset: ") + cudaGetErrorString(e));
+  }
+  fill_grid(p, h->grid);
+  *out = h;
+  return LBM_OK;
+}
+
+// Rows per block so that the step launches about one wave of blocks.
+int auto_rows(const lbm_handle* h, int threads) {
+  const int W = threads - 2;
+  const int bx = (h->p.nx + W - 1) / W;
+  int occ = 0;
+  const size_t smem = 3 * (size_t)threads * (h->p.precision == LBM_P_FP64 ? 8 : 4);
+  dispatch(h->p.precision, [&](auto* tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel<S>, threads, smem);
+    return 0;
+  });
+  if (occ < 1) occ = 1;
+  const long long slots = (long long)occ * std::max(1, h->num_sms);
+  long long by = std::max(1LL, slots / bx);
+  int rows = (int)((h->p.ny + by - 1) / by);
+  rows = std::max(rows, 8);
+  return std::min(rows, h->p.ny);
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t lbm_state_bytes(const lbm_params* p) {
+  std::string why;
+  int rc = validate(p, why);
+  if (rc != LBM_OK) return rc;
+  return (int64_t)(2 * buffer_bytes(p));
+}
+
+int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out) {
+  return create_impl(p, cuda_stream, nullptr, 0, out);
+}
+
+int lbm_create_in(const lbm_params* p, void* cuda_stream, void* device_buffer, int64_t bytes,
+                  lbm_handle** out) {
+  if (!device_buffer) return fail(nullptr, LBM_ERR_PARAM, "device_buffer is NULL");
+  return create_impl(p, cuda_stream, device_buffer, bytes, out);
+}
+
+int lbm_init_device(lbm_handle* h, const double* rho, const double* ux, const double* uy,
+                    const double* T) {
+  if (!h) return LBM_ERR_PARAM;
+  if (!rho || !ux || !uy || !T) return fail(h, LBM_ERR_PARAM, "NULL field pointer");
+  const long long n = (long long)h->p.nx * h->p.ny;
+  h->cur = 0;
+  Grid g = h->grid;
+  void* dst = buf_ptr(h, 0);
+  const double invT0 = 1.0 / h->p.T0;
+  dispatch(h->p.precision, [&](auto* tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    init_kernel<S><<<grid_blocks(n), 256, 0, h->stream>>>(g, static_cast<S*>(dst), rho, ux, uy,
+                                                           T, invT0);
+    return 0;
+  });
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "init kernel launch");
+  h->steps = 0;
+  h->ready = true;
+  return LBM_OK;
+}
+
+int lbm_init(lbm_handle* h, const double* rho, const double* ux, const double* uy,
+             const double* T) {
+  if (!h) return LBM_ERR_PARAM;
+  if (!rho || !ux || !uy || !T) return fail(h, LBM_ERR_PARAM, "NULL field pointer");
+  const size_t n = (size_t)h->p.nx * h->p.ny;
+  int rc = ensure_staging(h, 4 * n * sizeof(double));
+  if (rc) return rc;
+  const double* src[4] = {rho, ux, uy, T};
+  for (int k = 0; k < 4; ++k) {
+    cudaError_t e = cudaMemcpyAsync(h->staging + k * n, src[k], n * sizeof(double),
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy");
+  }
+  rc = lbm_init_device(h, h->staging, h->staging + n, h->staging + 2 * n, h->staging + 3 * n);
+  if (rc) return rc;
+  return lbm_sync(h);
+}
+
+int lbm_step(lbm_handle* h, int64_t n) {
+  if (!h) return LBM_ERR_PARAM;
+  if (n < 0) return fail(h, LBM_ERR_PARAM, "n must be >= 0");
+  if (!h->ready) return fail(h, LBM_ERR_STATE, "lbm_step before lbm_init");
+  const int threads = h->threads;
+  const int rows = h->rows > 0 ? h->rows : auto_rows(h, threads);
+  const int W = threads - 2;
+  dim3 grid((h->p.nx + W - 1) / W, (h->p.ny + rows - 1) / rows);
+  const size_t smem = 3 * (size_t)threads * (h->p.precision == LBM_P_FP64 ? 8 : 4);
+  for (int64_t s = 0; s < n; ++s) {
+    Grid g = h->grid;
+    g.src = buf_ptr(h, h->cur);
+    g.dst = buf_ptr(h, 1 - h->cur);
+    dispatch(h->p.precision, [&](auto* tag) {
+      using S = std::remove_pointer_t<decltype(tag)>;
+      step_kernel<S><<<grid, threads, smem, h->stream>>>(g, rows);
+      return 0;
+    });
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
+    h->cur = 1 - h->cur;
+    ++h->steps;
+  }
+  return LBM_OK;
+}
+
+static int export_impl(lbm_handle* h, double* rho, double* ux, double* uy, double* T,
+                       double* pops) {
+  const long long n = (long long)h->p.nx * h->p.ny;
+  Grid g = h->grid;
+  const void* src = buf_ptr(h, h->cur);
+  const double T0 = h->p.T0;
+  dispatch(h->p.precision, [&](auto* tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    export_kernel<S><<<grid_blocks(n), 256, 0, h->stream>>>(g, static_cast<const S*>(src), rho,
+                                                             ux, uy, T, T0, pops);
+    return 0;
+  });
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "export kernel launch");
+  return LBM_OK;
+}
+
+int lbm_moments_device(lbm_handle* h, double* rho, double* ux, double* uy, double* T) {
+  if (!h) return LBM_ERR_PARAM;
+  if (!h->ready) return fail(h, LBM_ERR_STATE, "lbm_moments before lbm_init");
+  if (!rho || !ux || !uy || !T) return fail(h, LBM_ERR_PARAM, "NULL output pointer");
+  return export_impl(h, rho, ux, uy, T, nullptr);
+}
+
+int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy, double* T) {
+  if (!h) return LBM_ERR_PARAM;
+  if (!h->ready) return fail(h, LBM_ERR_STATE, "lbm_moments before lbm_init");
+  if (!rho || !ux || !uy || !T) return fail(h, LBM_ERR_PARAM, "NULL output pointer");
+  const size_t n = (size_t)h->p.nx * h->p.ny;
+  int rc = ensure_staging(h, 4 * n * sizeof(double));
+  if (rc) return rc;
+  rc = export_impl(h, h->staging, h->staging + n, h->staging + 2 * n, h->staging + 3 * n, nullptr);
+  if (rc) return rc;
+  double* dst[4] = {rho, ux, uy, T};
+  for (int k = 0; k < 4; ++k) {
+    cudaError_t e = cudaMemcpyAsync(dst[k], h->staging + k * n, n * sizeof(double),
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "device-to-host copy");
+  }
+  rc = lbm_sync(h);
+  if (rc) return rc;
+  for (int k = 0; k < 4; ++k)
+    for (size_t i = 0; i < n; ++i)
+      if (!std::isfinite(dst[k][i])) return fail(h, LBM_ERR_NONFINITE, "non-finite moment");
+  return LBM_OK;
+}
+
+int lbm_conserved(lbm_handle* h, double out[4]) {
+  if (!h) return LBM_ERR_PARAM;
+  if (!h->ready) return fail(h, LBM_ERR_STATE, "lbm_conserved before lbm_init");
+  if (!out) return fail(h, LBM_ERR_PARAM, "out is NULL");
+  const long long n = (long long)h->p.nx * h->p.ny;
+  const int nb = (int)std::min<long long>(RED_BLOCKS, (n + RED_THREADS - 1) / RED_THREADS);
+  Grid g = h->grid;
+  const void* src = buf_ptr(h, h->cur);
+  dispatch(h->p.precision, [&](auto* tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    conserved_partial_kernel<S><<<nb, RED_THREADS, 0, h->stream>>>(
+        g, static_cast<const S*>(src), h->partial);
+    return 0;
+  });
+  conserved_final_kernel<<<1, RED_THREADS, 0, h->stream>>>(h->partial, nb, h->out4);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "reduction launch");
+  e = cudaMemcpyAsync(out, h->out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "device-to-host copy");
+  int rc = lbm_sync(h);
+  if (rc) return rc;
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(out[k])) return fail(h, LBM_ERR_NONFINITE, "non-finite sum");
+  return LBM_OK;
+}
+
+int lbm_get_state(lbm_handle* h, double* pops) {
+  if (!h) return LBM_ERR_PARAM;
+  if (!h->ready) return fail(h, LBM_ERR_STATE, "lbm_get_state before lbm_init");
+  if (!pops) return fail(h, LBM_ERR_PARAM, "pops is NULL");
+  const size_t n = (size_t)h->p.nx * h->p.ny;
+  int rc = ensure_staging(h, NPOP * n * sizeof(double));
+  if (rc) return rc;
+  rc = export_impl(h, nullptr, nullptr, nullptr, nullptr, h->staging);
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(pops, h->staging, NPOP * n * sizeof(double),
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "device-to-host copy");
+  return lbm_sync(h);
+}
+
+int lbm_set_state(lbm_handle* h, const double* pops) {
+  if (!h) return LBM_ERR_PARAM;
+  if (!pops) return fail(h, LBM_ERR_PARAM, "pops is NULL");
+  const long long n = (long long)h->p.nx * h->p.ny;
+  int rc = ensure_staging(h, NPOP * (size_t)n * sizeof(double));
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(h->staging, pops, NPOP * (size_t)n * sizeof(double),
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy");
+  h->cur = 0;
+  Grid g = h->grid;
+  void* dst = buf_ptr(h, 0);
+  const double* staged = h->staging;
+  dispatch(h->p.precision, [&](auto* tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    set_state_kernel<S><<<grid_blocks(n), 256, 0, h->stream>>>(g, static_cast<S*>(dst), staged);
+    return 0;
+  });
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "set-state launch");
+  h->steps = 0;
+  h->ready = true;
+  return lbm_sync(h);
+}
+
+int lbm_sync(lbm_handle* h) {
+  if (!h) return LBM_ERR_PARAM;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+  return LBM_OK;
+}
+
+int64_t lbm_steps_done(const lbm_handle* h) { return h ? h->steps : LBM_ERR_PARAM; }
+
+int lbm_set_launch(lbm_handle* h, int32_t threads, int32_t rows_per_block) {
+  if (!h) return LBM_ERR_PARAM;
+  if (threads < 64 || threads > 256 || threads % 32 != 0 || rows_per_block < 0)
+    return fail(h, LBM_ERR_PARAM, "threads must be a multiple of 32 in [64, 256], rows >= 0");
+  h->threads = threads;
+  h->rows = rows_per_block;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  if (h->owns && h->base) cudaFree(h->base);
+  if (h->partial) cudaFree(h->partial);
+  if (h->staging) cudaFree(h->staging);
+  delete h;
+}
+
+const char* lbm_last_error(const lbm_handle* h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+const char* lbm_status_string(int status) {
+  switch (status) {
+    case LBM_OK: return "LBM_OK";
+    case LBM_ERR_PARAM: return "LBM_ERR_PARAM";
+    case LBM_ERR_OOM: return "LBM_ERR_OOM";
+    case LBM_ERR_CUDA: return "LBM_ERR_CUDA";
+    case LBM_ERR_NONFINITE: return "LBM_ERR_NONFINITE";
+    case LBM_ERR_TIMEOUT: return "LBM_ERR_TIMEOUT";
+    case LBM_ERR_STATE: return "LBM_ERR_STATE";
+    default: return "LBM_ERR_UNKNOWN";
+  }
+}
+
+}  // extern "C"

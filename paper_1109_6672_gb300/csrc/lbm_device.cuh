@@ -1,0 +1,617 @@
+// Device side of the coupled DDF thermal lattice Boltzmann step (D2Q9), after
+// Li, Luo, He, Gao & Tao, arXiv:1109.6672, BGK scheme of Sec. III.C.1.
+//
+// State layout (one buffer; two buffers ping-pong):
+//   element (a, x, y), a = 0..17 (f_0..f_8, h_0..h_8), x in [-1, nx],
+//   y in [-1, ny], lives at  base + R0 + (y + 1) * 18 * pitch + a * pitch + x.
+//   Rows of the 18 populations of one lattice row are adjacent ("row
+//   interleaved SoA"); a warp reading 32 consecutive x of one population
+//   reads 32 contiguous elements.  pitch >= nx + 2 and is a multiple of 32, so
+//   x = -1 and x = nx fall in padding that no other element uses: that is the
+//   one-node ghost ring.
+//
+// Meaning of a buffer: it holds post-collision populations f*_a(s) at the
+// slot s from which node s + e_a pulls them, so the canonical pre-collision
+// state of node x is fbar_a(x) = buf_a(x - e_a) for every a (pull streaming,
+// left-hand side of Eqs. 34 and 36).  Interior slots are written by the
+// collision of the node itself; ghost slots are written at collision time by
+// boundary nodes (periodic copies, or the wall rules), so the pull needs no
+// boundary logic at all.
+//
+// The correction C_a (Eqs. 48-50) needs Q = rho u (1 - theta) of the four
+// axis neighbours at the same time level.  A block owns a strip of
+// blockDim.x - 2 columns and marches down its rows: each row's pulled
+// populations and moments are computed once (plus one halo column on each
+// side), Q_x is exchanged through shared memory, Q_y stays in the thread's
+// registers for the row above and below, and the row is collided one
+// iteration later, when the row above is known.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lbm {
+
+constexpr int NPOP = 18;
+constexpr int R0 = 32;  // elements before row -1 (keeps element (-1, -1) in range)
+
+enum { BC_PERIODIC = 0, BC_ISO = 1, BC_ADIA = 2 };
+enum { E_TOTAL = 0, E_INTERNAL = 1 };
+
+// D2Q9 velocities (Eq. 6 with c = 1) and weights (below Eq. 8).
+__host__ __device__ constexpr int ex(int a) {
+  return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int a) {
+  return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int a) {
+  return a == 0 ? 0 : (a <= 4 ? ((a + 1) % 4) + 1 : ((a - 3) % 4) + 5);
+}
+template <class C>
+__host__ __device__ constexpr C wgt(int a) {
+  return a == 0 ? C(4) / C(9) : (a <= 4 ? C(1) / C(9) : C(1) / C(36));
+}
+
+// Per-grid launch argument.  All physics in lattice units with R T0 = 1/3.
+struct Grid {
+  void* src;  // state at time t (pull layout)
+  void* dst;  // state at time t + 1
+  int nx, ny, pitch, rp;  // rp = 18 * pitch
+  int bc[4];              // x-, x+, y-, y+
+  int energy_model, correction, z_full;
+  double omega_f, omega_h;  // 2 / (2 tau + 1)
+  double g;                 // gravity, a = (0, -rho g)
+  double b;                 // degrees of freedom
+  double b6, six_b;         // b / 6 and 6 / b
+  double uw[4][2];          // wall velocities
+  double thw[4];            // wall theta = T_w / T0
+  float fref[9], href[9];   // rest equilibria (deviation storage)
+  double href_sum;          // sum of href in FP64
+};
+
+// ---- storage <-> compute ---------------------------------------------------
+
+template <class S>
+struct Io;
+template <>
+struct Io<double> {
+  using C = double;
+  static constexpr bool dev = false;
+  __device__ static double ld(const double* p) { return __ldg(p); }
+  __device__ static double to(double v) { return v; }
+  __device__ static double from(double v) { return v; }
+};
+template <>
+struct Io<float> {
+  using C = float;
+  static constexpr bool dev = false;
+  __device__ static float ld(const float* p) { return __ldg(p); }
+  __device__ static float to(float v) { return v; }
+  __device__ static float from(float v) { return v; }
+};
+template <>
+struct Io<__half> {
+  using C = float;
+  static constexpr bool dev = true;
+  __device__ static __half ld(const __half* p) { return __ldg(p); }
+  __device__ static float to(__half v) { return __half2float(v); }
+  __device__ static __half from(float v) { return __float2half_rn(v); }
+};
+template <>
+struct Io<__nv_bfloat16> {
+  using C = float;
+  static constexpr bool dev = true;
+  __device__ static __nv_bfloat16 ld(const __nv_bfloat16* p) { return __ldg(p); }
+  __device__ static float to(__nv_bfloat16 v) { return __bfloat162float(v); }
+  __device__ static __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
+};
+
+__device__ __forceinline__ long long slot(const Grid& g, int a, int x, int y) {
+  return (long long)R0 + (long long)(y + 1) * g.rp + (long long)a * g.pitch + x;
+}
+
+// Reference value of population a (0 unless the storage holds deviations).
+template <class S>
+__device__ __forceinline__ typename Io<S>::C pref(const Grid& g, int a) {
+  using C = typename Io<S>::C;
+  if constexpr (Io<S>::dev) return C(a < 9 ? g.fref[a] : g.href[a - 9]);
+  return C(0);
+}
+
+// Pull the 18 stored values of node (x, y): d[a] = buf_a(x - e_a).  For
+// deviation storage these are deviations; pref() adds the reference back.
+template <class S>
+__device__ __forceinline__ void pull(const Grid& g, const S* __restrict__ src, int x, int y,
+                                     typename Io<S>::C d[NPOP]) {
+  const S* p = src + slot(g, 0, x, y);
+#pragma unroll
+  for (int a = 0; a < NPOP; ++a) {
+    const int q = a % 9;
+    d[a] = Io<S>::to(Io<S>::ld(p + a * g.pitch - ey(q) * g.rp - ex(q)));
+  }
+}
+
+// Moments of the pulled state: Eq. 35 with the force shift (text under
+// Eq. 51), and Eq. 37 (total energy) or 2 sum h / (rho b R) (Eq. 38 form).
+// Deviation storage recovers rho and theta in FP64 from the FP32 sums of the
+// deviations and the FP64 sum of the references.
+template <class S>
+__device__ __forceinline__ void moments(const Grid& g, const typename Io<S>::C d[NPOP],
+                                        typename Io<S>::C& rho, typename Io<S>::C& ux,
+                                        typename Io<S>::C& uy, typename Io<S>::C& th) {
+  using C = typename Io<S>::C;
+  C sf = 0, sh = 0;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    sf += d[a];
+    sh += d[9 + a];
+  }
+  const C jx = (d[1] - d[3]) + (d[5] - d[7]) + (d[8] - d[6]);
+  const C jy = (d[2] - d[4]) + (d[5] - d[7]) + (d[6] - d[8]);
+  if constexpr (Io<S>::dev) {
+    const double rd = 1.0 + (double)sf;  // sum of the f references is 1
+    rho = (C)rd;
+    const C inv = C(1) / rho;
+    ux = jx * inv;
+    uy = (jy - C(0.5) * rho * (C)g.g) * inv;
+    double invd = (double)inv;
+    invd = invd * (2.0 - rd * invd);  // one Newton step to FP64 accuracy
+    const double e = (g.href_sum + (double)sh) * invd;
+    double thd;
+    if (g.energy_model == E_TOTAL)
+      thd = g.six_b * (e - 0.5 * ((double)ux * (double)ux + (double)uy * (double)uy));
+    else
+      thd = g.six_b * e;
+    th = (C)thd;
+  } else {
+    rho = sf;
+    ux = jx / rho;
+    uy = (jy - C(0.5) * rho * (C)g.g) / rho;
+    if (g.energy_model == E_TOTAL)
+      th = (C)g.six_b * (sh / rho - C(0.5) * (ux * ux + uy * uy));
+    else
+      th = (C)g.six_b * sh / rho;
+  }
+}
+
+// f^eq (Eq. 18a, R T0 = 1/3, D = 2, third-order velocity term dropped) and
+// h^eq (Eq. 18b or b R T f^eq / 2), evaluated per pair of opposite velocities:
+//   f^eq_a = rho w_a [1 + 3 eu + 9/2 eu^2 - 3/2 u^2 + (th-1)(3 e^2 - 2)/2
+//                     + 3/2 eu (th-1)(3 e^2 - 4)]
+//   h^eq_a = E f^eq_a + w_a p [3 eu + 9 eu^2 - 3 u^2 + th (3 e^2 - 2)/2],
+//   E = b th / 6 + u^2 / 2, p = rho th / 3.
+template <class C>
+__device__ __forceinline__ void equilibria(C rho, C ux, C uy, C th, C b6, bool total, C feq[9],
+                                           C heq[9]) {
+  const C usq = ux * ux + uy * uy;
+  const C tm1 = th - C(1);
+  const C A0 = C(1) - C(1.5) * usq;
+  const C E = b6 * th + C(0.5) * usq;
+  const C p = rho * th * (C(1) / C(3));
+  // rest population
+  feq[0] = rho * wgt<C>(0) * (A0 - tm1);
+  const C pb = C(-3) * usq - th;  // bracket of h^eq at e = 0: -3u^2 + th(-2)/2
+  heq[0] = total ? E * feq[0] + wgt<C>(0) * p * pb : b6 * th * feq[0];
+  // axis shell (e^2 = 1) and diagonal shell (e^2 = 2)
+  const C base1 = A0 + C(0.5) * tm1, lin1 = C(3) - C(1.5) * tm1;
+  const C base2 = A0 + C(2) * tm1, lin2 = C(3) * th;
+  const C hb1 = C(-3) * usq + C(0.5) * th, hb2 = C(-3) * usq + C(2) * th;
+  const C eus[4] = {ux, uy, ux + uy, uy - ux};  // e.u for a = 1, 2, 5, 6
+  const int ia[4] = {1, 2, 5, 6};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int a = ia[k], o = opp(a);
+    const C eu = eus[k];
+    const C w = wgt<C>(a);
+    const C even = (k < 2 ? base1 : base2) + C(4.5) * eu * eu;
+    const C odd = (k < 2 ? lin1 : lin2) * eu;
+    feq[a] = rho * w * (even + odd);
+    feq[o] = rho * w * (even - odd);
+    if (total) {
+      const C he = (k < 2 ? hb1 : hb2) + C(9) * eu * eu;
+      const C ho = C(3) * eu;
+      heq[a] = E * feq[a] + w * p * (he + ho);
+      heq[o] = E * feq[o] + w * p * (he - ho);
+    } else {
+      heq[a] = b6 * th * feq[a];
+      heq[o] = b6 * th * feq[o];
+    }
+  }
+}
+
+// Wall equilibria: f^eq at (rho, u_w, theta) (halfway bounce-back term) and
+// h^eq at the ghost (isothermal) or wall (adiabatic) state.
+template <class C>
+__device__ void wall_equilibria(const Grid& g, int side, C rho, C ux, C uy, C th, C fw[9],
+                                C hw[9]) {
+  const bool total = g.energy_model == E_TOTAL;
+  const C uwx = (C)g.uw[side][0], uwy = (C)g.uw[side][1];
+  C tmp[9];
+  equilibria<C>(rho, uwx, uwy, th, (C)g.b6, total, fw, tmp);
+  if (g.bc[side] == BC_ISO) {
+    const C thg = C(2) * (C)g.thw[side] - th;
+    const C rg = rho * th / thg;
+    equilibria<C>(rg, C(2) * uwx - ux, C(2) * uwy - uy, thg, (C)g.b6, total, tmp, hw);
+  } else {
+    for (int a = 0; a < 9; ++a) hw[a] = tmp[a];
+  }
+}
+
+template <class S>
+__device__ __forceinline__ void put(const Grid& g, S* dst, int a, int x, int y,
+                                    typename Io<S>::C v) {
+  dst[slot(g, a, x, y)] = Io<S>::from(v - pref<S>(g, a));
+}
+
+// Ghost-slot writes of a boundary node (x, y): periodic copies and the wall
+// rules.  v[0..8] = f*, v[9..17] = h*, v[18..26] = h^eq of the node.
+template <class S>
+__device__ __noinline__ void boundary_writes(const Grid& g, S* __restrict__ dst, int x, int y,
+                                             const typename Io<S>::C* v,
+                                             typename Io<S>::C rho, typename Io<S>::C ux,
+                                             typename Io<S>::C uy, typename Io<S>::C th) {
+  using C = typename Io<S>::C;
+  C fw[9], hw[9];
+  int have = -1;
+  for (int a = 1; a < 9; ++a) {
+    const int dx = x + ex(a), dy = y + ey(a);
+    const int ox = dx < 0 ? 0 : (dx >= g.nx ? 1 : -1);
+    const int oy = dy < 0 ? 2 : (dy >= g.ny ? 3 : -1);
+    if (ox < 0 && oy < 0) continue;
+    int side = -1;
+    if (ox >= 0 && g.bc[ox] != BC_PERIODIC)
+      side = ox;
+    else if (oy >= 0 && g.bc[oy] != BC_PERIODIC)
+      side = oy;
+    if (side < 0) {
+      // periodic: the node at wrap(d) pulls population a from wrap(d) - e_a
+      const int wx = (dx + g.nx) % g.nx, wy = (dy + g.ny) % g.ny;
+      put<S>(g, dst, a, wx - ex(a), wy - ey(a), v[a]);
+      put<S>(g, dst, 9 + a, wx - ex(a), wy - ey(a), v[9 + a]);
+      continue;
+    }
+    if (have != side) {
+      wall_equilibria<C>(g, side, rho, ux, uy, th, fw, hw);
+      have = side;
+    }
+    const int b = opp(a);  // reflected direction; node (x, y) pulls it from d
+    put<S>(g, dst, b, dx, dy, v[a] + (fw[b] - fw[a]));
+    C hin;
+    if (g.bc[side] == BC_ISO)
+      hin = hw[b] + (v[9 + b] - v[18 + b]);
+    else
+      hin = v[9 + a] + (hw[b] - hw[a]);
+    put<S>(g, dst, 9 + b, dx, dy, hin);
+  }
+}
+
+// Collision of one node (Eq. 34 with +(1 - w_f/2) C, Eq. 36 or Eq. 38) with
+// the correction C_a (Eq. 49) plus the Guo force F_a, then the stores.
+template <class S>
+__device__ __forceinline__ void collide_store(const Grid& g, S* __restrict__ dst, int x, int y,
+                                              const typename Io<S>::C d[NPOP],
+                                              typename Io<S>::C rho, typename Io<S>::C ux,
+                                              typename Io<S>::C uy, typename Io<S>::C th,
+                                              typename Io<S>::C dqx, typename Io<S>::C dqy) {
+  using C = typename Io<S>::C;
+  const bool total = g.energy_model == E_TOTAL;
+  const C wf = (C)g.omega_f, wh = (C)g.omega_h;
+  C feq[9], heq[9];
+  equilibria<C>(rho, ux, uy, th, (C)g.b6, total, feq, heq);
+
+  // C'_a = C_a + F_a
+  C cc[9];
+  {
+    const C phx = C(3) * (dqx + dqy), phy = dqx - dqy;
+    const C on = g.correction ? C(1) : C(0);
+    const C c0 = on * (-phx / C(9));
+    const C c13 = on * (-phx / C(36) + phy / C(4));
+    const C c24 = on * (-phx / C(36) - phy / C(4));
+    const C cd = on * (phx / C(18));
+    cc[0] = c0;
+    cc[1] = c13;
+    cc[3] = c13;
+    cc[2] = c24;
+    cc[4] = c24;
+    cc[5] = cd;
+    cc[6] = cd;
+    cc[7] = cd;
+    cc[8] = cd;
+    // F_a = w_a [3 e.a + 9 (e.u)(e.a) - 3 u.a], a = (0, ay)
+    const C ay = -rho * (C)g.g;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const C ea = C(ey(a)) * ay;
+      const C eu = C(ex(a)) * ux + C(ey(a)) * uy;
+      cc[a] += wgt<C>(a) * (C(3) * ea + C(9) * eu * ea - C(3) * uy * ay);
+    }
+  }
+
+  const C usq = ux * ux + uy * uy;
+  const C kc = C(1) - C(0.5) * wf;
+  const C kz = wh - wf;
+  C v[27];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const C fa = pref<S>(g, a) + d[a];
+    const C ha = pref<S>(g, 9 + a) + d[9 + a];
+    const C fneq = fa - feq[a];
+    v[a] = fa - wf * fneq + kc * cc[a];
+    C hs = ha - wh * (ha - heq[a]);
+    if (total) {
+      const C eu = C(ex(a)) * ux + C(ey(a)) * uy;
+      const C Z = g.z_full ? eu - C(0.5) * usq : eu;
+      hs += kz * Z * (fneq + C(0.5) * cc[a]);
+    }
+    v[9 + a] = hs;
+    v[18 + a] = heq[a];
+  }
+  S* p = dst + slot(g, 0, x, y);
+#pragma unroll
+  for (int a = 0; a < NPOP; ++a) p[a * g.pitch] = Io<S>::from(v[a] - pref<S>(g, a));
+  if (x == 0 || y == 0 || x == g.nx - 1 || y == g.ny - 1) {
+    C tmp[27];
+#pragma unroll
+    for (int a = 0; a < 27; ++a) tmp[a] = v[a];
+    boundary_writes<S>(g, dst, x, y, tmp, rho, ux, uy, th);
+  }
+}
+
+// Q of the mirror ghost across a wall side: 2 rho u_w (1 - theta_w) - Q.
+template <class C>
+__device__ __forceinline__ C ghost_q(const Grid& g, int side, int comp, C rho, C th, C q) {
+  const C thw = g.bc[side] == BC_ISO ? (C)g.thw[side] : th;
+  return C(2) * rho * (C)g.uw[side][comp] * (C(1) - thw) - q;
+}
+
+// One time step.  Block = strip of blockDim.x - 2 output columns (one halo
+// column each side), rows [blockIdx.y * rows, +rows).  Dynamic shared memory:
+// 3 * blockDim.x compute-precision words.
+template <class S>
+__global__ void __launch_bounds__(256) step_kernel(const Grid g, int rows) {
+  using C = typename Io<S>::C;
+  extern __shared__ unsigned char smem_raw[];
+  C* qxs = reinterpret_cast<C*>(smem_raw);
+  const int NT = blockDim.x, W = NT - 2, t = threadIdx.x;
+  const int nx = g.nx, ny = g.ny;
+  const int c = blockIdx.x * W - 1 + t;
+  const int y0 = blockIdx.y * rows;
+  if (y0 >= ny) return;  // whole block
+  const int y1 = min(y0 + rows, ny);
+  const S* __restrict__ src = static_cast<const S*>(g.src);
+  S* __restrict__ dst = static_cast<S*>(g.dst);
+
+  bool colv;
+  int ncol;
+  if (c >= 0 && c < nx) {
+    colv = true;
+    ncol = c;
+  } else if (c == -1) {
+    colv = g.bc[0] == BC_PERIODIC;
+    ncol = nx - 1;
+  } else if (c == nx) {
+    colv = g.bc[1] == BC_PERIODIC;
+    ncol = 0;
+  } else {
+    colv = false;
+    ncol = 0;
+  }
+  const bool outc = t >= 1 && t <= W && c < nx;
+  const bool wall_l = g.bc[0] != BC_PERIODIC, wall_r = g.bc[1] != BC_PERIODIC;
+  const bool wall_b = g.bc[2] != BC_PERIODIC, wall_t = g.bc[3] != BC_PERIODIC;
+
+  C pd[NPOP];
+  C prho = 1, pux = 0, puy = 0, pth = 1, pqx = 0, pqy = 0, qymm = 0;
+#pragma unroll
+  for (int a = 0; a < NPOP; ++a) pd[a] = 0;
+
+  int sl = 0;  // slot of row r in the 3-row ring
+  for (int r = y0 - 1; r <= y1; ++r) {
+    bool rowv;
+    int nrow;
+    if (r >= 0 && r < ny) {
+      rowv = true;
+      nrow = r;
+    } else if (r < 0) {
+      rowv = !wall_b;
+      nrow = ny - 1;
+    } else {
+      rowv = !wall_t;
+      nrow = 0;
+    }
+    C cd[NPOP];
+    C crho = 1, cux = 0, cuy = 0, cth = 1, cqx = 0, cqy = 0;
+    if (colv && rowv) {
+      pull<S>(g, src, ncol, nrow, cd);
+      moments<S>(g, cd, crho, cux, cuy, cth);
+      cqx = crho * cux * (C(1) - cth);
+      cqy = crho * cuy * (C(1) - cth);
+    } else {
+#pragma unroll
+      for (int a = 0; a < NPOP; ++a) cd[a] = 0;
+    }
+    qxs[sl * NT + t] = cqx;
+    __syncthreads();
+    const int ro = r - 1;
+    if (ro >= y0 && outc) {
+      const int ps = sl == 0 ? 2 : sl - 1;
+      const C qxl = (c > 0 || !wall_l) ? qxs[ps * NT + t - 1] : ghost_q<C>(g, 0, 0, prho, pth, pqx);
+      const C qxr =
+          (c < nx - 1 || !wall_r) ? qxs[ps * NT + t + 1] : ghost_q<C>(g, 1, 0, prho, pth, pqx);
+      const C qyu = (ro < ny - 1 || !wall_t) ? cqy : ghost_q<C>(g, 3, 1, prho, pth, pqy);
+      const C qyd = (ro > 0 || !wall_b) ? qymm : ghost_q<C>(g, 2, 1, prho, pth, pqy);
+      collide_store<S>(g, dst, c, ro, pd, prho, pux, puy, pth, C(0.5) * (qxr - qxl),
+                       C(0.5) * (qyu - qyd));
+    }
+#pragma unroll
+    for (int a = 0; a < NPOP; ++a) pd[a] = cd[a];
+    qymm = pqy;
+    prho = crho;
+    pux = cux;
+    puy = cuy;
+    pth = cth;
+    pqx = cqx;
+    pqy = cqy;
+    sl = sl == 2 ? 0 : sl + 1;
+  }
+}
+
+// ---- initialisation, state export, moments, reductions ---------------------
+
+// Writes population values p[18] (full values, FP64) of node (x, y) into the
+// slots the next pull reads: buf_a(x - e_a).
+template <class S>
+__device__ __forceinline__ void scatter_node(const Grid& g, S* __restrict__ buf, int x, int y,
+                                             const double p[NPOP]) {
+  for (int a = 0; a < NPOP; ++a) {
+    const int q = a % 9;
+    const double ref = Io<S>::dev ? (double)(a < 9 ? g.fref[a] : g.href[a - 9]) : 0.0;
+    buf[slot(g, a, x - ex(q), y - ey(q))] =
+        Io<S>::from((typename Io<S>::C)(Io<S>::dev ? (p[a] - ref) : p[a]));
+  }
+}
+
+// FP64 equilibrium populations of (rho, u, T/T0) (initial state).
+__device__ __forceinline__ void init_pops(const Grid& g, double rho, double ux, double uy,
+                                          double th, double p[NPOP]) {
+  double feq[9], heq[9];
+  equilibria<double>(rho, ux, uy, th, g.b6, g.energy_model == E_TOTAL, feq, heq);
+  for (int a = 0; a < 9; ++a) {
+    p[a] = feq[a];
+    p[9 + a] = heq[a];
+  }
+}
+
+template <class S>
+__global__ void init_kernel(const Grid g, S* buf, const double* __restrict__ rho,
+                            const double* __restrict__ ux, const double* __restrict__ uy,
+                            const double* __restrict__ T, double invT0) {
+  const long long n = (long long)g.nx * g.ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx), y = (int)(i / g.nx);
+    double p[NPOP];
+    init_pops(g, rho[i], ux[i], uy[i], T[i] * invT0, p);
+    scatter_node<S>(g, buf, x, y, p);
+  }
+}
+
+template <class S>
+__global__ void set_state_kernel(const Grid g, S* buf, const double* __restrict__ pops) {
+  const long long n = (long long)g.nx * g.ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx), y = (int)(i / g.nx);
+    double p[NPOP];
+    for (int a = 0; a < NPOP; ++a) p[a] = pops[(long long)a * n + i];
+    scatter_node<S>(g, buf, x, y, p);
+  }
+}
+
+// FP64 pull of node (x, y) from buffer buf.
+template <class S>
+__device__ __forceinline__ void pull_fp64(const Grid& g, const S* __restrict__ buf, int x, int y,
+                                          double p[NPOP]) {
+  const S* q = buf + slot(g, 0, x, y);
+  for (int a = 0; a < NPOP; ++a) {
+    const int k = a % 9;
+    const double ref = Io<S>::dev ? (double)(a < 9 ? g.fref[a] : g.href[a - 9]) : 0.0;
+    p[a] = ref + (double)Io<S>::to(q[a * g.pitch - ey(k) * g.rp - ex(k)]);
+  }
+}
+
+__device__ __forceinline__ void moments_fp64(const Grid& g, const double p[NPOP], double& rho,
+                                             double& ux, double& uy, double& th, double& sh) {
+  double r = 0, jx = 0, jy = 0;
+  sh = 0;
+  for (int a = 0; a < 9; ++a) {
+    r += p[a];
+    jx += ex(a) * p[a];
+    jy += ey(a) * p[a];
+    sh += p[9 + a];
+  }
+  rho = r;
+  ux = jx / r;
+  uy = (jy - 0.5 * r * g.g) / r;
+  if (g.energy_model == E_TOTAL)
+    th = g.six_b * (sh / r - 0.5 * (ux * ux + uy * uy));
+  else
+    th = g.six_b * sh / r;
+}
+
+// rho, u, T (FP64) and optionally the canonical populations [18][ny][nx].
+template <class S>
+__global__ void export_kernel(const Grid g, const S* __restrict__ buf, double* rho, double* ux,
+                              double* uy, double* T, double T0, double* pops) {
+  const long long n = (long long)g.nx * g.ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx), y = (int)(i / g.nx);
+    double p[NPOP];
+    pull_fp64<S>(g, buf, x, y, p);
+    if (pops) {
+      for (int a = 0; a < NPOP; ++a) pops[(long long)a * n + i] = p[a];
+    }
+    if (rho) {
+      double r, vx, vy, th, sh;
+      moments_fp64(g, p, r, vx, vy, th, sh);
+      rho[i] = r;
+      ux[i] = vx;
+      uy[i] = vy;
+      T[i] = th * T0;
+    }
+  }
+}
+
+// Sums of rho, rho u_x, rho u_y, hbar: per-block partials in a fixed order.
+constexpr int RED_THREADS = 256;
+template <class S>
+__global__ void __launch_bounds__(RED_THREADS) conserved_partial_kernel(const Grid g,
+                                                                        const S* __restrict__ buf,
+                                                                        double* partial) {
+  __shared__ double sm[4][RED_THREADS];
+  const long long n = (long long)g.nx * g.ny;
+  double acc[4] = {0, 0, 0, 0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx), y = (int)(i / g.nx);
+    double p[NPOP];
+    pull_fp64<S>(g, buf, x, y, p);
+    double r, vx, vy, th, sh;
+    moments_fp64(g, p, r, vx, vy, th, sh);
+    acc[0] += r;
+    acc[1] += r * vx;
+    acc[2] += r * vy;
+    acc[3] += sh;
+  }
+  for (int k = 0; k < 4; ++k) sm[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int k = 0; k < 4; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; ++k) partial[4 * blockIdx.x + k] = sm[k][0];
+}
+
+// Final fixed-order sum of nb partial quadruples into out[4].
+__global__ void conserved_final_kernel(const double* __restrict__ partial, int nb, double* out) {
+  __shared__ double sm[4][RED_THREADS];
+  double acc[4] = {0, 0, 0, 0};
+  for (int i = threadIdx.x; i < nb; i += blockDim.x)
+    for (int k = 0; k < 4; ++k) acc[k] += partial[4 * i + k];
+  for (int k = 0; k < 4; ++k) sm[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int k = 0; k < 4; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; ++k) out[k] = sm[k][0];
+}
+
+}  // namespace lbm

@@ -1,0 +1,271 @@
+"""ctypes binding of the C ABI in ``include/lbm.h`` (same names, argument
+marshalling only: every step of the method runs in the CUDA library).
+
+Loading fails loudly with ``RuntimeError`` when ``liblbm.so`` has not been
+built; there is no CPU fallback.  Host arrays are numpy float64 [ny, nx];
+device arrays are passed as integer addresses (e.g. ``tensor.data_ptr()``).
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+PKG = Path(__file__).resolve().parent
+LIB_PATH = PKG / "liblbm.so"
+
+LBM_OK, LBM_ERR_PARAM, LBM_ERR_OOM, LBM_ERR_CUDA = 0, -1, -2, -3
+LBM_ERR_NONFINITE, LBM_ERR_TIMEOUT, LBM_ERR_STATE = -4, -5, -6
+LBM_BC_PERIODIC, LBM_BC_WALL_ISOTHERMAL, LBM_BC_WALL_ADIABATIC = 0, 1, 2
+LBM_E_TOTAL, LBM_E_INTERNAL = 0, 1
+LBM_P_FP64, LBM_P_FP32, LBM_P_FP32_FP16, LBM_P_FP32_BF16 = 0, 1, 2, 3
+PRECISION_NAMES = {LBM_P_FP64: "f64", LBM_P_FP32: "f32", LBM_P_FP32_FP16: "f32/f16dev",
+                   LBM_P_FP32_BF16: "f32/bf16dev"}
+BYTES_PER_NODE_UPDATE = {LBM_P_FP64: 288, LBM_P_FP32: 144, LBM_P_FP32_FP16: 72,
+                         LBM_P_FP32_BF16: 72}
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("bc", ctypes.c_int32 * 4),
+        ("tau_f", ctypes.c_double), ("tau_h", ctypes.c_double), ("Pr", ctypes.c_double),
+        ("R", ctypes.c_double), ("T0", ctypes.c_double), ("b", ctypes.c_double),
+        ("u_wall", (ctypes.c_double * 2) * 4), ("T_wall", ctypes.c_double * 4),
+        ("g", ctypes.c_double), ("energy_model", ctypes.c_int32),
+        ("correction", ctypes.c_int32), ("z_full", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+    ]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status)} ({status}): {msg}")
+        self.status = status
+
+
+_lib = None
+_DP = ctypes.POINTER(ctypes.c_double)
+_H = ctypes.c_void_p
+
+
+def load() -> ctypes.CDLL:
+    """Load liblbm.so (built by ``paper_1109_6672_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB_PATH.exists():
+        raise RuntimeError(f"CUDA library {LIB_PATH} is not built; run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(str(LIB_PATH))
+    P = ctypes.POINTER(lbm_params)
+    sig = {
+        "lbm_state_bytes": (ctypes.c_int64, [P]),
+        "lbm_create": (ctypes.c_int, [P, ctypes.c_void_p, ctypes.POINTER(_H)]),
+        "lbm_create_in": (ctypes.c_int, [P, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.POINTER(_H)]),
+        "lbm_init": (ctypes.c_int, [_H, _DP, _DP, _DP, _DP]),
+        "lbm_init_device": (ctypes.c_int, [_H] + [ctypes.c_void_p] * 4),
+        "lbm_step": (ctypes.c_int, [_H, ctypes.c_int64]),
+        "lbm_moments": (ctypes.c_int, [_H, _DP, _DP, _DP, _DP]),
+        "lbm_moments_device": (ctypes.c_int, [_H] + [ctypes.c_void_p] * 4),
+        "lbm_conserved": (ctypes.c_int, [_H, _DP]),
+        "lbm_get_state": (ctypes.c_int, [_H, _DP]),
+        "lbm_set_state": (ctypes.c_int, [_H, _DP]),
+        "lbm_sync": (ctypes.c_int, [_H]),
+        "lbm_steps_done": (ctypes.c_int64, [_H]),
+        "lbm_set_launch": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int32]),
+        "lbm_destroy": (None, [_H]),
+        "lbm_last_error": (ctypes.c_char_p, [_H]),
+        "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().lbm_status_string(int(status)).decode()
+
+
+def make_params(p: dict) -> lbm_params:
+    """lbm_params from a dict with the same field names (see ``inputs``)."""
+    o = lbm_params()
+    o.nx, o.ny = int(p["nx"]), int(p["ny"])
+    for i in range(4):
+        o.bc[i] = int(p["bc"][i])
+        o.T_wall[i] = float(p.get("T_wall", [1.0] * 4)[i])
+        uw = p.get("u_wall", [[0.0, 0.0]] * 4)[i]
+        o.u_wall[i][0], o.u_wall[i][1] = float(uw[0]), float(uw[1])
+    o.tau_f, o.tau_h = float(p["tau_f"]), float(p["tau_h"])
+    o.Pr = float(p.get("Pr", 0.0))
+    o.R, o.T0, o.b = float(p["R"]), float(p["T0"]), float(p["b"])
+    o.g = float(p.get("g", 0.0))
+    o.energy_model = int(p.get("energy_model", LBM_E_TOTAL))
+    o.correction = int(p.get("correction", 1))
+    o.z_full = int(p.get("z_full", 1))
+    o.precision = int(p.get("precision", LBM_P_FP64))
+    return o
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_DP)
+
+
+def _check(status: int, h=None):
+    if status != LBM_OK:
+        raise LbmError(status, load().lbm_last_error(h).decode())
+
+
+# ---- the C ABI, one Python function per entry point -------------------------
+
+def lbm_state_bytes(params: dict) -> int:
+    n = load().lbm_state_bytes(ctypes.byref(make_params(params)))
+    if n < 0:
+        _check(int(n))
+    return int(n)
+
+
+def lbm_create(params: dict, stream: int = 0):
+    h = _H()
+    _check(load().lbm_create(ctypes.byref(make_params(params)), ctypes.c_void_p(stream or None),
+                             ctypes.byref(h)))
+    return h
+
+
+def lbm_create_in(params: dict, device_buffer: int, nbytes: int, stream: int = 0):
+    h = _H()
+    _check(load().lbm_create_in(ctypes.byref(make_params(params)), ctypes.c_void_p(stream or None),
+                                ctypes.c_void_p(device_buffer), int(nbytes), ctypes.byref(h)))
+    return h
+
+
+def lbm_init(h, rho, ux, uy, T):
+    arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (rho, ux, uy, T)]
+    _check(load().lbm_init(h, *[_dp(a) for a in arrs]), h)
+
+
+def lbm_init_device(h, d_rho: int, d_ux: int, d_uy: int, d_T: int):
+    _check(load().lbm_init_device(h, d_rho, d_ux, d_uy, d_T), h)
+
+
+def lbm_step(h, n: int = 1):
+    _check(load().lbm_step(h, int(n)), h)
+
+
+def lbm_moments(h, shape):
+    out = [np.empty(shape, dtype=np.float64) for _ in range(4)]
+    _check(load().lbm_moments(h, *[_dp(a) for a in out]), h)
+    return tuple(out)
+
+
+def lbm_moments_device(h, d_rho: int, d_ux: int, d_uy: int, d_T: int):
+    _check(load().lbm_moments_device(h, d_rho, d_ux, d_uy, d_T), h)
+
+
+def lbm_conserved(h) -> np.ndarray:
+    out = np.zeros(4)
+    _check(load().lbm_conserved(h, _dp(out)), h)
+    return out
+
+
+def lbm_get_state(h, shape) -> np.ndarray:
+    out = np.empty((18,) + tuple(shape), dtype=np.float64)
+    _check(load().lbm_get_state(h, _dp(out)), h)
+    return out
+
+
+def lbm_set_state(h, pops: np.ndarray):
+    a = np.ascontiguousarray(pops, dtype=np.float64)
+    _check(load().lbm_set_state(h, _dp(a)), h)
+
+
+def lbm_sync(h):
+    _check(load().lbm_sync(h), h)
+
+
+def lbm_steps_done(h) -> int:
+    return int(load().lbm_steps_done(h))
+
+
+def lbm_set_launch(h, threads: int, rows_per_block: int = 0):
+    _check(load().lbm_set_launch(h, int(threads), int(rows_per_block)), h)
+
+
+def lbm_destroy(h):
+    if h:
+        load().lbm_destroy(h)
+
+
+def lbm_last_error(h=None) -> str:
+    return load().lbm_last_error(h).decode()
+
+
+# ---- convenience wrapper ------------------------------------------------------
+
+class Lbm:
+    """One grid on the GPU.  ``Lbm(params).init(rho, ux, uy, T).step(n)``."""
+
+    def __init__(self, params: dict, stream: int = 0, device_buffer: int | None = None,
+                 nbytes: int = 0):
+        self.p = dict(params)
+        self.shape = (int(params["ny"]), int(params["nx"]))
+        if device_buffer is None:
+            self.h = lbm_create(self.p, stream)
+        else:
+            self.h = lbm_create_in(self.p, device_buffer, nbytes, stream)
+
+    def init(self, rho, ux, uy, T):
+        b = [np.broadcast_to(np.asarray(v, dtype=np.float64), self.shape) for v in (rho, ux, uy, T)]
+        lbm_init(self.h, *b)
+        return self
+
+    def step(self, n: int = 1):
+        lbm_step(self.h, n)
+        return self
+
+    def set_launch(self, threads: int, rows: int = 0):
+        lbm_set_launch(self.h, threads, rows)
+        return self
+
+    def moments(self):
+        return lbm_moments(self.h, self.shape)
+
+    def conserved(self) -> np.ndarray:
+        return lbm_conserved(self.h)
+
+    def pops(self) -> np.ndarray:
+        return lbm_get_state(self.h, self.shape)
+
+    def set_pops(self, pops: np.ndarray):
+        lbm_set_state(self.h, pops)
+        return self
+
+    def sync(self):
+        lbm_sync(self.h)
+        return self
+
+    @property
+    def steps_done(self) -> int:
+        return lbm_steps_done(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,64 @@
+"""The C ABI library builds, loads and exports every entry point declared in
+include/*.h; host-only calls (sizes, validation, status strings) work without
+a GPU.  No kernel is launched here."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+from paper_1109_6672_gb300 import build, inputs
+from paper_1109_6672_gb300 import lbm
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+def declared_functions():
+    names = []
+    for hdr in sorted((ROOT / "include").glob("*.h")):
+        text = re.sub(r"/\*.*?\*/", "", hdr.read_text(), flags=re.S)
+        for m in re.finditer(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(lbm_\w+)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return ctypes.CDLL(str(lbm.LIB_PATH))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lbm_create", "lbm_init", "lbm_step", "lbm_moments", "lbm_destroy",
+                     "lbm_conserved", "lbm_last_error"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_params_struct_size_matches_header(lib):
+    # lbm_params: 2+4 int32, 6 doubles, 8+4 doubles, 1 double, 4 int32
+    assert ctypes.sizeof(lbm.lbm_params) == 4 * 6 + 8 * 6 + 8 * 12 + 8 + 4 * 4
+
+
+def test_state_bytes_and_validation_without_gpu(lib):
+    lbm.load()
+    p, _ = inputs.periodic_box(n=4096, precision=lbm.LBM_P_FP32)
+    n = lbm.lbm_state_bytes(p)
+    assert n >= 2 * 18 * 4096 * 4096 * 4
+    assert lbm.lbm_state_bytes(dict(p, precision=lbm.LBM_P_FP32_BF16)) * 2 <= n + 4096
+    for bad in (dict(p, tau_f=0.0), dict(p, R=1.0), dict(p, b=1.0), dict(p, nx=0),
+                dict(p, bc=[0, 1, 0, 0]), dict(p, g=1e-3), dict(p, Pr=2.0),
+                dict(p, precision=7), dict(p, bc=[1, 1, 0, 0], nx=2)):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_state_bytes(bad)
+        assert e.value.status == lbm.LBM_ERR_PARAM
+
+
+def test_status_strings(lib):
+    assert lbm.status_string(lbm.LBM_ERR_NONFINITE) == "LBM_ERR_NONFINITE"
+    assert lbm.status_string(0) == "LBM_OK"
