@@ -30,6 +30,27 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled f+h D2Q9 GLUPS and % HBM roofline; served p50/p99 latency"
 UNIT = "GLUPS"
 
+# DRAM bytes (read + write) of one step launch at 4096^2, from one ncu capture
+# at 2048^2 scaled by the node count (profiles/step_pr_*_2048_full.md), keyed
+# by the hash of the kernel sources they were measured on; a changed kernel
+# reports null until it is captured again.
+KERNEL_SOURCES = ("lbm_device.cuh", "lbm_step_tma.cuh", "lbm_step_pr.cuh")
+MEASURED_TRAFFIC = {
+    ("545fb967eef8454a", "f32"): 2368.777216e6,
+    ("545fb967eef8454a", "bf16"): 1145.946112e6,
+}
+
+
+def kernel_hash():
+    import hashlib
+
+    csrc = os.path.join(ROOT, "paper_1109_6672_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
 
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -42,7 +63,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -237,7 +258,7 @@ def run_ours(args, rank, world, local_rank):
             gv = lbm.Lbm(pp, stream=stream.cuda_stream)
             with torch.cuda.stream(stream):
                 lbm.lbm_init_device(gv.h, *[t.data_ptr() for t in dev_fields])
-            ksteps = max(3, args.steps // (8 if pv == lbm.LBM_P_FP64 else 1))
+            ksteps = max(3, args.steps // (16 if pv == lbm.LBM_P_FP64 else 2))
             gv.step(args.warmup)
             gv.sync()
             tv = time_steps(torch, lbm, gv, stream, ksteps)
@@ -259,6 +280,9 @@ def run_ours(args, rank, world, local_rank):
                "sample": f"{side}x{side} periodic box of the same workload, {args.ref_steps} steps "
                          f"({dt:.1f} s), FP64, OpenMP over rows"}
 
+    traffic = None
+    if n == 4096 and args.threads in (0, 1) and args.rows == 0:
+        traffic = MEASURED_TRAFFIC.get((kernel_hash(), args.precision))
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -274,8 +298,10 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "state 2x18 populations per node >> 129 MB L2; no flush",
                        "replicas": world},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "step_kernel", "algorithmic_bytes_per_launch": nodes * bpn},
+                         "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "step_pr_kernel", "algorithmic_bytes_per_launch": nodes * bpn,
+                         "traffic_note": "DRAM read+write bytes per launch from ncu at 2048^2, "
+                                         "scaled x4 (node count); null if the kernel changed"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(4 * nodes * 8 / e2e_steps),
@@ -293,7 +319,7 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f32", choices=["f64", "f32", "f16", "bf16"])
@@ -301,7 +327,7 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--rows", type=int, default=0)
     ap.add_argument("--ref-side", type=int, default=1024)
-    ap.add_argument("--ref-steps", type=int, default=60)
+    ap.add_argument("--ref-steps", type=int, default=800)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     args = ap.parse_args()

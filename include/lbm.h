@@ -155,10 +155,16 @@ int lbm_sync(lbm_handle* h);
 /* Time steps taken since the last lbm_init() / lbm_set_state(). */
 int64_t lbm_steps_done(const lbm_handle* h);
 
-/* Launch shape of the step kernel: threads per block (a multiple of 32 in
- * 64..256; each block owns threads - 2 columns, default 128) and rows per
- * block (>= 1; 0 = about one wave of blocks, the default). */
-int lbm_set_launch(lbm_handle* h, int32_t threads, int32_t rows_per_block);
+/* Step kernel and launch shape.  variant 0 or 1 (default): pulled-row
+ * staging by the tensor memory accelerator (TMA), 128 columns per block;
+ * 2: the same with 256 columns per block (two per thread); 64..256, a
+ * multiple of 32: the register-pull kernel, each block owning variant - 2
+ * columns.  rows_per_block >= 1, or 0 for the default (6 rows for FP32
+ * storage, 12 otherwise, for the TMA kernel; about one wave of blocks for the
+ * register-pull kernel).  rows_per_block (and the block width of the
+ * register-pull kernel) never changes a bit of the result; different variants
+ * agree to rounding (different FMA contraction). */
+int lbm_set_launch(lbm_handle* h, int32_t variant, int32_t rows_per_block);
 
 /* Frees the handle and the device memory it owns.  NULL-safe. */
 void lbm_destroy(lbm_handle* h);

@@ -1,6 +1,8 @@
 // Host side of the single-grid C ABI declared in include/lbm.h: parameter
 // validation, device state, launches of the kernels in lbm_device.cuh.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -12,6 +14,7 @@
 #include "lbm.h"
 #include "lbm_device.cuh"
 #include "lbm_host.h"
+#include "lbm_launch.h"
 
 using namespace lbm;
 
@@ -27,9 +30,11 @@ struct lbm_handle {
   int64_t steps = 0;
   bool ready = false;
   Grid grid{};
-  int threads = 128, rows = 0;
+  int variant = TMA_PR_1, rows = 0;  // 1, 2: pulled-row TMA kernel; 64..256: register pull
+  CUtensorMap maps[2][2];            // TMA descriptors [buffer][columns per thread - 1]
   double* partial = nullptr;  // reduction scratch: RED_BLOCKS x 4
   double* out4 = nullptr;     // reduction result
+  int* status = nullptr;      // device error word of the step kernels
   double* staging = nullptr;  // device staging for host transfers
   size_t staging_bytes = 0;
   std::string err;
@@ -148,11 +153,11 @@ int validate(const lbm_params* p, std::string& why) {
   return LBM_OK;
 }
 
-int pitch_of(int nx) { return ((nx + 2 + 31) / 32) * 32; }
+int pitch_of(int nx) { return ((nx + XOFF + 1 + 31) / 32) * 32; }
 
 size_t buffer_elems(const lbm_params* p) {
   const size_t pitch = (size_t)pitch_of(p->nx);
-  size_t n = (size_t)R0 + (size_t)(p->ny + 2) * NPOP * pitch + 32;
+  size_t n = (size_t)(p->ny + 2) * NPOP * pitch;
   return (n + 127) / 128 * 128;
 }
 
@@ -164,21 +169,34 @@ void fill_grid(const lbm_params* p, Grid& g) {
   g.ny = p->ny;
   g.pitch = pitch_of(p->nx);
   g.rp = NPOP * g.pitch;
+  Phys<double>& k = g.pd;
   for (int s = 0; s < 4; ++s) {
     g.bc[s] = p->bc[s];
-    g.uw[s][0] = p->u_wall[s][0];
-    g.uw[s][1] = p->u_wall[s][1];
-    g.thw[s] = p->T_wall[s] / p->T0;
+    k.uw[s][0] = p->u_wall[s][0];
+    k.uw[s][1] = p->u_wall[s][1];
+    k.thw[s] = p->T_wall[s] / p->T0;
   }
   g.energy_model = p->energy_model;
   g.correction = p->correction;
   g.z_full = p->z_full;
-  g.omega_f = 2.0 / (2.0 * p->tau_f + 1.0);
-  g.omega_h = 2.0 / (2.0 * p->tau_h + 1.0);
-  g.g = p->g;
-  g.b = p->b;
-  g.b6 = p->b / 6.0;
-  g.six_b = 6.0 / p->b;
+  g.has_force = p->g != 0.0;
+  k.omega_f = 2.0 / (2.0 * p->tau_f + 1.0);
+  k.omega_h = 2.0 / (2.0 * p->tau_h + 1.0);
+  k.g = p->g;
+  k.b6 = p->b / 6.0;
+  k.six_b = 6.0 / p->b;
+  Phys<float>& f = g.pf;
+  f.omega_f = (float)k.omega_f;
+  f.omega_h = (float)k.omega_h;
+  f.g = (float)k.g;
+  f.b6 = (float)k.b6;
+  f.six_b = (float)k.six_b;
+  for (int s = 0; s < 4; ++s) {
+    f.uw[s][0] = (float)k.uw[s][0];
+    f.uw[s][1] = (float)k.uw[s][1];
+    f.thw[s] = (float)k.thw[s];
+  }
+  g.status = nullptr;
   // rest equilibria rho = 1, u = 0, theta = 1: f = w, h = w (b + 3 e^2 - 2)/6
   // (total energy) or w b / 6 (internal energy)
   double hs = 0.0;
@@ -227,6 +245,48 @@ int ensure_staging(lbm_handle* h, size_t bytes) {
 
 int grid_blocks(long long n) { return (int)std::max(1LL, std::min(4096LL, (n + 255) / 256)); }
 
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+namespace lbm_host {
+
+// 3-D view of one state buffer for the TMA row loads: (x + 32, population,
+// y + 1) with a box of one lattice row, all 18 populations, box_cols columns.
+int make_tensor_map(CUtensorMap* map, void* buffer, const lbm_params& p, const Grid& g,
+                    int box_cols, int box_planes) {
+  auto fn = encode_fn();
+  if (!fn) return LBM_ERR_CUDA;
+  const size_t es = elem_size(p.precision);
+  CUtensorMapDataType dt = p.precision == LBM_P_FP64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                           : p.precision == LBM_P_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                           : p.precision == LBM_P_FP32_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                             : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)NPOP, (cuuint64_t)(g.ny + 2)};
+  cuuint64_t strides[2] = {(cuuint64_t)g.pitch * es, (cuuint64_t)g.rp * es};
+  cuuint32_t box[3] = {(cuuint32_t)box_cols, (cuuint32_t)box_planes, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, dt, 3, buffer, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? LBM_OK : LBM_ERR_CUDA;
+}
+
+}  // namespace lbm_host
+
+namespace {
+
 int create_impl(const lbm_params* p, void* stream, void* ext, int64_t ext_bytes, lbm_handle** out) {
   if (!out) return fail(nullptr, LBM_ERR_PARAM, "out is NULL");
   *out = nullptr;
@@ -261,7 +321,7 @@ int create_impl(const lbm_params* p, void* stream, void* ext, int64_t ext_bytes,
     }
     h->owns = true;
   }
-  e = cudaMalloc(&h->partial, sizeof(double) * (RED_BLOCKS * 4 + 4));
+  e = cudaMalloc(&h->partial, sizeof(double) * (RED_BLOCKS * 4 + 4) + 64);
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (h->owns) cudaFree(h->base);
@@ -269,6 +329,8 @@ int create_impl(const lbm_params* p, void* stream, void* ext, int64_t ext_bytes,
     return fail(nullptr, LBM_ERR_OOM, "cudaMalloc of the reduction scratch failed");
   }
   h->out4 = h->partial + RED_BLOCKS * 4;
+  h->status = reinterpret_cast<int*>(h->out4 + 4);
+  cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
   // ghost slots that no rule writes are never read; zero everything once so
   // the buffers hold defined values
   e = cudaMemsetAsync(h->base, 0, need, h->stream);
@@ -277,19 +339,36 @@ int create_impl(const lbm_params* p, void* stream, void* ext, int64_t ext_bytes,
     return fail(nullptr, LBM_ERR_CUDA, std::string("memset: ") + cudaGetErrorString(e));
   }
   fill_grid(p, h->grid);
+  h->grid.status = h->status;
+  for (int b = 0; b < 2; ++b) {
+    for (int k = 0; k < 2; ++k) {
+      rc = make_tensor_map(&h->maps[b][k], buf_ptr(h, b), h->p, h->grid, tma_box(k + 1), 6);
+      if (rc != LBM_OK) {
+        lbm_destroy(h);
+        return fail(nullptr, rc, "cuTensorMapEncodeTiled failed");
+      }
+    }
+  }
   *out = h;
   return LBM_OK;
 }
 
+// Columns a block of the selected kernel owns.
+int block_cols(int variant) { return variant >= 64 ? variant - 2 : tma_cols(variant); }
+
 // Rows per block so that the step launches about one wave of blocks.
-int auto_rows(const lbm_handle* h, int threads) {
-  const int W = threads - 2;
+int auto_rows(const lbm_handle* h, int variant) {
+  const int W = block_cols(variant);
   const int bx = (h->p.nx + W - 1) / W;
   int occ = 0;
-  const size_t smem = 3 * (size_t)threads * (h->p.precision == LBM_P_FP64 ? 8 : 4);
   dispatch(h->p.precision, [&](auto* tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel<S>, threads, smem);
+    if (variant >= 64) {
+      const size_t smem = 3 * (size_t)variant * sizeof(typename Io<S>::C);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel<S>, variant, smem);
+    } else {
+      occ = occupancy_step_tma<S>(h->grid, variant);
+    }
     return 0;
   });
   if (occ < 1) occ = 1;
@@ -365,21 +444,30 @@ int lbm_step(lbm_handle* h, int64_t n) {
   if (!h) return LBM_ERR_PARAM;
   if (n < 0) return fail(h, LBM_ERR_PARAM, "n must be >= 0");
   if (!h->ready) return fail(h, LBM_ERR_STATE, "lbm_step before lbm_init");
-  const int threads = h->threads;
-  const int rows = h->rows > 0 ? h->rows : auto_rows(h, threads);
-  const int W = threads - 2;
+  const int variant = h->variant;
+  const int rows = h->rows > 0 ? h->rows
+                   : variant >= 64 ? auto_rows(h, variant)
+                                   : std::min(h->p.ny, tma_default_rows(elem_size(h->p.precision)));
+  const int W = block_cols(variant);
+  const int npt = variant >= 64 ? 1 : tma_npt(variant);
   dim3 grid((h->p.nx + W - 1) / W, (h->p.ny + rows - 1) / rows);
-  const size_t smem = 3 * (size_t)threads * (h->p.precision == LBM_P_FP64 ? 8 : 4);
   for (int64_t s = 0; s < n; ++s) {
     Grid g = h->grid;
     g.src = buf_ptr(h, h->cur);
     g.dst = buf_ptr(h, 1 - h->cur);
+    const CUtensorMap& map = h->maps[h->cur][npt - 1];
+    cudaError_t e = cudaSuccess;
     dispatch(h->p.precision, [&](auto* tag) {
       using S = std::remove_pointer_t<decltype(tag)>;
-      step_kernel<S><<<grid, threads, smem, h->stream>>>(g, rows);
+      if (variant >= 64) {
+        const size_t smem = 3 * (size_t)variant * sizeof(typename Io<S>::C);
+        step_kernel<S><<<grid, variant, smem, h->stream>>>(g, rows);
+        e = cudaGetLastError();
+      } else {
+        e = launch_step_tma<S>(g, map, variant, rows, grid, h->stream);
+      }
       return 0;
     });
-    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
     h->cur = 1 - h->cur;
     ++h->steps;
@@ -448,7 +536,7 @@ int lbm_conserved(lbm_handle* h, double out[4]) {
         g, static_cast<const S*>(src), h->partial);
     return 0;
   });
-  conserved_final_kernel<<<1, RED_THREADS, 0, h->stream>>>(h->partial, nb, h->out4);
+  conserved_final_kernel<><<<1, RED_THREADS, 0, h->stream>>>(h->partial, nb, h->out4);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "reduction launch");
   e = cudaMemcpyAsync(out, h->out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -502,18 +590,27 @@ int lbm_set_state(lbm_handle* h, const double* pops) {
 
 int lbm_sync(lbm_handle* h) {
   if (!h) return LBM_ERR_PARAM;
-  cudaError_t e = cudaStreamSynchronize(h->stream);
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+  if (st != 0) {
+    cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+    cudaStreamSynchronize(h->stream);
+    return fail(h, LBM_ERR_TIMEOUT, "a step kernel gave up waiting for a staged row");
+  }
   return LBM_OK;
 }
 
 int64_t lbm_steps_done(const lbm_handle* h) { return h ? h->steps : LBM_ERR_PARAM; }
 
-int lbm_set_launch(lbm_handle* h, int32_t threads, int32_t rows_per_block) {
+int lbm_set_launch(lbm_handle* h, int32_t variant, int32_t rows_per_block) {
   if (!h) return LBM_ERR_PARAM;
-  if (threads < 64 || threads > 256 || threads % 32 != 0 || rows_per_block < 0)
-    return fail(h, LBM_ERR_PARAM, "threads must be a multiple of 32 in [64, 256], rows >= 0");
-  h->threads = threads;
+  if ((variant > 2 && (variant < 64 || variant > 256 || variant % 32 != 0)) || variant < 0 ||
+      rows_per_block < 0)
+    return fail(h, LBM_ERR_PARAM,
+                "variant must be 0, 1, 2 or a multiple of 32 in [64, 256]; rows >= 0");
+  h->variant = variant == 0 ? TMA_PR_1 : variant;
   h->rows = rows_per_block;
   return LBM_OK;
 }

@@ -3,12 +3,18 @@
 //
 // State layout (one buffer; two buffers ping-pong):
 //   element (a, x, y), a = 0..17 (f_0..f_8, h_0..h_8), x in [-1, nx],
-//   y in [-1, ny], lives at  base + R0 + (y + 1) * 18 * pitch + a * pitch + x.
+//   y in [-1, ny], lives at
+//       base + (y + 1) * 18 * pitch + plane(a) * pitch + x + 32.
 //   Rows of the 18 populations of one lattice row are adjacent ("row
 //   interleaved SoA"); a warp reading 32 consecutive x of one population
-//   reads 32 contiguous elements.  pitch >= nx + 2 and is a multiple of 32, so
-//   x = -1 and x = nx fall in padding that no other element uses: that is the
-//   one-node ghost ring.
+//   reads 32 contiguous elements, and x = 0 starts a 32-element boundary, so
+//   the stores of a block whose first column is a multiple of 32 are aligned.
+//   pitch >= nx + 33 and is a multiple of 32; x = -1 and x = nx fall in
+//   padding that no other element uses: that is the one-node ghost ring.
+//   plane(a) groups the populations by e_y: planes 0-5 hold e_y = +1
+//   (f2 f5 f6 h2 h5 h6), 6-11 e_y = 0 (f0 f1 f3 h0 h1 h3), 12-17 e_y = -1
+//   (f4 f7 f8 h4 h7 h8), so the values one lattice row pulls from the row
+//   below, the same row and the row above are three contiguous plane groups.
 //
 // Meaning of a buffer: it holds post-collision populations f*_a(s) at the
 // slot s from which node s + e_a pulls them, so the canonical pre-collision
@@ -34,7 +40,7 @@
 namespace lbm {
 
 constexpr int NPOP = 18;
-constexpr int R0 = 32;  // elements before row -1 (keeps element (-1, -1) in range)
+constexpr int XOFF = 32;  // element offset of x = 0 within a population row
 
 enum { BC_PERIODIC = 0, BC_ISO = 1, BC_ADIA = 2 };
 enum { E_TOTAL = 0, E_INTERNAL = 1 };
@@ -54,22 +60,49 @@ __host__ __device__ constexpr C wgt(int a) {
   return a == 0 ? C(4) / C(9) : (a <= 4 ? C(1) / C(9) : C(1) / C(36));
 }
 
-// Per-grid launch argument.  All physics in lattice units with R T0 = 1/3.
+// Storage plane of population a (0..17): group by e_y (+1, 0, -1), then
+// distribution (f, h), then velocity.
+__host__ __device__ constexpr int pgroup(int a) {
+  return ey(a % 9) > 0 ? 0 : (ey(a % 9) == 0 ? 1 : 2);
+}
+__host__ __device__ constexpr int pidx(int q) {
+  return (q == 2 || q == 0 || q == 4) ? 0 : ((q == 5 || q == 1 || q == 7) ? 1 : 2);
+}
+__host__ __device__ constexpr int plane(int a) {
+  return 6 * pgroup(a) + 3 * (a / 9) + pidx(a % 9);
+}
+
+// Physical constants in one arithmetic precision (lattice units, R T0 = 1/3).
+template <class C>
+struct Phys {
+  C omega_f, omega_h;  // 2 / (2 tau + 1)
+  C g;                 // gravity, a = (0, -rho g)
+  C b6, six_b;         // b / 6 and 6 / b
+  C uw[4][2];          // wall velocities
+  C thw[4];            // wall theta = T_w / T0
+};
+
+// Per-grid launch argument.
 struct Grid {
   void* src;  // state at time t (pull layout)
   void* dst;  // state at time t + 1
   int nx, ny, pitch, rp;  // rp = 18 * pitch
   int bc[4];              // x-, x+, y-, y+
-  int energy_model, correction, z_full;
-  double omega_f, omega_h;  // 2 / (2 tau + 1)
-  double g;                 // gravity, a = (0, -rho g)
-  double b;                 // degrees of freedom
-  double b6, six_b;         // b / 6 and 6 / b
-  double uw[4][2];          // wall velocities
-  double thw[4];            // wall theta = T_w / T0
-  float fref[9], href[9];   // rest equilibria (deviation storage)
-  double href_sum;          // sum of href in FP64
+  int energy_model, correction, z_full, has_force;
+  Phys<double> pd;
+  Phys<float> pf;
+  float fref[9], href[9];  // rest equilibria (deviation storage)
+  double href_sum;         // sum of href in FP64
+  int* status;             // device error word (bounded waits), may be NULL
 };
+
+template <class C>
+__host__ __device__ __forceinline__ const Phys<C>& phys(const Grid& g) {
+  if constexpr (sizeof(C) == 8)
+    return g.pd;
+  else
+    return g.pf;
+}
 
 // ---- storage <-> compute ---------------------------------------------------
 
@@ -109,7 +142,7 @@ struct Io<__nv_bfloat16> {
 };
 
 __device__ __forceinline__ long long slot(const Grid& g, int a, int x, int y) {
-  return (long long)R0 + (long long)(y + 1) * g.rp + (long long)a * g.pitch + x;
+  return (long long)(y + 1) * g.rp + (long long)plane(a) * g.pitch + (x + XOFF);
 }
 
 // Reference value of population a (0 unless the storage holds deviations).
@@ -129,7 +162,7 @@ __device__ __forceinline__ void pull(const Grid& g, const S* __restrict__ src, i
 #pragma unroll
   for (int a = 0; a < NPOP; ++a) {
     const int q = a % 9;
-    d[a] = Io<S>::to(Io<S>::ld(p + a * g.pitch - ey(q) * g.rp - ex(q)));
+    d[a] = Io<S>::to(Io<S>::ld(p + (plane(a) - plane(0)) * g.pitch - ey(q) * g.rp - ex(q)));
   }
 }
 
@@ -150,29 +183,27 @@ __device__ __forceinline__ void moments(const Grid& g, const typename Io<S>::C d
   }
   const C jx = (d[1] - d[3]) + (d[5] - d[7]) + (d[8] - d[6]);
   const C jy = (d[2] - d[4]) + (d[5] - d[7]) + (d[6] - d[8]);
+  const Phys<C>& k = phys<C>(g);
   if constexpr (Io<S>::dev) {
-    const double rd = 1.0 + (double)sf;  // sum of the f references is 1
-    rho = (C)rd;
+    // rho = 1 + sum of f deviations (the f references sum to 1); the energy
+    // balance rho E - rho u^2 / 2 is formed in FP64 from the FP64 sum of the
+    // h references and the FP32 sum of the h deviations.
+    rho = C(1) + sf;
     const C inv = C(1) / rho;
     ux = jx * inv;
-    uy = (jy - C(0.5) * rho * (C)g.g) * inv;
-    double invd = (double)inv;
-    invd = invd * (2.0 - rd * invd);  // one Newton step to FP64 accuracy
-    const double e = (g.href_sum + (double)sh) * invd;
-    double thd;
-    if (g.energy_model == E_TOTAL)
-      thd = g.six_b * (e - 0.5 * ((double)ux * (double)ux + (double)uy * (double)uy));
-    else
-      thd = g.six_b * e;
-    th = (C)thd;
+    uy = (jy - C(0.5) * rho * k.g) * inv;
+    double e = g.href_sum + (double)sh;
+    if (g.energy_model == E_TOTAL) e -= 0.5 * (double)(rho * (ux * ux + uy * uy));
+    th = k.six_b * (C)e * inv;
   } else {
     rho = sf;
-    ux = jx / rho;
-    uy = (jy - C(0.5) * rho * (C)g.g) / rho;
+    const C inv = C(1) / rho;
+    ux = jx * inv;
+    uy = (jy - C(0.5) * rho * k.g) * inv;
     if (g.energy_model == E_TOTAL)
-      th = (C)g.six_b * (sh / rho - C(0.5) * (ux * ux + uy * uy));
+      th = k.six_b * (sh * inv - C(0.5) * (ux * ux + uy * uy));
     else
-      th = (C)g.six_b * sh / rho;
+      th = k.six_b * sh * inv;
   }
 }
 
@@ -227,13 +258,14 @@ template <class C>
 __device__ void wall_equilibria(const Grid& g, int side, C rho, C ux, C uy, C th, C fw[9],
                                 C hw[9]) {
   const bool total = g.energy_model == E_TOTAL;
-  const C uwx = (C)g.uw[side][0], uwy = (C)g.uw[side][1];
+  const Phys<C>& k = phys<C>(g);
+  const C uwx = k.uw[side][0], uwy = k.uw[side][1];
   C tmp[9];
-  equilibria<C>(rho, uwx, uwy, th, (C)g.b6, total, fw, tmp);
+  equilibria<C>(rho, uwx, uwy, th, k.b6, total, fw, tmp);
   if (g.bc[side] == BC_ISO) {
-    const C thg = C(2) * (C)g.thw[side] - th;
+    const C thg = C(2) * k.thw[side] - th;
     const C rg = rho * th / thg;
-    equilibria<C>(rg, C(2) * uwx - ux, C(2) * uwy - uy, thg, (C)g.b6, total, tmp, hw);
+    equilibria<C>(rg, C(2) * uwx - ux, C(2) * uwy - uy, thg, k.b6, total, tmp, hw);
   } else {
     for (int a = 0; a < 9; ++a) hw[a] = tmp[a];
   }
@@ -297,20 +329,19 @@ __device__ __forceinline__ void collide_store(const Grid& g, S* __restrict__ dst
                                               typename Io<S>::C dqx, typename Io<S>::C dqy) {
   using C = typename Io<S>::C;
   const bool total = g.energy_model == E_TOTAL;
-  const C wf = (C)g.omega_f, wh = (C)g.omega_h;
+  const Phys<C>& k = phys<C>(g);
+  const C wf = k.omega_f, wh = k.omega_h;
   C feq[9], heq[9];
-  equilibria<C>(rho, ux, uy, th, (C)g.b6, total, feq, heq);
+  equilibria<C>(rho, ux, uy, th, k.b6, total, feq, heq);
 
   // C'_a = C_a + F_a
   C cc[9];
-  {
+  if (g.correction) {
     const C phx = C(3) * (dqx + dqy), phy = dqx - dqy;
-    const C on = g.correction ? C(1) : C(0);
-    const C c0 = on * (-phx / C(9));
-    const C c13 = on * (-phx / C(36) + phy / C(4));
-    const C c24 = on * (-phx / C(36) - phy / C(4));
-    const C cd = on * (phx / C(18));
-    cc[0] = c0;
+    const C c13 = phx * C(-1.0 / 36.0) + phy * C(0.25);
+    const C c24 = phx * C(-1.0 / 36.0) - phy * C(0.25);
+    const C cd = phx * C(1.0 / 18.0);
+    cc[0] = phx * C(-1.0 / 9.0);
     cc[1] = c13;
     cc[3] = c13;
     cc[2] = c24;
@@ -319,8 +350,13 @@ __device__ __forceinline__ void collide_store(const Grid& g, S* __restrict__ dst
     cc[6] = cd;
     cc[7] = cd;
     cc[8] = cd;
+  } else {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) cc[a] = C(0);
+  }
+  if (g.has_force) {
     // F_a = w_a [3 e.a + 9 (e.u)(e.a) - 3 u.a], a = (0, ay)
-    const C ay = -rho * (C)g.g;
+    const C ay = -rho * k.g;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       const C ea = C(ey(a)) * ay;
@@ -350,7 +386,8 @@ __device__ __forceinline__ void collide_store(const Grid& g, S* __restrict__ dst
   }
   S* p = dst + slot(g, 0, x, y);
 #pragma unroll
-  for (int a = 0; a < NPOP; ++a) p[a * g.pitch] = Io<S>::from(v[a] - pref<S>(g, a));
+  for (int a = 0; a < NPOP; ++a)
+    p[(plane(a) - plane(0)) * g.pitch] = Io<S>::from(v[a] - pref<S>(g, a));
   if (x == 0 || y == 0 || x == g.nx - 1 || y == g.ny - 1) {
     C tmp[27];
 #pragma unroll
@@ -362,8 +399,9 @@ __device__ __forceinline__ void collide_store(const Grid& g, S* __restrict__ dst
 // Q of the mirror ghost across a wall side: 2 rho u_w (1 - theta_w) - Q.
 template <class C>
 __device__ __forceinline__ C ghost_q(const Grid& g, int side, int comp, C rho, C th, C q) {
-  const C thw = g.bc[side] == BC_ISO ? (C)g.thw[side] : th;
-  return C(2) * rho * (C)g.uw[side][comp] * (C(1) - thw) - q;
+  const Phys<C>& k = phys<C>(g);
+  const C thw = g.bc[side] == BC_ISO ? k.thw[side] : th;
+  return C(2) * rho * k.uw[side][comp] * (C(1) - thw) - q;
 }
 
 // One time step.  Block = strip of blockDim.x - 2 output columns (one halo
@@ -477,7 +515,7 @@ __device__ __forceinline__ void scatter_node(const Grid& g, S* __restrict__ buf,
 __device__ __forceinline__ void init_pops(const Grid& g, double rho, double ux, double uy,
                                           double th, double p[NPOP]) {
   double feq[9], heq[9];
-  equilibria<double>(rho, ux, uy, th, g.b6, g.energy_model == E_TOTAL, feq, heq);
+  equilibria<double>(rho, ux, uy, th, g.pd.b6, g.energy_model == E_TOTAL, feq, heq);
   for (int a = 0; a < 9; ++a) {
     p[a] = feq[a];
     p[9 + a] = heq[a];
@@ -518,7 +556,7 @@ __device__ __forceinline__ void pull_fp64(const Grid& g, const S* __restrict__ b
   for (int a = 0; a < NPOP; ++a) {
     const int k = a % 9;
     const double ref = Io<S>::dev ? (double)(a < 9 ? g.fref[a] : g.href[a - 9]) : 0.0;
-    p[a] = ref + (double)Io<S>::to(q[a * g.pitch - ey(k) * g.rp - ex(k)]);
+    p[a] = ref + (double)Io<S>::to(q[(plane(a) - plane(0)) * g.pitch - ey(k) * g.rp - ex(k)]);
   }
 }
 
@@ -534,11 +572,11 @@ __device__ __forceinline__ void moments_fp64(const Grid& g, const double p[NPOP]
   }
   rho = r;
   ux = jx / r;
-  uy = (jy - 0.5 * r * g.g) / r;
+  uy = (jy - 0.5 * r * g.pd.g) / r;
   if (g.energy_model == E_TOTAL)
-    th = g.six_b * (sh / r - 0.5 * (ux * ux + uy * uy));
+    th = g.pd.six_b * (sh / r - 0.5 * (ux * ux + uy * uy));
   else
-    th = g.six_b * sh / r;
+    th = g.pd.six_b * sh / r;
 }
 
 // rho, u, T (FP64) and optionally the canonical populations [18][ny][nx].
@@ -597,7 +635,9 @@ __global__ void __launch_bounds__(RED_THREADS) conserved_partial_kernel(const Gr
     for (int k = 0; k < 4; ++k) partial[4 * blockIdx.x + k] = sm[k][0];
 }
 
-// Final fixed-order sum of nb partial quadruples into out[4].
+// Final fixed-order sum of nb partial quadruples into out[4].  (A template
+// only so that every translation unit including this header may define it.)
+template <int UNUSED = 0>
 __global__ void conserved_final_kernel(const double* __restrict__ partial, int nb, double* out) {
   __shared__ double sm[4][RED_THREADS];
   double acc[4] = {0, 0, 0, 0};

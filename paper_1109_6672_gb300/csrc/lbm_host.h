@@ -1,6 +1,7 @@
 // Host helpers shared by the single-grid and batched entry points.
 #pragma once
 
+#include <cuda.h>
 #include <stddef.h>
 
 #include <string>
@@ -19,5 +20,8 @@ size_t buffer_elems(const lbm_params* p);
 size_t buffer_bytes(const lbm_params* p);
 // Fill the kernel argument (everything but the buffer pointers).
 void fill_grid(const lbm_params* p, lbm::Grid& g);
+// TMA descriptor of one state buffer for the row-staged step kernel.
+int make_tensor_map(CUtensorMap* map, void* buffer, const lbm_params& p, const lbm::Grid& g,
+                    int box_cols, int box_planes);
 
 }  // namespace lbm_host

@@ -1,0 +1,260 @@
+// Pulled-row TMA step kernel.
+//
+// The population planes are stored grouped by e_y (lbm_device.cuh), so the 18
+// values that lattice row r pulls are three contiguous plane groups: the
+// e_y = +1 group of row r - 1, the e_y = 0 group of row r and the e_y = -1
+// group of row r + 1.  One ring slot in shared memory holds one such "pulled
+// row" (3 groups x NB boxes of the tensor map, columns x0 - 8 .. x0 + TWC + 7),
+// delivered by cp.async.bulk.tensor and guarded by an mbarrier with
+// transaction-count completion.  The moments of row r and the collision of row
+// r - 1 each read one slot, so a ring of D slots keeps D - 2 rows in flight.
+// Rows across a periodic y boundary are staged the same way (their node row
+// wraps; the ghost rows supply the wrapped neighbours).
+//
+// Block = 4 compute warps (each thread NPT columns, 128 apart) + 1 helper
+// warp.  The helper warp computes Q_x of the two halo columns (x0 - 1 and
+// x0 + TWC) and issues the copies, so the compute warps do identical work per
+// row; one block barrier per row publishes Q_x and frees the slot of row r - 1.
+//
+// Waits on mbarriers are bounded by the global timer; on timeout the block
+// sets *g.status, drains its own copies (bounded) and returns.
+#pragma once
+
+#include "lbm_step_tma.cuh"
+
+namespace lbm {
+
+constexpr int PR_COMPUTE = 128;              // compute threads per block
+constexpr int PR_THREADS = PR_COMPUTE + 32;  // plus the helper warp
+
+template <class S, int NPT>
+struct PrGeom {
+  static constexpr int TWC = PR_COMPUTE * NPT;  // output columns per block
+  static constexpr int NB = NPT == 1 ? 1 : 2;   // boxes per plane group
+  static constexpr int BW = (TWC + 16) / NB;    // columns per box
+  static constexpr int GB =                     // elements per box (128 B aligned)
+      (int)(((size_t)6 * BW * sizeof(S) + 127) / 128 * 128 / sizeof(S));
+  static constexpr int SLOT = 3 * NB * GB;  // elements per pulled row
+  static constexpr int D = sizeof(S) == 8 ? 3 : 4;
+  static constexpr unsigned BOX_BYTES = 6 * BW * sizeof(S);
+  static constexpr size_t smem_bytes() {
+    return (size_t)D * SLOT * sizeof(S) + 2 * (TWC + 2) * sizeof(typename Io<S>::C) + D * 8;
+  }
+  static_assert(BW % 8 == 0, "box starts must stay 16-byte aligned");
+  static_assert((GB * sizeof(S)) % 128 == 0, "boxes must start on 128-byte boundaries");
+};
+
+// Offset inside a plane-group block of staged column sc (local column + 8).
+template <class S, int NPT>
+__device__ __forceinline__ int pr_col(int sc) {
+  using G = PrGeom<S, NPT>;
+  const int b = sc >= G::BW ? 1 : 0;
+  return b * G::GB + (sc - b * G::BW);
+}
+
+// Pulled populations of a node from a slot; co[e_x + 1] = column offsets.
+template <class S, int NPT>
+__device__ __forceinline__ void pull_pr(const S* slot, const int co[3],
+                                        typename Io<S>::C d[NPOP]) {
+  using G = PrGeom<S, NPT>;
+#pragma unroll
+  for (int a = 0; a < NPOP; ++a) {
+    const int grp = pgroup(a), lp = plane(a) - 6 * grp;
+    d[a] = Io<S>::to(slot[grp * G::NB * G::GB + lp * G::BW + co[ex(a % 9) + 1]]);
+  }
+}
+
+template <class S, int NPT, int M>
+__global__ void __launch_bounds__(PR_THREADS) step_pr_kernel(
+    const Grid g, const __grid_constant__ CUtensorMap map, int rows) {
+  using C = typename Io<S>::C;
+  using G = PrGeom<S, NPT>;
+  constexpr int D = G::D, TWC = G::TWC;
+  constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
+  extern __shared__ __align__(1024) unsigned char smem[];
+  S* ring = reinterpret_cast<S*>(smem);
+  C* qxs = reinterpret_cast<C*>(smem + (size_t)D * G::SLOT * sizeof(S));
+  unsigned char* bar_mem = reinterpret_cast<unsigned char*>(qxs + 2 * (TWC + 2));
+  const unsigned ring_s = smem_u32(ring), bar_s = smem_u32(bar_mem);
+
+  const int t = threadIdx.x, nx = g.nx, ny = g.ny;
+  const int x0 = blockIdx.x * TWC;
+  const int y0 = blockIdx.y * rows;
+  if (y0 >= ny) return;  // whole block
+  const int y1 = min(y0 + rows, ny);
+  const bool wall_l = g.bc[0] != BC_PERIODIC, wall_r = g.bc[1] != BC_PERIODIC;
+  const bool wall_b = g.bc[2] != BC_PERIODIC, wall_t = g.bc[3] != BC_PERIODIC;
+  // staged pulled rows rs .. re (halo rows only where they hold nodes)
+  const int rs = (y0 >= 1 || !wall_b) ? y0 - 1 : y0;
+  const int re = (y1 < ny || !wall_t) ? y1 : y1 - 1;
+  const int nq = re - rs + 1;
+  const S* __restrict__ src = static_cast<const S*>(g.src);
+  S* __restrict__ dst = static_cast<S*>(g.dst);
+  const int pitch = g.pitch;
+  const bool helper = t >= PR_COMPUTE;
+  const int hl = t - PR_COMPUTE;  // helper lane
+
+  if (t == 0) {
+    for (int i = 0; i < D; ++i) mbar_init(bar_s + 8 * i, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  int issued = 0;  // staged rows issued so far (helper lane 0)
+  auto issue_upto = [&](int kmax) {
+    kmax = min(kmax, nq - 1);
+    for (; issued <= kmax; ++issued) {
+      const int s = issued % D;
+      const unsigned bar = bar_s + 8 * s;
+      int nr = rs + issued;  // node row of this pulled row
+      nr = nr < 0 ? nr + ny : (nr >= ny ? nr - ny : nr);
+      mbar_expect_tx(bar, 3 * G::NB * G::BOX_BYTES);
+#pragma unroll
+      for (int grp = 0; grp < 3; ++grp)
+#pragma unroll
+        for (int b = 0; b < G::NB; ++b)
+          tma_load_box(ring_s + (unsigned)((s * G::SLOT + (grp * G::NB + b) * G::GB) * sizeof(S)),
+                       &map, bar, x0 - 8 + b * G::BW + XOFF, 6 * grp, nr + grp);  // row nr-1+grp, +1
+    }
+  };
+  if (helper && hl == 0) issue_upto(D - 2);
+
+  // columns handled by this thread and their staged-column offsets
+  int cols[NPT], co[NPT][3];
+#pragma unroll
+  for (int i = 0; i < NPT; ++i) {
+    const int lc = helper ? (hl == 0 ? -1 : TWC) : t + PR_COMPUTE * i;
+    cols[i] = x0 + lc;
+    co[i][0] = pr_col<S, NPT>(lc + 9);  // e_x = -1 pulls from x + 1
+    co[i][1] = pr_col<S, NPT>(lc + 8);
+    co[i][2] = pr_col<S, NPT>(lc + 7);  // e_x = +1 pulls from x - 1
+  }
+  // where the (first) node of this thread comes from: 0 idle, 1 ring, 2 global
+  int src0 = 0, gx0 = 0;
+  {
+    const int c = cols[0];
+    if (helper && hl > 1) {
+      src0 = 0;
+    } else if (c >= 0 && c < nx) {
+      src0 = 1;
+      gx0 = c;
+    } else if (c == -1 && !wall_l) {
+      src0 = 2;
+      gx0 = nx - 1;
+    } else if (c == nx && !wall_r) {
+      src0 = 2;
+      gx0 = 0;
+    }
+  }
+
+  C prho[NPT], pux[NPT], puy[NPT], pth[NPT], pqx[NPT], pqy[NPT], qymm[NPT];
+#pragma unroll
+  for (int i = 0; i < NPT; ++i) {
+    prho[i] = 1;
+    pux[i] = puy[i] = pqx[i] = pqy[i] = qymm[i] = 0;
+    pth[i] = 1;
+  }
+  int qs = 0;  // Q_x slot of the current row
+  for (int r = y0 - 1; r <= y1; ++r) {
+    C crho[NPT], cux[NPT], cuy[NPT], cth[NPT], cqx[NPT], cqy[NPT];
+#pragma unroll
+    for (int i = 0; i < NPT; ++i) {
+      crho[i] = 1;
+      cux[i] = cuy[i] = cqx[i] = cqy[i] = 0;
+      cth[i] = 1;
+    }
+    bool ok = true;
+    const int k = r - rs;
+    if (k >= 0 && k < nq) {
+      ok = mbar_wait(bar_s + 8 * (k % D), (k / D) & 1, WAIT_NS);
+      const S* slot = ring + (k % D) * G::SLOT;
+      int nr = r < 0 ? r + ny : (r >= ny ? r - ny : r);
+#pragma unroll
+      for (int i = 0; i < NPT; ++i) {
+        if (helper && i > 0) break;
+        int how;
+        int gx;
+        if (i == 0) {
+          how = src0;
+          gx = gx0;
+        } else {
+          const int c = cols[i];
+          how = c < nx ? 1 : ((c == nx && !wall_r) ? 2 : 0);
+          gx = c < nx ? c : 0;
+        }
+        if (!how) continue;
+        C d[NPOP];
+        if (how == 1)
+          pull_pr<S, NPT>(slot, co[i], d);
+        else
+          pull<S>(g, src, gx, nr, d);
+        moments_m<S, M>(g, d, crho[i], cux[i], cuy[i], cth[i]);
+        cqx[i] = crho[i] * cux[i] * (C(1) - cth[i]);
+        cqy[i] = crho[i] * cuy[i] * (C(1) - cth[i]);
+      }
+    }
+    C* qrow = qxs + qs * (TWC + 2);
+    if (!helper) {
+#pragma unroll
+      for (int i = 0; i < NPT; ++i) qrow[t + PR_COMPUTE * i + 1] = cqx[i];
+    } else if (hl == 0) {
+      qrow[0] = cqx[0];
+    } else if (hl == 1) {
+      qrow[TWC + 1] = cqx[0];
+    }
+    const int ro = r - 1;
+    if (!helper && ro >= y0) {
+      const S* slot = ring + ((k - 1) % D) * G::SLOT;  // pulled row ro (k - 1 >= 0)
+      const C* qprev = qxs + (qs ^ 1) * (TWC + 2);
+      S* prow = dst + (long long)(ro + 1) * g.rp + XOFF;
+#pragma unroll
+      for (int i = 0; i < NPT; ++i) {
+        const int c = cols[i];
+        if (c >= nx) continue;
+        C d[NPOP];
+        pull_pr<S, NPT>(slot, co[i], d);
+        const int lq = t + PR_COMPUTE * i + 1;
+        const C qxl =
+            (c > 0 || !wall_l) ? qprev[lq - 1] : ghost_q<C>(g, 0, 0, prho[i], pth[i], pqx[i]);
+        const C qxr = (c < nx - 1 || !wall_r) ? qprev[lq + 1]
+                                              : ghost_q<C>(g, 1, 0, prho[i], pth[i], pqx[i]);
+        const C qyu =
+            (ro < ny - 1 || !wall_t) ? cqy[i] : ghost_q<C>(g, 3, 1, prho[i], pth[i], pqy[i]);
+        const C qyd =
+            (ro > 0 || !wall_b) ? qymm[i] : ghost_q<C>(g, 2, 1, prho[i], pth[i], pqy[i]);
+        C v[27];
+        collide_m<S, M>(g, prow + c, pitch, d, prho[i], pux[i], puy[i], pth[i],
+                        C(0.5) * (qxr - qxl), C(0.5) * (qyu - qyd), v);
+        if (c == 0 || ro == 0 || c == nx - 1 || ro == ny - 1) {
+          C tmp[27];
+#pragma unroll
+          for (int a = 0; a < 27; ++a) tmp[a] = v[a];
+          boundary_writes<S>(g, dst, c, ro, tmp, prho[i], pux[i], puy[i], pth[i]);
+        }
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      // a staged row never arrived: record, drain what is in flight, leave
+      if (helper && hl == 0) {
+        if (g.status) atomicOr(g.status, 1);
+        for (int j = max(k, 0); j < issued; ++j)
+          mbar_wait(bar_s + 8 * (j % D), (j / D) & 1, WAIT_NS / 4);
+      }
+      return;
+    }
+    // everyone is done with pulled row r - 1: refill its slot
+    if (helper && hl == 0) issue_upto(k + D - 1);
+#pragma unroll
+    for (int i = 0; i < NPT; ++i) {
+      qymm[i] = pqy[i];
+      prho[i] = crho[i];
+      pux[i] = cux[i];
+      puy[i] = cuy[i];
+      pth[i] = cth[i];
+      pqx[i] = cqx[i];
+      pqy[i] = cqy[i];
+    }
+    qs ^= 1;
+  }
+}
+
+}  // namespace lbm

@@ -1,0 +1,208 @@
+// Building blocks of the TMA-staged step kernel (lbm_step_pr.cuh): the
+// compile-time physics mode, the per-node moments and collision written for
+// one mode, and the mbarrier / bulk-tensor-copy primitives.
+//
+// The physics mode (total or internal energy, form of Z, correction, force)
+// is a template parameter, so the per-direction code is straight-line.
+#pragma once
+
+#include <cuda.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// ---- compile-time physics mode ---------------------------------------------
+
+enum { MODE_TOTAL = 1, MODE_ZFULL = 2, MODE_CORR = 4, MODE_FORCE = 8 };
+
+template <int M>
+struct Mode {
+  static constexpr bool total = (M & MODE_TOTAL) != 0;
+  static constexpr bool zfull = (M & MODE_ZFULL) != 0;
+  static constexpr bool corr = (M & MODE_CORR) != 0;
+  static constexpr bool force = (M & MODE_FORCE) != 0;
+};
+
+// The eight modes the validated parameters can produce (Z only matters for
+// total energy; gravity needs internal energy).
+inline int mode_of(const Grid& g) {
+  int m = 0;
+  if (g.energy_model == E_TOTAL) {
+    m |= MODE_TOTAL;
+    if (g.z_full) m |= MODE_ZFULL;
+  } else if (g.has_force) {
+    m |= MODE_FORCE;
+  }
+  if (g.correction) m |= MODE_CORR;
+  return m;
+}
+
+// Moments (Eq. 35 with the force shift, Eq. 37 or the Eq. 38 form); deviation
+// storage forms rho E - rho u^2 / 2 in FP64.
+template <class S, int M>
+__device__ __forceinline__ void moments_m(const Grid& g, const typename Io<S>::C d[NPOP],
+                                          typename Io<S>::C& rho, typename Io<S>::C& ux,
+                                          typename Io<S>::C& uy, typename Io<S>::C& th) {
+  using C = typename Io<S>::C;
+  using MD = Mode<M>;
+  const Phys<C>& k = phys<C>(g);
+  const C sf = (d[0] + d[1]) + (d[2] + d[3]) + (d[4] + d[5]) + (d[6] + d[7]) + d[8];
+  const C sh = (d[9] + d[10]) + (d[11] + d[12]) + (d[13] + d[14]) + (d[15] + d[16]) + d[17];
+  const C jx = (d[1] - d[3]) + (d[5] - d[7]) + (d[8] - d[6]);
+  C jy = (d[2] - d[4]) + (d[5] - d[7]) + (d[6] - d[8]);
+  if constexpr (Io<S>::dev) {
+    rho = C(1) + sf;  // the f references sum to 1
+  } else {
+    rho = sf;
+  }
+  if constexpr (MD::force) jy -= C(0.5) * rho * k.g;
+  C inv;
+  if constexpr (sizeof(C) == 4)
+    inv = __frcp_rn(rho);
+  else
+    inv = C(1) / rho;
+  ux = jx * inv;
+  uy = jy * inv;
+  if constexpr (Io<S>::dev) {
+    double e = g.href_sum + (double)sh;
+    if constexpr (MD::total) e -= 0.5 * (double)(rho * (ux * ux + uy * uy));
+    th = k.six_b * (C)e * inv;
+  } else if constexpr (MD::total) {
+    th = k.six_b * (sh * inv - C(0.5) * (ux * ux + uy * uy));
+  } else {
+    th = k.six_b * sh * inv;
+  }
+}
+
+// Collision (Eq. 34 with +(1 - w_f/2) C', Eq. 36 or Eq. 38; C' = C_a of
+// Eq. 49 plus the Guo force) of one node and its 18 stores at p (node slot,
+// population stride `pitch`).  v receives f*, h*, h^eq for the wall rules.
+template <class S, int M>
+__device__ __forceinline__ void collide_m(const Grid& g, S* __restrict__ p, int pitch,
+                                          const typename Io<S>::C d[NPOP], typename Io<S>::C rho,
+                                          typename Io<S>::C ux, typename Io<S>::C uy,
+                                          typename Io<S>::C th, typename Io<S>::C dqx,
+                                          typename Io<S>::C dqy, typename Io<S>::C v[27]) {
+  using C = typename Io<S>::C;
+  using MD = Mode<M>;
+  const Phys<C>& k = phys<C>(g);
+  const C wf = k.omega_f, wh = k.omega_h;
+  C feq[9], heq[9];
+  equilibria<C>(rho, ux, uy, th, k.b6, MD::total, feq, heq);
+
+  C cc[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) cc[a] = C(0);
+  if constexpr (MD::corr) {
+    const C phx = C(3) * (dqx + dqy), phy = dqx - dqy;
+    const C c13 = phx * C(-1.0 / 36.0) + phy * C(0.25);
+    const C c24 = phx * C(-1.0 / 36.0) - phy * C(0.25);
+    const C cd = phx * C(1.0 / 18.0);
+    cc[0] = phx * C(-1.0 / 9.0);
+    cc[1] = c13;
+    cc[3] = c13;
+    cc[2] = c24;
+    cc[4] = c24;
+    cc[5] = cd;
+    cc[6] = cd;
+    cc[7] = cd;
+    cc[8] = cd;
+  }
+  if constexpr (MD::force) {
+    // F_a = w_a [3 e.a + 9 (e.u)(e.a) - 3 u.a], a = (0, ay)
+    const C ay = -rho * k.g;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const C ea = C(ey(a)) * ay;
+      const C eu = C(ex(a)) * ux + C(ey(a)) * uy;
+      cc[a] += wgt<C>(a) * (C(3) * ea + C(9) * eu * ea - C(3) * uy * ay);
+    }
+  }
+  const C kc = C(1) - C(0.5) * wf;
+  const C kz = wh - wf;
+  const C zc = MD::zfull ? C(0.5) * (ux * ux + uy * uy) : C(0);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    C fa = d[a], ha = d[9 + a];
+    if constexpr (Io<S>::dev) {
+      fa += pref<S>(g, a);
+      ha += pref<S>(g, 9 + a);
+    }
+    const C fneq = fa - feq[a];
+    v[a] = fa - wf * fneq + kc * cc[a];
+    C hs = ha - wh * (ha - heq[a]);
+    if constexpr (MD::total) {
+      const C eu = C(ex(a)) * ux + C(ey(a)) * uy;
+      hs += kz * (eu - zc) * (fneq + C(0.5) * cc[a]);
+    }
+    v[9 + a] = hs;
+    v[18 + a] = heq[a];
+  }
+#pragma unroll
+  for (int a = 0; a < NPOP; ++a) {
+    if constexpr (Io<S>::dev)
+      p[plane(a) * pitch] = Io<S>::from(v[a] - pref<S>(g, a));
+    else
+      p[plane(a) * pitch] = Io<S>::from(v[a]);
+  }
+}
+
+// ---- TMA pipeline primitives ----------------------------------------------
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of the barrier, giving up after `limit_ns`.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity,
+                                          unsigned long long limit_ns) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_test(bar, parity)) {
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_box(unsigned dst, const CUtensorMap* map, unsigned bar,
+                                             int cx, int ca, int cy) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(cx), "r"(ca), "r"(cy), "r"(bar)
+      : "memory");
+}
+
+}  // namespace lbm
