@@ -148,6 +148,35 @@ int lbm_conserved(lbm_handle* h, double out[4]);
 int lbm_get_state(lbm_handle* h, double* pops);
 int lbm_set_state(lbm_handle* h, const double* pops);
 
+/* Allocation-free form of lbm_conserved() for callers that cannot allocate
+ * device memory when they need the sums: code inside CUDA stream capture,
+ * serving loops whose device memory belongs to a pool that forbids outside
+ * allocations, and latency-bound paths that cannot afford cudaMalloc's
+ * implicit synchronisation.  (The paper has no counterpart; this is a
+ * property of the library, not of the method.)
+ *   p        parameters of the grid (validated as in lbm_create()).
+ *   d_state  device pointer to one state buffer in the library's layout: for a
+ *            handle made by lbm_create_in() on buffer B, the state after k
+ *            steps since lbm_init()/lbm_set_state() starts at
+ *            B + (k % 2) * lbm_state_bytes(p) / 2 (256-byte aligned).
+ *   d_out    device pointer to 4 doubles (8-byte aligned): sums of rho,
+ *            rho u_x, rho u_y and hbar, the same values lbm_conserved()
+ *            returns.
+ *   cuda_stream  stream to enqueue on (NULL = default stream); asynchronous.
+ * Calls no cudaMalloc, cudaFree or allocating routine: the per-block partial
+ * sums live in a file-scope device array of 1024 quadruples of doubles
+ * (32 KiB) that every device loading the library keeps until process exit;
+ * grids needing more partial slots are rejected with LBM_ERR_PARAM (with the
+ * library's node limit of 2^31 none does).  The first call on a device looks
+ * the array up on that device (make it, with that device current, before any
+ * stream capture).  All calls share the array: calls that overlap on the GPU
+ * (different streams, or devices sharing nothing but the host thread's
+ * current device) race and must be ordered by the caller.  Returns
+ * LBM_ERR_PARAM for invalid arguments, LBM_ERR_CUDA if the lookup or a launch
+ * fails. */
+int lbm_conserved_noalloc(const lbm_params* p, const void* d_state, double* d_out,
+                          void* cuda_stream);
+
 /* Waits for all work enqueued on the handle's stream; reports a pending
  * kernel error as LBM_ERR_CUDA. */
 int lbm_sync(lbm_handle* h);

@@ -70,6 +70,8 @@ def load() -> ctypes.CDLL:
         "lbm_moments": (ctypes.c_int, [_H, _DP, _DP, _DP, _DP]),
         "lbm_moments_device": (ctypes.c_int, [_H] + [ctypes.c_void_p] * 4),
         "lbm_conserved": (ctypes.c_int, [_H, _DP]),
+        "lbm_conserved_noalloc": (ctypes.c_int, [P, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p]),
         "lbm_get_state": (ctypes.c_int, [_H, _DP]),
         "lbm_set_state": (ctypes.c_int, [_H, _DP]),
         "lbm_sync": (ctypes.c_int, [_H]),
@@ -171,6 +173,15 @@ def lbm_conserved(h) -> np.ndarray:
     out = np.zeros(4)
     _check(load().lbm_conserved(h, _dp(out)), h)
     return out
+
+
+def lbm_conserved_noalloc(params: dict, d_state: int, d_out: int, stream: int = 0):
+    """Allocation-free conserved sums into device memory (4 doubles at d_out)
+    from the state buffer at d_state; asynchronous on `stream`."""
+    st = load().lbm_conserved_noalloc(ctypes.byref(make_params(params)), ctypes.c_void_p(d_state),
+                                      ctypes.c_void_p(d_out), ctypes.c_void_p(stream or None))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_conserved_noalloc failed")
 
 
 def lbm_get_state(h, shape) -> np.ndarray:
