@@ -165,6 +165,109 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def batch_and_serving(torch, args):
+    """Batched cavities (256 grids, sides 64..512) with 16-bit deviation storage
+    against per-grid FP64 launches, the error of each storage precision against
+    FP64 after 10 000 steps, and a bounded serving trace at load factor 0.7."""
+    from paper_1109_6672_gb300 import inputs, lbm, serve
+
+    out = {}
+    names = {lbm.LBM_P_FP32_BF16: "bf16", lbm.LBM_P_FP32_FP16: "f16", lbm.LBM_P_FP32: "f32"}
+
+    def batched(precision):
+        grids = inputs.batch_cavities(count=args.batch_grids, seed=4, precision=precision)
+        nodes = sum(p["nx"] * p["ny"] for p, _ in grids)
+        pool = sum(lbm.lbm_state_bytes(p) for p, _ in grids) + (64 << 20)
+        b = lbm.Batch(precision, len(grids), pool)
+        for p, f in grids:
+            b.add(p, f, 10 ** 9)
+        tuned = b.autotune(3)
+        b.run(args.batch_steps)  # capture + warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.run(args.batch_steps)
+        dt = time.perf_counter() - t0
+        b.close()
+        glups = nodes * args.batch_steps / dt / 1e9
+        return grids, nodes, glups, tuned
+
+    grids, nodes, glups, tuned = batched(lbm.LBM_P_FP32_BF16)
+    sims = glups * 1e9 / (nodes / len(grids) * 10000)
+    _, _, glups16, tuned16 = batched(lbm.LBM_P_FP32_FP16)
+    # plain one-grid-per-launch FP64 path
+    f64 = [lbm.Lbm(dict(p, precision=lbm.LBM_P_FP64)).init(*f) for p, f in grids]
+    for g in f64:
+        g.step(2)
+    torch.cuda.synchronize()
+    k64 = max(5, args.batch_steps // 4)
+    t0 = time.perf_counter()
+    for _ in range(k64):
+        for g in f64:
+            g.step(1)
+    torch.cuda.synchronize()
+    dt64 = time.perf_counter() - t0
+    for g in f64:
+        g.close()
+    glups64 = nodes * k64 / dt64 / 1e9
+    sims64 = glups64 * 1e9 / (nodes / len(grids) * 10000)
+    # error of each storage precision (batched) against the FP64 path after
+    # 10 000 steps, on grids of side <= 256 spanning the dT range of the batch
+    small = sorted((g for g in grids if g[0]["nx"] <= 256),
+                   key=lambda g: abs(g[0]["T_wall"][0] - g[0]["T_wall"][1]))
+    pick = [small[round(i * (len(small) - 1) / max(args.batch_err_grids - 1, 1))]
+            for i in range(args.batch_err_grids)] if small else []
+    errs = {names[q]: [] for q in names}
+    for p, f in pick:
+        ref = lbm.Lbm(dict(p, precision=lbm.LBM_P_FP64)).init(*f).step(10000)
+        rho64, ux64, uy64, T64 = ref.moments()
+        ref.close()
+        dTw = abs(p["T_wall"][0] - p["T_wall"][1])
+        umax = max(np.abs(ux64).max(), np.abs(uy64).max())
+        for q in names:
+            pq = dict(p, precision=q)
+            bb = lbm.Batch(q, 1, lbm.lbm_state_bytes(pq) + (1 << 20))
+            sl = bb.add(pq, f, 10000)
+            while bb.remaining(sl):
+                bb.run(min(1000, bb.remaining(sl)))
+            rho, ux, uy, T = bb.moments(sl)
+            bb.close()
+            du = np.sqrt((ux - ux64) ** 2 + (uy - uy64) ** 2)
+            errs[names[q]].append({
+                "n": p["nx"], "dT_over_T0": dTw,
+                "T_max_rel": float(np.abs(T - T64).max() / np.abs(T64).max()),
+                "T_l2_rel": float(np.sqrt(np.mean((T - T64) ** 2) / np.mean(T64 ** 2))),
+                "T_max_over_dT": float(np.abs(T - T64).max() / dTw),
+                "u_max_over_umax": float(du.max() / umax),
+                "u_l2_over_umax": float(np.sqrt(np.mean(du ** 2)) / umax)})
+    out["batch"] = {
+        "grids": len(grids), "nodes": nodes, "precision": "f32 arithmetic, bf16 storage",
+        "steps_timed": args.batch_steps, "glups": glups, "sims_per_s_10k_steps": sims,
+        "autotune": tuned,
+        "f16_storage": {"glups": glups16, "autotune": tuned16,
+                        "sims_per_s_10k_steps": glups16 * 1e9 / (nodes / len(grids) * 10000)},
+        "fp64_one_grid_per_launch": {"glups": glups64, "sims_per_s_10k_steps": sims64,
+                                     "steps_timed": k64},
+        "speedup_sims_per_s": sims / sims64,
+        "error_vs_fp64_after_10k_steps": errs,
+    }
+    # serving: bounded trace, arrivals scaled to 70 % of the batched throughput
+    trace = serve.make_trace(args.serve_requests, seed=5, rate=50.0, cavity_sides=(32, 512),
+                             couette_ny=(17, 257), steps_range=(1000, 10000))
+    factor = serve.load_factor_scale(trace, glups, load=0.7)
+    serve.scale_arrivals(trace, factor)
+    sb = lbm.Batch(lbm.LBM_P_FP32_BF16, 64, 8 << 30)
+    srv = serve.Server(sb, lbm.LBM_P_FP32_BF16, seg_max=256, seg_min=16)
+    res = srv.run(trace)
+    sb.close()
+    st = serve.summarize(res, srv.wall, srv.node_updates)
+    st.update({"load_factor": 0.7, "arrival_time_scale": factor,
+               "trace": f"{args.serve_requests} requests, 70 % cavity (side 32-512) / 30 % "
+                        "Couette (ny 17-257), 1e3-1e4 steps, Poisson arrivals (seed 5) "
+                        "time-scaled to 0.7 of the batched throughput"})
+    out["serving"] = st
+    return out
+
+
 def time_steps(torch, lbm_mod, g, stream, steps):
     """CUDA-event time of `steps` back-to-back step launches on `stream`."""
     e0 = torch.cuda.Event(enable_timing=True)
@@ -271,6 +374,10 @@ def run_ours(args, rank, world, local_rank):
     else:
         g.close()
 
+    extra = {}
+    if rank == 0 and world == 1 and args.batch:
+        extra = batch_and_serving(torch, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cores = cpu_cores()
@@ -310,6 +417,7 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clk.summary(),
             "variants": variants,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -330,6 +438,11 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=800)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", dest="variants", action="store_false")
+    ap.add_argument("--no-batch", dest="batch", action="store_false")
+    ap.add_argument("--batch-grids", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--batch-err-grids", type=int, default=4)
+    ap.add_argument("--serve-requests", type=int, default=40)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

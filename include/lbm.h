@@ -177,6 +177,66 @@ int lbm_set_state(lbm_handle* h, const double* pops);
 int lbm_conserved_noalloc(const lbm_params* p, const void* d_state, double* d_out,
                           void* cuda_stream);
 
+/* ---- Batched grids ---------------------------------------------------------
+ * Many independent grids (any sizes, physics modes and boundary conditions, one
+ * storage precision) advance together: one kernel launch per time step covers
+ * every grid, k steps are replayed from a CUDA graph captured once per k, and
+ * the per-grid work is split into items (128 columns x rows of one grid) that a
+ * persistent grid of blocks takes in turn.  Results do not depend on which other
+ * grids are in the batch, nor on the schedule.  Grids are placed in one device
+ * pool (first fit, 256-byte aligned); lbm_batch_add() admits a grid only if a
+ * slot and lbm_state_bytes(p) of contiguous pool space are free. */
+typedef struct lbm_batch lbm_batch;
+
+/* Creates a batch for `precision` (LBM_P_*) with up to max_grids slots and a
+ * device pool of pool_bytes (allocated here; lbm_batch_create_in() takes a
+ * caller-owned, 256-byte aligned pool instead).  cuda_stream NULL: the batch
+ * creates its own non-blocking stream (graph capture needs one). */
+int lbm_batch_create(int32_t precision, int32_t max_grids, int64_t pool_bytes, void* cuda_stream,
+                     lbm_batch** out);
+int lbm_batch_create_in(int32_t precision, int32_t max_grids, void* device_pool,
+                        int64_t pool_bytes, void* cuda_stream, lbm_batch** out);
+
+/* Admits a grid (params as for lbm_create(), precision equal to the batch's),
+ * initialises it to equilibrium at the host fields (as lbm_init()) and gives it
+ * a budget of `steps` time steps.  *slot receives its slot.  LBM_ERR_OOM if no
+ * slot or no pool space is free (the batch is unchanged).  Synchronous. */
+int lbm_batch_add(lbm_batch* b, const lbm_params* p, const double* rho, const double* ux,
+                  const double* uy, const double* T, int64_t steps, int32_t* slot);
+
+/* Advances every admitted grid by min(k, its remaining budget) steps, k in
+ * [0, 4096], with one graph launch; synchronous. */
+int lbm_batch_run(lbm_batch* b, int64_t k);
+
+/* Remaining step budget of a slot (negative LBM_ERR_* for a free slot). */
+int64_t lbm_batch_remaining(const lbm_batch* b, int32_t slot);
+
+/* Moments (as lbm_moments()) and canonical populations (as lbm_get_state())
+ * of a slot's current state into host arrays; synchronous. */
+int lbm_batch_moments(lbm_batch* b, int32_t slot, double* rho, double* ux, double* uy,
+                      double* T);
+int lbm_batch_get_state(lbm_batch* b, int32_t slot, double* pops);
+
+/* Releases a slot and its pool space. */
+int lbm_batch_remove(lbm_batch* b, int32_t slot);
+
+/* Autotuner: times `reps` launches of one step of the admitted grids (without
+ * advancing them) for each candidate schedule -- rows per work item in
+ * {4, 6, 8, 12, 16, 24} x atomic or round-robin item assignment -- and keeps
+ * the fastest.  out_best (may be NULL): rows, dynamic (1 atomic, 0 round
+ * robin), microseconds per step. */
+int lbm_batch_autotune(lbm_batch* b, int32_t reps, int64_t out_best[3]);
+
+/* Sets the schedule by hand (rows 0 = default). */
+int lbm_batch_set_schedule(lbm_batch* b, int32_t rows, int32_t dynamic);
+
+/* out: admitted grids, their total nodes, free pool bytes, largest free range,
+ * rows per item, dynamic flag. */
+int lbm_batch_info(const lbm_batch* b, int64_t out[6]);
+
+void lbm_batch_destroy(lbm_batch* b); /* NULL-safe */
+const char* lbm_batch_last_error(const lbm_batch* b);
+
 /* Waits for all work enqueued on the handle's stream; reports a pending
  * kernel error as LBM_ERR_CUDA. */
 int lbm_sync(lbm_handle* h);

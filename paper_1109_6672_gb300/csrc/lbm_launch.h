@@ -30,4 +30,16 @@ cudaError_t launch_step_tma(const Grid& g, const CUtensorMap& map, int variant, 
 template <class S>
 int occupancy_step_tma(const Grid& g, int variant);
 
+struct BatchGrid;
+struct WorkItem;
+struct BatchCtl;
+
+// One step of the batched kernel (lbm_batch.cuh) for the items of physics
+// mode `mode` over `blocks` persistent blocks, and its resident blocks per SM.
+template <class S>
+cudaError_t launch_batch_step(const BatchGrid* grids, const WorkItem* items, BatchCtl* ctl, int j,
+                              int mode, int blocks, cudaStream_t stream);
+template <class S>
+int occupancy_batch(int mode);
+
 }  // namespace lbm

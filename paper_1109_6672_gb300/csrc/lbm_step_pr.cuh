@@ -64,23 +64,57 @@ __device__ __forceinline__ void pull_pr(const S* slot, const int co[3],
   }
 }
 
+// Shared-memory layout of a block: ring slots, Q_x rows, mbarriers.
+template <class S, int NPT>
+struct PrSmem {
+  using C = typename Io<S>::C;
+  using G = PrGeom<S, NPT>;
+  __device__ static S* ring(unsigned char* smem) { return reinterpret_cast<S*>(smem); }
+  __device__ static C* qxs(unsigned char* smem) {
+    return reinterpret_cast<C*>(smem + (size_t)G::D * G::SLOT * sizeof(S));
+  }
+  __device__ static unsigned bars(unsigned char* smem) {
+    return smem_u32(qxs(smem) + 2 * (G::TWC + 2));
+  }
+};
+
+// Initialise the ring's mbarriers (once per kernel, all threads call).
+template <class S, int NPT>
+__device__ __forceinline__ void pr_init(unsigned char* smem) {
+  if (threadIdx.x == 0) {
+    const unsigned bar_s = PrSmem<S, NPT>::bars(smem);
+    for (int i = 0; i < PrGeom<S, NPT>::D; ++i) mbar_init(bar_s + 8 * i, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+}
+
+// Rows staged by a block that owns rows [y0, y0 + rows) of grid g.
+__device__ __forceinline__ int pr_staged_rows(const Grid& g, int y0, int rows) {
+  const int y1 = min(y0 + rows, g.ny);
+  const int rs = (y0 >= 1 || g.bc[2] == BC_PERIODIC) ? y0 - 1 : y0;
+  const int re = (y1 < g.ny || g.bc[3] == BC_PERIODIC) ? y1 : y1 - 1;
+  return re - rs + 1;
+}
+
+// One block's share of a step: columns [x0, x0 + TWC), rows [y0, y0 + rows)
+// of grid g, reading the state at src through the tensor map `map` and
+// writing the next state to dst.  kbase counts the rows this block staged
+// before (ring slot and mbarrier phase continue across calls).  Returns 0, or
+// 1 if a staged row never arrived (after draining its own copies).
 template <class S, int NPT, int M>
-__global__ void __launch_bounds__(PR_THREADS) step_pr_kernel(
-    const Grid g, const __grid_constant__ CUtensorMap map, int rows) {
+__device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, const void* src_v,
+                                        void* dst_v, int x0, int y0, int rows, unsigned char* smem,
+                                        int kbase) {
   using C = typename Io<S>::C;
   using G = PrGeom<S, NPT>;
   constexpr int D = G::D, TWC = G::TWC;
   constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
-  extern __shared__ __align__(1024) unsigned char smem[];
-  S* ring = reinterpret_cast<S*>(smem);
-  C* qxs = reinterpret_cast<C*>(smem + (size_t)D * G::SLOT * sizeof(S));
-  unsigned char* bar_mem = reinterpret_cast<unsigned char*>(qxs + 2 * (TWC + 2));
-  const unsigned ring_s = smem_u32(ring), bar_s = smem_u32(bar_mem);
+  S* ring = PrSmem<S, NPT>::ring(smem);
+  C* qxs = PrSmem<S, NPT>::qxs(smem);
+  const unsigned ring_s = smem_u32(ring), bar_s = PrSmem<S, NPT>::bars(smem);
 
   const int t = threadIdx.x, nx = g.nx, ny = g.ny;
-  const int x0 = blockIdx.x * TWC;
-  const int y0 = blockIdx.y * rows;
-  if (y0 >= ny) return;  // whole block
   const int y1 = min(y0 + rows, ny);
   const bool wall_l = g.bc[0] != BC_PERIODIC, wall_r = g.bc[1] != BC_PERIODIC;
   const bool wall_b = g.bc[2] != BC_PERIODIC, wall_t = g.bc[3] != BC_PERIODIC;
@@ -88,22 +122,17 @@ __global__ void __launch_bounds__(PR_THREADS) step_pr_kernel(
   const int rs = (y0 >= 1 || !wall_b) ? y0 - 1 : y0;
   const int re = (y1 < ny || !wall_t) ? y1 : y1 - 1;
   const int nq = re - rs + 1;
-  const S* __restrict__ src = static_cast<const S*>(g.src);
-  S* __restrict__ dst = static_cast<S*>(g.dst);
+  const S* __restrict__ src = static_cast<const S*>(src_v);
+  S* __restrict__ dst = static_cast<S*>(dst_v);
   const int pitch = g.pitch;
   const bool helper = t >= PR_COMPUTE;
   const int hl = t - PR_COMPUTE;  // helper lane
 
-  if (t == 0) {
-    for (int i = 0; i < D; ++i) mbar_init(bar_s + 8 * i, 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
   int issued = 0;  // staged rows issued so far (helper lane 0)
   auto issue_upto = [&](int kmax) {
     kmax = min(kmax, nq - 1);
     for (; issued <= kmax; ++issued) {
-      const int s = issued % D;
+      const int s = (kbase + issued) % D;
       const unsigned bar = bar_s + 8 * s;
       int nr = rs + issued;  // node row of this pulled row
       nr = nr < 0 ? nr + ny : (nr >= ny ? nr - ny : nr);
@@ -113,7 +142,7 @@ __global__ void __launch_bounds__(PR_THREADS) step_pr_kernel(
 #pragma unroll
         for (int b = 0; b < G::NB; ++b)
           tma_load_box(ring_s + (unsigned)((s * G::SLOT + (grp * G::NB + b) * G::GB) * sizeof(S)),
-                       &map, bar, x0 - 8 + b * G::BW + XOFF, 6 * grp, nr + grp);  // row nr-1+grp, +1
+                       map, bar, x0 - 8 + b * G::BW + XOFF, 6 * grp, nr + grp);  // row nr-1+grp, +1
     }
   };
   if (helper && hl == 0) issue_upto(D - 2);
@@ -165,8 +194,8 @@ __global__ void __launch_bounds__(PR_THREADS) step_pr_kernel(
     bool ok = true;
     const int k = r - rs;
     if (k >= 0 && k < nq) {
-      ok = mbar_wait(bar_s + 8 * (k % D), (k / D) & 1, WAIT_NS);
-      const S* slot = ring + (k % D) * G::SLOT;
+      ok = mbar_wait(bar_s + 8 * ((kbase + k) % D), ((kbase + k) / D) & 1, WAIT_NS);
+      const S* slot = ring + ((kbase + k) % D) * G::SLOT;
       int nr = r < 0 ? r + ny : (r >= ny ? r - ny : r);
 #pragma unroll
       for (int i = 0; i < NPT; ++i) {
@@ -203,7 +232,7 @@ __global__ void __launch_bounds__(PR_THREADS) step_pr_kernel(
     }
     const int ro = r - 1;
     if (!helper && ro >= y0) {
-      const S* slot = ring + ((k - 1) % D) * G::SLOT;  // pulled row ro (k - 1 >= 0)
+      const S* slot = ring + ((kbase + k - 1) % D) * G::SLOT;  // pulled row ro (k - 1 >= 0)
       const C* qprev = qxs + (qs ^ 1) * (TWC + 2);
       S* prow = dst + (long long)(ro + 1) * g.rp + XOFF;
 #pragma unroll
@@ -237,9 +266,9 @@ __global__ void __launch_bounds__(PR_THREADS) step_pr_kernel(
       if (helper && hl == 0) {
         if (g.status) atomicOr(g.status, 1);
         for (int j = max(k, 0); j < issued; ++j)
-          mbar_wait(bar_s + 8 * (j % D), (j / D) & 1, WAIT_NS / 4);
+          mbar_wait(bar_s + 8 * ((kbase + j) % D), ((kbase + j) / D) & 1, WAIT_NS / 4);
       }
-      return;
+      return 1;
     }
     // everyone is done with pulled row r - 1: refill its slot
     if (helper && hl == 0) issue_upto(k + D - 1);
@@ -255,6 +284,17 @@ __global__ void __launch_bounds__(PR_THREADS) step_pr_kernel(
     }
     qs ^= 1;
   }
+  return 0;
+}
+
+template <class S, int NPT, int M>
+__global__ void __launch_bounds__(PR_THREADS) step_pr_kernel(
+    const Grid g, const __grid_constant__ CUtensorMap map, int rows) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int y0 = blockIdx.y * rows;
+  if (y0 >= g.ny) return;  // whole block
+  pr_init<S, NPT>(smem);
+  pr_block<S, NPT, M>(g, &map, g.src, g.dst, blockIdx.x * PrGeom<S, NPT>::TWC, y0, rows, smem, 0);
 }
 
 }  // namespace lbm

@@ -80,6 +80,24 @@ def load() -> ctypes.CDLL:
         "lbm_destroy": (None, [_H]),
         "lbm_last_error": (ctypes.c_char_p, [_H]),
         "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "lbm_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                            ctypes.c_void_p, ctypes.POINTER(_H)]),
+        "lbm_batch_create_in": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                               ctypes.c_int64, ctypes.c_void_p,
+                                               ctypes.POINTER(_H)]),
+        "lbm_batch_add": (ctypes.c_int, [_H, P, _DP, _DP, _DP, _DP, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int32)]),
+        "lbm_batch_run": (ctypes.c_int, [_H, ctypes.c_int64]),
+        "lbm_batch_remaining": (ctypes.c_int64, [_H, ctypes.c_int32]),
+        "lbm_batch_moments": (ctypes.c_int, [_H, ctypes.c_int32, _DP, _DP, _DP, _DP]),
+        "lbm_batch_get_state": (ctypes.c_int, [_H, ctypes.c_int32, _DP]),
+        "lbm_batch_remove": (ctypes.c_int, [_H, ctypes.c_int32]),
+        "lbm_batch_autotune": (ctypes.c_int, [_H, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_int64)]),
+        "lbm_batch_set_schedule": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int32]),
+        "lbm_batch_info": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int64)]),
+        "lbm_batch_destroy": (None, [_H]),
+        "lbm_batch_last_error": (ctypes.c_char_p, [_H]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -280,3 +298,140 @@ class Lbm:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# ---- batched grids ------------------------------------------------------------
+
+def _bcheck(status: int, h=None):
+    if status != LBM_OK:
+        raise LbmError(status, load().lbm_batch_last_error(h).decode())
+
+
+def lbm_batch_create(precision: int, max_grids: int, pool_bytes: int, stream: int = 0):
+    h = _H()
+    _bcheck(load().lbm_batch_create(int(precision), int(max_grids), int(pool_bytes),
+                                    ctypes.c_void_p(stream or None), ctypes.byref(h)))
+    return h
+
+
+def lbm_batch_create_in(precision: int, max_grids: int, device_pool: int, pool_bytes: int,
+                        stream: int = 0):
+    h = _H()
+    _bcheck(load().lbm_batch_create_in(int(precision), int(max_grids), ctypes.c_void_p(device_pool),
+                                       int(pool_bytes), ctypes.c_void_p(stream or None),
+                                       ctypes.byref(h)))
+    return h
+
+
+def lbm_batch_add(h, params: dict, rho, ux, uy, T, steps: int) -> int:
+    shape = (int(params["ny"]), int(params["nx"]))
+    arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(v, dtype=np.float64), shape))
+            for v in (rho, ux, uy, T)]
+    slot = ctypes.c_int32(-1)
+    _bcheck(load().lbm_batch_add(h, ctypes.byref(make_params(params)), *[_dp(a) for a in arrs],
+                                 int(steps), ctypes.byref(slot)), h)
+    return int(slot.value)
+
+
+def lbm_batch_run(h, k: int):
+    _bcheck(load().lbm_batch_run(h, int(k)), h)
+
+
+def lbm_batch_remaining(h, slot: int) -> int:
+    r = int(load().lbm_batch_remaining(h, int(slot)))
+    if r < 0:
+        raise LbmError(r, "no such slot")
+    return r
+
+
+def lbm_batch_moments(h, slot: int, shape):
+    out = [np.empty(shape, dtype=np.float64) for _ in range(4)]
+    _bcheck(load().lbm_batch_moments(h, int(slot), *[_dp(a) for a in out]), h)
+    return tuple(out)
+
+
+def lbm_batch_get_state(h, slot: int, shape) -> np.ndarray:
+    out = np.empty((18,) + tuple(shape), dtype=np.float64)
+    _bcheck(load().lbm_batch_get_state(h, int(slot), _dp(out)), h)
+    return out
+
+
+def lbm_batch_remove(h, slot: int):
+    _bcheck(load().lbm_batch_remove(h, int(slot)), h)
+
+
+def lbm_batch_autotune(h, reps: int = 5):
+    out = (ctypes.c_int64 * 3)()
+    _bcheck(load().lbm_batch_autotune(h, int(reps), out), h)
+    return {"rows": int(out[0]), "dynamic": int(out[1]), "us_per_step": int(out[2])}
+
+
+def lbm_batch_set_schedule(h, rows: int, dynamic: int):
+    _bcheck(load().lbm_batch_set_schedule(h, int(rows), int(dynamic)), h)
+
+
+def lbm_batch_info(h) -> dict:
+    out = (ctypes.c_int64 * 6)()
+    _bcheck(load().lbm_batch_info(h, out), h)
+    keys = ("grids", "nodes", "free_bytes", "largest_free", "rows", "dynamic")
+    return {k: int(v) for k, v in zip(keys, out)}
+
+
+def lbm_batch_destroy(h):
+    if h:
+        load().lbm_batch_destroy(h)
+
+
+class Batch:
+    """Many grids advanced together (one launch per step for all of them)."""
+
+    def __init__(self, precision: int, max_grids: int, pool_bytes: int, stream: int = 0,
+                 device_pool: int | None = None):
+        if device_pool is None:
+            self.h = lbm_batch_create(precision, max_grids, pool_bytes, stream)
+        else:
+            self.h = lbm_batch_create_in(precision, max_grids, device_pool, pool_bytes, stream)
+        self.precision = precision
+        self.shapes = {}
+
+    def add(self, params: dict, fields, steps: int) -> int:
+        slot = lbm_batch_add(self.h, params, *fields, steps)
+        self.shapes[slot] = (int(params["ny"]), int(params["nx"]))
+        return slot
+
+    def run(self, k: int):
+        lbm_batch_run(self.h, k)
+        return self
+
+    def remaining(self, slot: int) -> int:
+        return lbm_batch_remaining(self.h, slot)
+
+    def moments(self, slot: int):
+        return lbm_batch_moments(self.h, slot, self.shapes[slot])
+
+    def pops(self, slot: int) -> np.ndarray:
+        return lbm_batch_get_state(self.h, slot, self.shapes[slot])
+
+    def remove(self, slot: int):
+        lbm_batch_remove(self.h, slot)
+        self.shapes.pop(slot, None)
+
+    def autotune(self, reps: int = 5) -> dict:
+        return lbm_batch_autotune(self.h, reps)
+
+    def set_schedule(self, rows: int, dynamic: int):
+        lbm_batch_set_schedule(self.h, rows, dynamic)
+
+    def info(self) -> dict:
+        return lbm_batch_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
