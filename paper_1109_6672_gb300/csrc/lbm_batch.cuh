@@ -48,45 +48,85 @@ __host__ __device__ constexpr int mode_slot(int m) {
                                                       : 7;
 }
 
+// Ring depth (0: as the single-grid kernel) and resident blocks per SM that
+// the register budget of the batched kernel is sized for.
+template <class S>
+__host__ __device__ constexpr int batch_depth() {
+  return 0;
+}
+template <class S>
+__host__ __device__ constexpr int batch_min_blocks() {
+  return sizeof(S) == 2 ? 4 : pr_min_blocks<S, 1>();
+}
 template <class S, int M>
-__global__ void __launch_bounds__(PR_THREADS, 4) batch_step_kernel(const BatchGrid* __restrict__ grids,
-                                                                const WorkItem* __restrict__ items,
-                                                                BatchCtl* ctl, int j) {
+__global__ void __launch_bounds__(PR_THREADS, (batch_min_blocks<S>()))
+    batch_step_kernel(const BatchGrid* __restrict__ grids, const WorkItem* __restrict__ items,
+                      BatchCtl* ctl, int j) {
   constexpr int MS = mode_slot(M);
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ int s_item;
   __shared__ Grid s_grid;
-  pr_init<S, 1>(smem);
+  constexpr int DD = batch_depth<S>();
+  pr_init<S, 1, DD>(smem);
   const int b0 = ctl->begin[MS], b1 = ctl->end[MS];
   const bool dyn = ctl->dynamic != 0;
-  int kbase = 0;
-  int it = b0 + blockIdx.x;
-  for (;;) {
-    if (dyn) {
-      if (threadIdx.x == 0) s_item = b0 + atomicAdd(&ctl->counters[MS][j], 1);
-      __syncthreads();
-      it = s_item;
+  // helper lane 0 issues the copies; it also takes the items from the queue,
+  // one ahead, so that the next item's first rows are staged early
+  const bool fetcher = threadIdx.x == PR_COMPUTE;
+  int rr = b0 + blockIdx.x;  // round-robin cursor
+  auto fetch = [&]() {       // next item of a grid that steps at j
+    for (;;) {
+      int it;
+      if (dyn) {
+        it = b0 + atomicAdd(&ctl->counters[MS][j], 1);
+      } else {
+        it = rr;
+        rr += gridDim.x;
+      }
+      if (it >= b1) return b1;
+      if (j < grids[items[it].grid].seg_steps) return it;
     }
+  };
+  int nxt = b1, pre = 0, kbase = 0;
+  if (fetcher) {
+    s_item = fetch();
+    nxt = s_item < b1 ? fetch() : b1;
+  }
+  __syncthreads();
+  for (;;) {
+    const int it = s_item;
     if (it >= b1) break;
     const WorkItem w = items[it];
     const BatchGrid& bg = grids[w.grid];
-    if (j < bg.seg_steps) {
-      // the grid descriptor in shared memory: uniform reads for the whole item
-      const int* gsrc = reinterpret_cast<const int*>(&bg.g);
-      int* gdst = reinterpret_cast<int*>(&s_grid);
-      for (int i = threadIdx.x; i < (int)(sizeof(Grid) / sizeof(int)); i += blockDim.x)
-        gdst[i] = gsrc[i];
-      __syncthreads();
-      const int par = (int)((bg.t0 + j) & 1);
-      const int st = pr_block<S, 1, M>(s_grid, &bg.maps[par], bg.buf[par], bg.buf[par ^ 1], w.x0,
-                                       w.y0, w.rows, smem, kbase);
-      kbase += pr_staged_rows(s_grid, w.y0, w.rows);
-      if (st) return;  // timeout recorded in the grid's status word
+    // the grid descriptor in shared memory: uniform reads for the whole item
+    const int* gsrc = reinterpret_cast<const int*>(&bg.g);
+    int* gdst = reinterpret_cast<int*>(&s_grid);
+    for (int i = threadIdx.x; i < (int)(sizeof(Grid) / sizeof(int)); i += blockDim.x)
+      gdst[i] = gsrc[i];
+    PrNext next{nullptr, 0, 0, 0, 0};
+    if (fetcher && nxt < b1) {
+      const WorkItem wn = items[nxt];
+      const BatchGrid& gn = grids[wn.grid];
+      next.map = &gn.maps[(int)((gn.t0 + j) & 1)];
+      next.x0 = wn.x0;
+      next.ny = gn.g.ny;
+      next.nq = pr_span(gn.g.ny, gn.g.bc[2] == BC_PERIODIC, gn.g.bc[3] == BC_PERIODIC, wn.y0,
+                        wn.rows, next.rs);
     }
-    if (dyn)
-      __syncthreads();  // everyone has read s_item (and s_grid) before they change
-    else
-      it += gridDim.x;
+    __syncthreads();
+    const int par = (int)((bg.t0 + j) & 1);
+    int pre_out = 0;
+    const int st = pr_block<S, 1, M, DD>(s_grid, &bg.maps[par], bg.buf[par], bg.buf[par ^ 1], w.x0,
+                                     w.y0, w.rows, smem, kbase, pre, next, &pre_out);
+    if (st) return;  // timeout recorded in the grid's status word
+    kbase += pr_staged_rows(s_grid, w.y0, w.rows);
+    // every thread passed the share's last barrier: s_item and s_grid are free
+    if (fetcher) {
+      s_item = nxt;
+      pre = pre_out;
+      nxt = nxt < b1 ? fetch() : b1;
+    }
+    __syncthreads();
   }
 }
 

@@ -278,8 +278,11 @@ __device__ __forceinline__ void put(const Grid& g, S* dst, int a, int x, int y,
 }
 
 // Ghost-slot writes of a boundary node (x, y): periodic copies and the wall
-// rules.  v[0..8] = f*, v[9..17] = h*, v[18..26] = h^eq of the node.
-template <class S>
+// rules.  v[0..8] = f*, v[9..17] = h*, v[18..26] = h^eq of the node.  A
+// population leaving through a corner takes the x side's rule when that side
+// is a wall, else the y side's.  SKIPX: the populations that leave through the
+// x sides (x wall or periodic in both directions) are written by xedge_writes.
+template <class S, bool SKIPX = false>
 __device__ __noinline__ void boundary_writes(const Grid& g, S* __restrict__ dst, int x, int y,
                                              const typename Io<S>::C* v,
                                              typename Io<S>::C rho, typename Io<S>::C ux,
@@ -297,6 +300,7 @@ __device__ __noinline__ void boundary_writes(const Grid& g, S* __restrict__ dst,
       side = ox;
     else if (oy >= 0 && g.bc[oy] != BC_PERIODIC)
       side = oy;
+    if (SKIPX && ox >= 0 && (side == ox || side < 0)) continue;
     if (side < 0) {
       // periodic: the node at wrap(d) pulls population a from wrap(d) - e_a
       const int wx = (dx + g.nx) % g.nx, wy = (dy + g.ny) % g.ny;
@@ -316,6 +320,97 @@ __device__ __noinline__ void boundary_writes(const Grid& g, S* __restrict__ dst,
     else
       hin = v[9 + a] + (hw[b] - hw[a]);
     put<S>(g, dst, 9 + b, dx, dy, hin);
+  }
+}
+
+// f^eq and h^eq of one direction e = (EX, EY) (same expressions as
+// `equilibria`).
+template <class C, int EX, int EY>
+__device__ __forceinline__ void eq_dir(C rho, C ux, C uy, C th, C b6, bool total, C& f, C& h) {
+  constexpr int e2 = EX * EX + EY * EY;
+  const C usq = ux * ux + uy * uy;
+  const C tm1 = th - C(1);
+  const C A0 = C(1) - C(1.5) * usq;
+  const C eu = C(EX) * ux + C(EY) * uy;
+  const C w = wgt<C>(e2 == 1 ? 1 : 5);
+  const C even = (e2 == 1 ? A0 + C(0.5) * tm1 : A0 + C(2) * tm1) + C(4.5) * eu * eu;
+  const C odd = (e2 == 1 ? C(3) - C(1.5) * tm1 : C(3) * th) * eu;
+  f = rho * w * (even + odd);
+  if (total) {
+    const C E = b6 * th + C(0.5) * usq;
+    const C p = rho * th * (C(1) / C(3));
+    const C he = (e2 == 1 ? C(-3) * usq + C(0.5) * th : C(-3) * usq + C(2) * th) + C(9) * eu * eu;
+    h = E * f + w * p * (he + C(3) * eu);
+  } else {
+    h = b6 * th * f;
+  }
+}
+
+// One population a leaving an x-edge node (x, y) through x side XS.  Wall:
+// f halfway bounce-back with the moving-wall term, h by the ghost-node
+// equilibrium (isothermal) or bounce-back (adiabatic), as in boundary_writes
+// but with the odd equilibrium parts written out for this direction alone.
+// Periodic x: the copy into the opposite ghost column, unless the population
+// also leaves through a y wall (boundary_writes takes it then).
+template <class S, int XS, int A>
+__device__ __forceinline__ void xedge_one(const Grid& g, S* __restrict__ dst, int x, int y,
+                                          const typename Io<S>::C* v, typename Io<S>::C rho,
+                                          typename Io<S>::C ux, typename Io<S>::C uy,
+                                          typename Io<S>::C th) {
+  using C = typename Io<S>::C;
+  constexpr int B = opp(A), EX = ex(A), EY = ey(A);
+  constexpr bool diag = EY != 0;
+  const int dx = x + EX, dy = y + EY;
+  if (g.bc[XS] != BC_PERIODIC) {
+    const Phys<C>& k = phys<C>(g);
+    const bool total = g.energy_model == E_TOTAL;
+    const C uwx = k.uw[XS][0], uwy = k.uw[XS][1];
+    const C euw = C(EX) * uwx + C(EY) * uwy;
+    const C w = wgt<C>(A);
+    const C lin = diag ? C(3) * th : C(3) - C(1.5) * (th - C(1));
+    const C fodd = rho * w * lin * euw;  // odd part of f^eq_A at (rho, u_w, theta)
+    put<S>(g, dst, B, dx, dy, v[A] - C(2) * fodd);
+    C hin;
+    if (g.bc[XS] == BC_ISO) {
+      const C thg = C(2) * k.thw[XS] - th;
+      C fg, hg;
+      eq_dir<C, ex(B), ey(B)>(rho * th / thg, C(2) * uwx - ux, C(2) * uwy - uy, thg, k.b6, total,
+                              fg, hg);
+      hin = hg + (v[9 + B] - v[18 + B]);
+    } else {
+      C hodd;  // odd part of h^eq_A at (rho, u_w, theta)
+      if (total) {
+        const C E = k.b6 * th + C(0.5) * (uwx * uwx + uwy * uwy);
+        hodd = E * fodd + w * (rho * th * (C(1) / C(3))) * C(3) * euw;
+      } else {
+        hodd = k.b6 * th * fodd;
+      }
+      hin = v[9 + A] - C(2) * hodd;
+    }
+    put<S>(g, dst, 9 + B, dx, dy, hin);
+    return;
+  }
+  if (EY != 0 && (dy < 0 || dy >= g.ny) && g.bc[dy < 0 ? 2 : 3] != BC_PERIODIC) return;
+  const int wx = (dx + g.nx) % g.nx, wy = (dy + g.ny) % g.ny;
+  put<S>(g, dst, A, wx - EX, wy - EY, v[A]);
+  put<S>(g, dst, 9 + A, wx - EX, wy - EY, v[9 + A]);
+}
+
+// Ghost-slot writes of the populations leaving an x-edge node through x side
+// XS (0: x = 0, populations 3, 6, 7; 1: x = nx - 1, populations 1, 5, 8).
+template <class S, int XS>
+__device__ __forceinline__ void xedge_writes(const Grid& g, S* __restrict__ dst, int x, int y,
+                                             const typename Io<S>::C* v, typename Io<S>::C rho,
+                                             typename Io<S>::C ux, typename Io<S>::C uy,
+                                             typename Io<S>::C th) {
+  if (XS == 0) {
+    xedge_one<S, 0, 3>(g, dst, x, y, v, rho, ux, uy, th);
+    xedge_one<S, 0, 6>(g, dst, x, y, v, rho, ux, uy, th);
+    xedge_one<S, 0, 7>(g, dst, x, y, v, rho, ux, uy, th);
+  } else {
+    xedge_one<S, 1, 1>(g, dst, x, y, v, rho, ux, uy, th);
+    xedge_one<S, 1, 5>(g, dst, x, y, v, rho, ux, uy, th);
+    xedge_one<S, 1, 8>(g, dst, x, y, v, rho, ux, uy, th);
   }
 }
 

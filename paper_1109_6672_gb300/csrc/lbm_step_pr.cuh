@@ -27,7 +27,8 @@ namespace lbm {
 constexpr int PR_COMPUTE = 128;              // compute threads per block
 constexpr int PR_THREADS = PR_COMPUTE + 32;  // plus the helper warp
 
-template <class S, int NPT>
+// DD: ring depth (0: 3 slots for FP64 storage, else 4).
+template <class S, int NPT, int DD = 0>
 struct PrGeom {
   static constexpr int TWC = PR_COMPUTE * NPT;  // output columns per block
   static constexpr int NB = NPT == 1 ? 1 : 2;   // boxes per plane group
@@ -35,7 +36,7 @@ struct PrGeom {
   static constexpr int GB =                     // elements per box (128 B aligned)
       (int)(((size_t)6 * BW * sizeof(S) + 127) / 128 * 128 / sizeof(S));
   static constexpr int SLOT = 3 * NB * GB;  // elements per pulled row
-  static constexpr int D = sizeof(S) == 8 ? 3 : 4;
+  static constexpr int D = DD ? DD : (sizeof(S) == 8 ? 3 : 4);
   static constexpr unsigned BOX_BYTES = 6 * BW * sizeof(S);
   static constexpr size_t smem_bytes() {
     return (size_t)D * SLOT * sizeof(S) + 2 * (TWC + 2) * sizeof(typename Io<S>::C) + D * 8;
@@ -65,10 +66,10 @@ __device__ __forceinline__ void pull_pr(const S* slot, const int co[3],
 }
 
 // Shared-memory layout of a block: ring slots, Q_x rows, mbarriers.
-template <class S, int NPT>
+template <class S, int NPT, int DD = 0>
 struct PrSmem {
   using C = typename Io<S>::C;
-  using G = PrGeom<S, NPT>;
+  using G = PrGeom<S, NPT, DD>;
   __device__ static S* ring(unsigned char* smem) { return reinterpret_cast<S*>(smem); }
   __device__ static C* qxs(unsigned char* smem) {
     return reinterpret_cast<C*>(smem + (size_t)G::D * G::SLOT * sizeof(S));
@@ -79,40 +80,61 @@ struct PrSmem {
 };
 
 // Initialise the ring's mbarriers (once per kernel, all threads call).
-template <class S, int NPT>
+template <class S, int NPT, int DD = 0>
 __device__ __forceinline__ void pr_init(unsigned char* smem) {
   if (threadIdx.x == 0) {
-    const unsigned bar_s = PrSmem<S, NPT>::bars(smem);
-    for (int i = 0; i < PrGeom<S, NPT>::D; ++i) mbar_init(bar_s + 8 * i, 1);
+    const unsigned bar_s = PrSmem<S, NPT, DD>::bars(smem);
+    for (int i = 0; i < PrGeom<S, NPT, DD>::D; ++i) mbar_init(bar_s + 8 * i, 1);
     mbar_fence_init();
   }
   __syncthreads();
 }
 
-// Rows staged by a block that owns rows [y0, y0 + rows) of grid g.
-__device__ __forceinline__ int pr_staged_rows(const Grid& g, int y0, int rows) {
-  const int y1 = min(y0 + rows, g.ny);
-  const int rs = (y0 >= 1 || g.bc[2] == BC_PERIODIC) ? y0 - 1 : y0;
-  const int re = (y1 < g.ny || g.bc[3] == BC_PERIODIC) ? y1 : y1 - 1;
+// Pulled rows staged by a block that owns rows [y0, y0 + rows) of a grid with
+// ny rows: rs .. rs + count - 1 (halo rows only where they hold nodes).
+__device__ __forceinline__ int pr_span(int ny, bool periodic_b, bool periodic_t, int y0, int rows,
+                                       int& rs) {
+  const int y1 = min(y0 + rows, ny);
+  rs = (y0 >= 1 || periodic_b) ? y0 - 1 : y0;
+  const int re = (y1 < ny || periodic_t) ? y1 : y1 - 1;
   return re - rs + 1;
 }
+
+__device__ __forceinline__ int pr_staged_rows(const Grid& g, int y0, int rows) {
+  int rs;
+  return pr_span(g.ny, g.bc[2] == BC_PERIODIC, g.bc[3] == BC_PERIODIC, y0, rows, rs);
+}
+
+// The share a block takes after the current one (persistent kernels): its
+// first pulled rows are staged while the current share finishes.  nq = 0:
+// no next share.
+struct PrNext {
+  const CUtensorMap* map;
+  int x0, rs, nq, ny;
+};
 
 // One block's share of a step: columns [x0, x0 + TWC), rows [y0, y0 + rows)
 // of grid g, reading the state at src through the tensor map `map` and
 // writing the next state to dst.  kbase counts the rows this block staged
-// before (ring slot and mbarrier phase continue across calls).  Returns 0, or
-// 1 if a staged row never arrived (after draining its own copies).
-template <class S, int NPT, int M>
+// before (ring slot and mbarrier phase continue across calls); `pre` of this
+// share's rows were already issued by the previous call, and once this share's
+// rows are all issued the copies run on into `next` (*pre_out: how many).
+// Only helper lane 0 issues copies, so pre / *pre_out matter in that thread
+// alone.  Returns 0, or 1 if a staged row never arrived (after draining its own
+// copies).
+template <class S, int NPT, int M, int DD = 0>
 __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, const void* src_v,
                                         void* dst_v, int x0, int y0, int rows, unsigned char* smem,
-                                        int kbase) {
+                                        int kbase, int pre = 0, PrNext next = PrNext{nullptr, 0, 0, 0, 0},
+                                        int* pre_out = nullptr) {
   using C = typename Io<S>::C;
-  using G = PrGeom<S, NPT>;
+  using G = PrGeom<S, NPT, DD>;
+  using SM = PrSmem<S, NPT, DD>;
   constexpr int D = G::D, TWC = G::TWC;
   constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
-  S* ring = PrSmem<S, NPT>::ring(smem);
-  C* qxs = PrSmem<S, NPT>::qxs(smem);
-  const unsigned ring_s = smem_u32(ring), bar_s = PrSmem<S, NPT>::bars(smem);
+  S* ring = SM::ring(smem);
+  C* qxs = SM::qxs(smem);
+  const unsigned ring_s = smem_u32(ring), bar_s = SM::bars(smem);
 
   const int t = threadIdx.x, nx = g.nx, ny = g.ny;
   const int y1 = min(y0 + rows, ny);
@@ -128,21 +150,26 @@ __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, c
   const bool helper = t >= PR_COMPUTE;
   const int hl = t - PR_COMPUTE;  // helper lane
 
-  int issued = 0;  // staged rows issued so far (helper lane 0)
+  // staged rows issued so far (helper lane 0), counted from this share's
+  // first row; indices >= nq are rows of the next share
+  int issued = pre;
   auto issue_upto = [&](int kmax) {
-    kmax = min(kmax, nq - 1);
+    kmax = min(kmax, nq + next.nq - 1);
     for (; issued <= kmax; ++issued) {
       const int s = (kbase + issued) % D;
       const unsigned bar = bar_s + 8 * s;
-      int nr = rs + issued;  // node row of this pulled row
-      nr = nr < 0 ? nr + ny : (nr >= ny ? nr - ny : nr);
+      const bool own = issued < nq;
+      const CUtensorMap* m = own ? map : next.map;
+      const int xs = own ? x0 : next.x0, yn = own ? ny : next.ny;
+      int nr = own ? rs + issued : next.rs + (issued - nq);  // node row of this pulled row
+      nr = nr < 0 ? nr + yn : (nr >= yn ? nr - yn : nr);
       mbar_expect_tx(bar, 3 * G::NB * G::BOX_BYTES);
 #pragma unroll
       for (int grp = 0; grp < 3; ++grp)
 #pragma unroll
         for (int b = 0; b < G::NB; ++b)
           tma_load_box(ring_s + (unsigned)((s * G::SLOT + (grp * G::NB + b) * G::GB) * sizeof(S)),
-                       map, bar, x0 - 8 + b * G::BW + XOFF, 6 * grp, nr + grp);  // row nr-1+grp, +1
+                       m, bar, xs - 8 + b * G::BW + XOFF, 6 * grp, nr + grp);  // row nr-1+grp, +1
     }
   };
   if (helper && hl == 0) issue_upto(D - 2);
@@ -253,11 +280,15 @@ __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, c
         C v[27];
         collide_m<S, M>(g, prow + c, pitch, d, prho[i], pux[i], puy[i], pth[i],
                         C(0.5) * (qxr - qxl), C(0.5) * (qyu - qyd), v);
-        if (c == 0 || ro == 0 || c == nx - 1 || ro == ny - 1) {
+        // ghost-slot writes: x edges inline (one thread of a warp), the edge
+        // rows (every thread of the row) through the general routine
+        if (c == 0) xedge_writes<S, 0>(g, dst, c, ro, v, prho[i], pux[i], puy[i], pth[i]);
+        if (c == nx - 1) xedge_writes<S, 1>(g, dst, c, ro, v, prho[i], pux[i], puy[i], pth[i]);
+        if (ro == 0 || ro == ny - 1) {
           C tmp[27];
 #pragma unroll
           for (int a = 0; a < 27; ++a) tmp[a] = v[a];
-          boundary_writes<S>(g, dst, c, ro, tmp, prho[i], pux[i], puy[i], pth[i]);
+          boundary_writes<S, true>(g, dst, c, ro, tmp, prho[i], pux[i], puy[i], pth[i]);
         }
       }
     }
@@ -284,11 +315,19 @@ __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, c
     }
     qs ^= 1;
   }
+  if (pre_out) *pre_out = max(issued - nq, 0);
   return 0;
 }
 
+// Resident blocks per SM that the register budget is sized for (the shared
+// memory of the ring allows as many): the rare wall branches may spill.
+template <class S, int NPT>
+__host__ __device__ constexpr int pr_min_blocks() {
+  return NPT != 1 ? 1 : (sizeof(S) == 8 ? 3 : (sizeof(S) == 4 ? 5 : 6));
+}
+
 template <class S, int NPT, int M>
-__global__ void __launch_bounds__(PR_THREADS) step_pr_kernel(
+__global__ void __launch_bounds__(PR_THREADS, (pr_min_blocks<S, NPT>())) step_pr_kernel(
     const Grid g, const __grid_constant__ CUtensorMap map, int rows) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int y0 = blockIdx.y * rows;
