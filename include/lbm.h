@@ -65,7 +65,10 @@ enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL_ISOTHERMAL = 1, LBM_BC_WALL_ADIABATIC = 
 enum { LBM_E_TOTAL = 0, LBM_E_INTERNAL = 1 };
 /* Storage / arithmetic: FP64 everywhere; FP32 everywhere; FP32 arithmetic with
  * populations stored as FP16 or BF16 deviations from the rest equilibrium
- * (rho = 1, u = 0, T = T0), T recovered and reductions accumulated in FP64. */
+ * (rho = 1, u = 0, T = T0), T recovered and reductions accumulated in FP64.
+ * The 16-bit stores of a time step round stochastically (zero-mean error;
+ * the random bits are a function of step, node and population only, see
+ * lbm_set_steps_done); FP16 holds 256 x the deviation. */
 enum { LBM_P_FP64 = 0, LBM_P_FP32 = 1, LBM_P_FP32_FP16 = 2, LBM_P_FP32_BF16 = 3 };
 
 typedef struct {
@@ -243,6 +246,15 @@ int lbm_sync(lbm_handle* h);
 
 /* Time steps taken since the last lbm_init() / lbm_set_state(). */
 int64_t lbm_steps_done(const lbm_handle* h);
+
+/* Sets the step counter (no counterpart in the paper).  The 16-bit storage
+ * precisions round every stored deviation stochastically with random bits
+ * drawn from (step counter, node, population), so a run resumed from a
+ * state saved with lbm_get_state() after t steps reproduces the
+ * uninterrupted run bit for bit only if the counter is set back to t after
+ * lbm_set_state().  Other precisions do not read it.  t < 0:
+ * LBM_ERR_PARAM. */
+int lbm_set_steps_done(lbm_handle* h, int64_t t);
 
 /* Step kernel and launch shape.  variant 0 or 1 (default): pulled-row
  * staging by the tensor memory accelerator (TMA), 128 columns per block;

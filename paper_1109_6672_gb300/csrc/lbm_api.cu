@@ -455,6 +455,7 @@ int lbm_step(lbm_handle* h, int64_t n) {
     Grid g = h->grid;
     g.src = buf_ptr(h, h->cur);
     g.dst = buf_ptr(h, 1 - h->cur);
+    g.t = (unsigned)h->steps;
     const CUtensorMap& map = h->maps[h->cur][npt - 1];
     cudaError_t e = cudaSuccess;
     dispatch(h->p.precision, [&](auto* tag) {
@@ -603,6 +604,13 @@ int lbm_sync(lbm_handle* h) {
 }
 
 int64_t lbm_steps_done(const lbm_handle* h) { return h ? h->steps : LBM_ERR_PARAM; }
+
+int lbm_set_steps_done(lbm_handle* h, int64_t t) {
+  if (!h) return LBM_ERR_PARAM;
+  if (t < 0) return fail(h, LBM_ERR_PARAM, "step count must be >= 0");
+  h->steps = t;
+  return LBM_OK;
+}
 
 int lbm_set_launch(lbm_handle* h, int32_t variant, int32_t rows_per_block) {
   if (!h) return LBM_ERR_PARAM;

@@ -56,7 +56,7 @@ __host__ __device__ constexpr int batch_depth() {
 }
 template <class S>
 __host__ __device__ constexpr int batch_min_blocks() {
-  return sizeof(S) == 2 ? 4 : pr_min_blocks<S, 1>();
+  return sizeof(S) == 8 ? 3 : 4;
 }
 template <class S, int M>
 __global__ void __launch_bounds__(PR_THREADS, (batch_min_blocks<S>()))
@@ -103,6 +103,8 @@ __global__ void __launch_bounds__(PR_THREADS, (batch_min_blocks<S>()))
     int* gdst = reinterpret_cast<int*>(&s_grid);
     for (int i = threadIdx.x; i < (int)(sizeof(Grid) / sizeof(int)); i += blockDim.x)
       gdst[i] = gsrc[i];
+    __syncthreads();
+    if (threadIdx.x == 0) s_grid.t = (unsigned)(bg.t0 + j);
     PrNext next{nullptr, 0, 0, 0, 0};
     if (fetcher && nxt < b1) {
       const WorkItem wn = items[nxt];

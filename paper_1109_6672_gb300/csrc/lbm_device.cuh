@@ -94,6 +94,7 @@ struct Grid {
   float fref[9], href[9];  // rest equilibria (deviation storage)
   double href_sum;         // sum of href in FP64
   int* status;             // device error word (bounded waits), may be NULL
+  unsigned t;              // time step being taken (stochastic rounding counter)
 };
 
 template <class C>
@@ -124,13 +125,27 @@ struct Io<float> {
   __device__ static float to(float v) { return v; }
   __device__ static float from(float v) { return v; }
 };
+// 16-bit deviations.  FP16 holds 256 x the deviation (an exact scaling that
+// moves deviations down to 2.4e-7 into the normal range; the largest, 255, is
+// far above any population).  from_sr() rounds stochastically with the 32
+// random bits r: up with probability equal to the dropped fraction of a
+// spacing, so the rounding error has zero mean (non-finite values and FP16
+// overflow round to nearest, so they stay non-finite).
 template <>
 struct Io<__half> {
   using C = float;
   static constexpr bool dev = true;
   __device__ static __half ld(const __half* p) { return __ldg(p); }
-  __device__ static float to(__half v) { return __half2float(v); }
-  __device__ static __half from(float v) { return __float2half_rn(v); }
+  __device__ static float to(__half v) { return __half2float(v) * (1.0f / 256.0f); }
+  __device__ static __half from(float v) { return __float2half_rn(v * 256.0f); }
+  __device__ static __half from_sr(float v, unsigned r) {
+    const float x = v * 256.0f;
+    if (!(fabsf(x) < 65504.0f)) return __float2half_rn(x);
+    // FP32 -> FP16 keeps 10 of 23 mantissa bits: add 13 random bits, cut
+    // them, and convert the now exactly representable value
+    const unsigned u = (__float_as_uint(x) + (r >> 19)) & 0xFFFFE000u;
+    return __float2half_rz(__uint_as_float(u));
+  }
 };
 template <>
 struct Io<__nv_bfloat16> {
@@ -139,7 +154,55 @@ struct Io<__nv_bfloat16> {
   __device__ static __nv_bfloat16 ld(const __nv_bfloat16* p) { return __ldg(p); }
   __device__ static float to(__nv_bfloat16 v) { return __bfloat162float(v); }
   __device__ static __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
+  __device__ static __nv_bfloat16 from_sr(float v, unsigned r) {
+    const unsigned u = __float_as_uint(v);
+    if ((u & 0x7F800000u) == 0x7F800000u) return __float2bfloat16_rn(v);
+    // BF16 is the upper half of FP32: add 16 random bits below it and cut
+    return __ushort_as_bfloat16((unsigned short)((u + (r >> 16)) >> 16));
+  }
 };
+
+// ---- random bits of the stochastic rounding --------------------------------
+// Round-to-nearest repeats the same rounding error at every step where the
+// flow is (nearly) steady, and those errors add up in the conserved moments;
+// stochastic rounding makes them cancel on average.  The random bits are a
+// counter-based function of (step, node, population), so results depend
+// neither on the launch shape nor on the other grids of a batch.
+constexpr unsigned SR_SEED = 0x2545F491u;
+
+__device__ __forceinline__ unsigned sr_hash(const Grid& g, int x, int y) {
+  unsigned h = ((unsigned)x * 0x9E3779B1u) ^ ((unsigned)y * 0x85EBCA77u) ^ (g.t * 0xC2B2AE3Du) ^
+               SR_SEED;
+  h ^= h >> 16;  // 32-bit integer finaliser (xor-shift-multiply)
+  h *= 0x7FEB352Du;
+  h ^= h >> 15;
+  h *= 0x846CA68Bu;
+  h ^= h >> 16;
+  return h;
+}
+
+// Random words of a node: the linear congruential sequence
+// x -> 1664525 x + 1013904223 (mod 2^32) started at the node's hash h.
+// Word k + 1 rounds stream k: population k (0..17) of the node's own stores;
+// 18 + a / 27 + a: wall values of f_a / h_a that the node writes into ghost
+// slots.  The node's own stores walk the sequence one multiply-add per value;
+// the rare ghost-slot writes step to word k + 1 directly.
+__device__ __forceinline__ unsigned lcg_next(unsigned r) { return r * 1664525u + 1013904223u; }
+__device__ __forceinline__ unsigned sr_bits(unsigned h, int k) {
+  unsigned r = h;
+  for (int i = 0; i <= k; ++i) r = lcg_next(r);
+  return r;
+}
+
+// Store of one value (deviation for 16-bit storage, rounded stochastically
+// with the random word r).
+template <class S>
+__device__ __forceinline__ S store_val(typename Io<S>::C v, unsigned r) {
+  if constexpr (Io<S>::dev)
+    return Io<S>::from_sr(v, r);
+  else
+    return Io<S>::from(v);
+}
 
 __device__ __forceinline__ long long slot(const Grid& g, int a, int x, int y) {
   return (long long)(y + 1) * g.rp + (long long)plane(a) * g.pitch + (x + XOFF);
@@ -169,11 +232,13 @@ __device__ __forceinline__ void pull(const Grid& g, const S* __restrict__ src, i
 // Moments of the pulled state: Eq. 35 with the force shift (text under
 // Eq. 51), and Eq. 37 (total energy) or 2 sum h / (rho b R) (Eq. 38 form).
 // Deviation storage recovers rho and theta in FP64 from the FP32 sums of the
-// deviations and the FP64 sum of the references.
+// deviations and the FP64 sum of the references.  Es = sum h / rho, the
+// specific energy the collision's h^eq carries (collision_equilibria).
 template <class S>
 __device__ __forceinline__ void moments(const Grid& g, const typename Io<S>::C d[NPOP],
                                         typename Io<S>::C& rho, typename Io<S>::C& ux,
-                                        typename Io<S>::C& uy, typename Io<S>::C& th) {
+                                        typename Io<S>::C& uy, typename Io<S>::C& th,
+                                        typename Io<S>::C& Es) {
   using C = typename Io<S>::C;
   C sf = 0, sh = 0;
 #pragma unroll
@@ -193,6 +258,7 @@ __device__ __forceinline__ void moments(const Grid& g, const typename Io<S>::C d
     ux = jx * inv;
     uy = (jy - C(0.5) * rho * k.g) * inv;
     double e = g.href_sum + (double)sh;
+    Es = (C)e * inv;
     if (g.energy_model == E_TOTAL) e -= 0.5 * (double)(rho * (ux * ux + uy * uy));
     th = k.six_b * (C)e * inv;
   } else {
@@ -200,11 +266,20 @@ __device__ __forceinline__ void moments(const Grid& g, const typename Io<S>::C d
     const C inv = C(1) / rho;
     ux = jx * inv;
     uy = (jy - C(0.5) * rho * k.g) * inv;
+    Es = sh * inv;
     if (g.energy_model == E_TOTAL)
-      th = k.six_b * (sh * inv - C(0.5) * (ux * ux + uy * uy));
+      th = k.six_b * (Es - C(0.5) * (ux * ux + uy * uy));
     else
-      th = k.six_b * sh * inv;
+      th = k.six_b * Es;
   }
+}
+
+template <class S>
+__device__ __forceinline__ void moments(const Grid& g, const typename Io<S>::C d[NPOP],
+                                        typename Io<S>::C& rho, typename Io<S>::C& ux,
+                                        typename Io<S>::C& uy, typename Io<S>::C& th) {
+  typename Io<S>::C Es;
+  moments<S>(g, d, rho, ux, uy, th, Es);
 }
 
 // f^eq (Eq. 18a, R T0 = 1/3, D = 2, third-order velocity term dropped) and
@@ -213,18 +288,23 @@ __device__ __forceinline__ void moments(const Grid& g, const typename Io<S>::C d
 //                     + 3/2 eu (th-1)(3 e^2 - 4)]
 //   h^eq_a = E f^eq_a + w_a p [3 eu + 9 eu^2 - 3 u^2 + th (3 e^2 - 2)/2],
 //   E = b th / 6 + u^2 / 2, p = rho th / 3.
+// Es is the specific energy the h^eq moment carries: E (total-energy model)
+// or b th / 6 (internal-energy model, h^eq = Es f^eq).
+//
+// In FP32 the rest populations are formed as the remainders of the moment
+// sums, f^eq_0 = rho - sum_{a>0} f^eq_a and h^eq_0 = rho Es - sum_{a>0} h^eq_a
+// (Eq. 19a/19b make this an identity): with the weights rounded to FP32 the
+// direct formula would miss sum f^eq = rho by a fixed 7e-9 relative, which
+// the collision would add to the mass (and energy) of every node at every
+// step.  FP64 keeps the direct formula.
 template <class C>
-__device__ __forceinline__ void equilibria(C rho, C ux, C uy, C th, C b6, bool total, C feq[9],
-                                           C heq[9]) {
+__device__ __forceinline__ void equilibria_es(C rho, C ux, C uy, C th, C Es, bool total, C feq[9],
+                                              C heq[9]) {
+  constexpr bool remainder = sizeof(C) == 4;
   const C usq = ux * ux + uy * uy;
   const C tm1 = th - C(1);
   const C A0 = C(1) - C(1.5) * usq;
-  const C E = b6 * th + C(0.5) * usq;
   const C p = rho * th * (C(1) / C(3));
-  // rest population
-  feq[0] = rho * wgt<C>(0) * (A0 - tm1);
-  const C pb = C(-3) * usq - th;  // bracket of h^eq at e = 0: -3u^2 + th(-2)/2
-  heq[0] = total ? E * feq[0] + wgt<C>(0) * p * pb : b6 * th * feq[0];
   // axis shell (e^2 = 1) and diagonal shell (e^2 = 2)
   const C base1 = A0 + C(0.5) * tm1, lin1 = C(3) - C(1.5) * tm1;
   const C base2 = A0 + C(2) * tm1, lin2 = C(3) * th;
@@ -243,13 +323,46 @@ __device__ __forceinline__ void equilibria(C rho, C ux, C uy, C th, C b6, bool t
     if (total) {
       const C he = (k < 2 ? hb1 : hb2) + C(9) * eu * eu;
       const C ho = C(3) * eu;
-      heq[a] = E * feq[a] + w * p * (he + ho);
-      heq[o] = E * feq[o] + w * p * (he - ho);
+      heq[a] = Es * feq[a] + w * p * (he + ho);
+      heq[o] = Es * feq[o] + w * p * (he - ho);
     } else {
-      heq[a] = b6 * th * feq[a];
-      heq[o] = b6 * th * feq[o];
+      heq[a] = Es * feq[a];
+      heq[o] = Es * feq[o];
     }
   }
+  // rest population
+  if constexpr (remainder) {
+    const C sf = ((feq[1] + feq[2]) + (feq[3] + feq[4])) + ((feq[5] + feq[6]) + (feq[7] + feq[8]));
+    const C sh = ((heq[1] + heq[2]) + (heq[3] + heq[4])) + ((heq[5] + heq[6]) + (heq[7] + heq[8]));
+    feq[0] = rho - sf;
+    heq[0] = rho * Es - sh;
+  } else {
+    feq[0] = rho * wgt<C>(0) * (A0 - tm1);
+    const C pb = C(-3) * usq - th;  // bracket of h^eq at e = 0: -3u^2 + th(-2)/2
+    heq[0] = total ? Es * feq[0] + wgt<C>(0) * p * pb : Es * feq[0];
+  }
+}
+
+// The same from theta alone (Es from b / 6).
+template <class C>
+__device__ __forceinline__ void equilibria(C rho, C ux, C uy, C th, C b6, bool total, C feq[9],
+                                           C heq[9]) {
+  const C Es = total ? b6 * th + C(0.5) * (ux * ux + uy * uy) : b6 * th;
+  equilibria_es<C>(rho, ux, uy, th, Es, total, feq, heq);
+}
+
+// Equilibria of the collision.  FP32: h^eq carries the specific energy Es
+// recovered from the node's own sum of h (rho Es = sum h), so that the
+// relaxation conserves energy to rounding; forming it from theta through
+// b / 6 and 6 / b (each rounded to FP32) would bias it by up to 2e-8
+// relative per step.  FP64: from theta.
+template <class C>
+__device__ __forceinline__ void collision_equilibria(C rho, C ux, C uy, C th, C Es, C b6,
+                                                     bool total, C feq[9], C heq[9]) {
+  if constexpr (sizeof(C) == 4)
+    equilibria_es<C>(rho, ux, uy, th, Es, total, feq, heq);
+  else
+    equilibria<C>(rho, ux, uy, th, b6, total, feq, heq);
 }
 
 // Wall equilibria: f^eq at (rho, u_w, theta) (halfway bounce-back term) and
@@ -273,8 +386,8 @@ __device__ void wall_equilibria(const Grid& g, int side, C rho, C ux, C uy, C th
 
 template <class S>
 __device__ __forceinline__ void put(const Grid& g, S* dst, int a, int x, int y,
-                                    typename Io<S>::C v) {
-  dst[slot(g, a, x, y)] = Io<S>::from(v - pref<S>(g, a));
+                                    typename Io<S>::C v, unsigned h, int k) {
+  dst[slot(g, a, x, y)] = store_val<S>(v - pref<S>(g, a), Io<S>::dev ? sr_bits(h, k) : 0u);
 }
 
 // Ghost-slot writes of a boundary node (x, y): periodic copies and the wall
@@ -290,6 +403,7 @@ __device__ __noinline__ void boundary_writes(const Grid& g, S* __restrict__ dst,
   using C = typename Io<S>::C;
   C fw[9], hw[9];
   int have = -1;
+  const unsigned hs = Io<S>::dev ? sr_hash(g, x, y) : 0u;
   for (int a = 1; a < 9; ++a) {
     const int dx = x + ex(a), dy = y + ey(a);
     const int ox = dx < 0 ? 0 : (dx >= g.nx ? 1 : -1);
@@ -304,8 +418,8 @@ __device__ __noinline__ void boundary_writes(const Grid& g, S* __restrict__ dst,
     if (side < 0) {
       // periodic: the node at wrap(d) pulls population a from wrap(d) - e_a
       const int wx = (dx + g.nx) % g.nx, wy = (dy + g.ny) % g.ny;
-      put<S>(g, dst, a, wx - ex(a), wy - ey(a), v[a]);
-      put<S>(g, dst, 9 + a, wx - ex(a), wy - ey(a), v[9 + a]);
+      put<S>(g, dst, a, wx - ex(a), wy - ey(a), v[a], hs, a);
+      put<S>(g, dst, 9 + a, wx - ex(a), wy - ey(a), v[9 + a], hs, 9 + a);
       continue;
     }
     if (have != side) {
@@ -313,13 +427,13 @@ __device__ __noinline__ void boundary_writes(const Grid& g, S* __restrict__ dst,
       have = side;
     }
     const int b = opp(a);  // reflected direction; node (x, y) pulls it from d
-    put<S>(g, dst, b, dx, dy, v[a] + (fw[b] - fw[a]));
+    put<S>(g, dst, b, dx, dy, v[a] + (fw[b] - fw[a]), hs, 18 + b);
     C hin;
     if (g.bc[side] == BC_ISO)
       hin = hw[b] + (v[9 + b] - v[18 + b]);
     else
       hin = v[9 + a] + (hw[b] - hw[a]);
-    put<S>(g, dst, 9 + b, dx, dy, hin);
+    put<S>(g, dst, 9 + b, dx, dy, hin, hs, 27 + b);
   }
 }
 
@@ -369,7 +483,8 @@ __device__ __forceinline__ void xedge_one(const Grid& g, S* __restrict__ dst, in
     const C w = wgt<C>(A);
     const C lin = diag ? C(3) * th : C(3) - C(1.5) * (th - C(1));
     const C fodd = rho * w * lin * euw;  // odd part of f^eq_A at (rho, u_w, theta)
-    put<S>(g, dst, B, dx, dy, v[A] - C(2) * fodd);
+    const unsigned hs = Io<S>::dev ? sr_hash(g, x, y) : 0u;
+    put<S>(g, dst, B, dx, dy, v[A] - C(2) * fodd, hs, 18 + B);
     C hin;
     if (g.bc[XS] == BC_ISO) {
       const C thg = C(2) * k.thw[XS] - th;
@@ -387,13 +502,14 @@ __device__ __forceinline__ void xedge_one(const Grid& g, S* __restrict__ dst, in
       }
       hin = v[9 + A] - C(2) * hodd;
     }
-    put<S>(g, dst, 9 + B, dx, dy, hin);
+    put<S>(g, dst, 9 + B, dx, dy, hin, hs, 27 + B);
     return;
   }
   if (EY != 0 && (dy < 0 || dy >= g.ny) && g.bc[dy < 0 ? 2 : 3] != BC_PERIODIC) return;
   const int wx = (dx + g.nx) % g.nx, wy = (dy + g.ny) % g.ny;
-  put<S>(g, dst, A, wx - EX, wy - EY, v[A]);
-  put<S>(g, dst, 9 + A, wx - EX, wy - EY, v[9 + A]);
+  const unsigned hs = Io<S>::dev ? sr_hash(g, x, y) : 0u;
+  put<S>(g, dst, A, wx - EX, wy - EY, v[A], hs, A);
+  put<S>(g, dst, 9 + A, wx - EX, wy - EY, v[9 + A], hs, 9 + A);
 }
 
 // Ghost-slot writes of the populations leaving an x-edge node through x side
@@ -421,13 +537,14 @@ __device__ __forceinline__ void collide_store(const Grid& g, S* __restrict__ dst
                                               const typename Io<S>::C d[NPOP],
                                               typename Io<S>::C rho, typename Io<S>::C ux,
                                               typename Io<S>::C uy, typename Io<S>::C th,
-                                              typename Io<S>::C dqx, typename Io<S>::C dqy) {
+                                              typename Io<S>::C Es, typename Io<S>::C dqx,
+                                              typename Io<S>::C dqy) {
   using C = typename Io<S>::C;
   const bool total = g.energy_model == E_TOTAL;
   const Phys<C>& k = phys<C>(g);
   const C wf = k.omega_f, wh = k.omega_h;
   C feq[9], heq[9];
-  equilibria<C>(rho, ux, uy, th, k.b6, total, feq, heq);
+  collision_equilibria<C>(rho, ux, uy, th, Es, k.b6, total, feq, heq);
 
   // C'_a = C_a + F_a
   C cc[9];
@@ -480,9 +597,12 @@ __device__ __forceinline__ void collide_store(const Grid& g, S* __restrict__ dst
     v[18 + a] = heq[a];
   }
   S* p = dst + slot(g, 0, x, y);
+  unsigned r = Io<S>::dev ? sr_hash(g, x, y) : 0u;
 #pragma unroll
-  for (int a = 0; a < NPOP; ++a)
-    p[(plane(a) - plane(0)) * g.pitch] = Io<S>::from(v[a] - pref<S>(g, a));
+  for (int a = 0; a < NPOP; ++a) {
+    if constexpr (Io<S>::dev) r = lcg_next(r);
+    p[(plane(a) - plane(0)) * g.pitch] = store_val<S>(v[a] - pref<S>(g, a), r);
+  }
   if (x == 0 || y == 0 || x == g.nx - 1 || y == g.ny - 1) {
     C tmp[27];
 #pragma unroll
@@ -536,7 +656,7 @@ __global__ void __launch_bounds__(256) step_kernel(const Grid g, int rows) {
   const bool wall_b = g.bc[2] != BC_PERIODIC, wall_t = g.bc[3] != BC_PERIODIC;
 
   C pd[NPOP];
-  C prho = 1, pux = 0, puy = 0, pth = 1, pqx = 0, pqy = 0, qymm = 0;
+  C prho = 1, pux = 0, puy = 0, pth = 1, pes = 0, pqx = 0, pqy = 0, qymm = 0;
 #pragma unroll
   for (int a = 0; a < NPOP; ++a) pd[a] = 0;
 
@@ -555,10 +675,10 @@ __global__ void __launch_bounds__(256) step_kernel(const Grid g, int rows) {
       nrow = 0;
     }
     C cd[NPOP];
-    C crho = 1, cux = 0, cuy = 0, cth = 1, cqx = 0, cqy = 0;
+    C crho = 1, cux = 0, cuy = 0, cth = 1, ces = 0, cqx = 0, cqy = 0;
     if (colv && rowv) {
       pull<S>(g, src, ncol, nrow, cd);
-      moments<S>(g, cd, crho, cux, cuy, cth);
+      moments<S>(g, cd, crho, cux, cuy, cth, ces);
       cqx = crho * cux * (C(1) - cth);
       cqy = crho * cuy * (C(1) - cth);
     } else {
@@ -575,7 +695,7 @@ __global__ void __launch_bounds__(256) step_kernel(const Grid g, int rows) {
           (c < nx - 1 || !wall_r) ? qxs[ps * NT + t + 1] : ghost_q<C>(g, 1, 0, prho, pth, pqx);
       const C qyu = (ro < ny - 1 || !wall_t) ? cqy : ghost_q<C>(g, 3, 1, prho, pth, pqy);
       const C qyd = (ro > 0 || !wall_b) ? qymm : ghost_q<C>(g, 2, 1, prho, pth, pqy);
-      collide_store<S>(g, dst, c, ro, pd, prho, pux, puy, pth, C(0.5) * (qxr - qxl),
+      collide_store<S>(g, dst, c, ro, pd, prho, pux, puy, pth, pes, C(0.5) * (qxr - qxl),
                        C(0.5) * (qyu - qyd));
     }
 #pragma unroll
@@ -585,6 +705,7 @@ __global__ void __launch_bounds__(256) step_kernel(const Grid g, int rows) {
     pux = cux;
     puy = cuy;
     pth = cth;
+    pes = ces;
     pqx = cqx;
     pqy = cqy;
     sl = sl == 2 ? 0 : sl + 1;

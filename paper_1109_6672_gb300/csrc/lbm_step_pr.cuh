@@ -202,20 +202,20 @@ __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, c
     }
   }
 
-  C prho[NPT], pux[NPT], puy[NPT], pth[NPT], pqx[NPT], pqy[NPT], qymm[NPT];
+  C prho[NPT], pux[NPT], puy[NPT], pth[NPT], pes[NPT], pqx[NPT], pqy[NPT], qymm[NPT];
 #pragma unroll
   for (int i = 0; i < NPT; ++i) {
     prho[i] = 1;
-    pux[i] = puy[i] = pqx[i] = pqy[i] = qymm[i] = 0;
+    pux[i] = puy[i] = pqx[i] = pqy[i] = qymm[i] = pes[i] = 0;
     pth[i] = 1;
   }
   int qs = 0;  // Q_x slot of the current row
   for (int r = y0 - 1; r <= y1; ++r) {
-    C crho[NPT], cux[NPT], cuy[NPT], cth[NPT], cqx[NPT], cqy[NPT];
+    C crho[NPT], cux[NPT], cuy[NPT], cth[NPT], ces[NPT], cqx[NPT], cqy[NPT];
 #pragma unroll
     for (int i = 0; i < NPT; ++i) {
       crho[i] = 1;
-      cux[i] = cuy[i] = cqx[i] = cqy[i] = 0;
+      cux[i] = cuy[i] = cqx[i] = cqy[i] = ces[i] = 0;
       cth[i] = 1;
     }
     bool ok = true;
@@ -243,7 +243,7 @@ __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, c
           pull_pr<S, NPT>(slot, co[i], d);
         else
           pull<S>(g, src, gx, nr, d);
-        moments_m<S, M>(g, d, crho[i], cux[i], cuy[i], cth[i]);
+        moments_m<S, M>(g, d, crho[i], cux[i], cuy[i], cth[i], ces[i]);
         cqx[i] = crho[i] * cux[i] * (C(1) - cth[i]);
         cqy[i] = crho[i] * cuy[i] * (C(1) - cth[i]);
       }
@@ -278,7 +278,7 @@ __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, c
         const C qyd =
             (ro > 0 || !wall_b) ? qymm[i] : ghost_q<C>(g, 2, 1, prho[i], pth[i], pqy[i]);
         C v[27];
-        collide_m<S, M>(g, prow + c, pitch, d, prho[i], pux[i], puy[i], pth[i],
+        collide_m<S, M>(g, prow + c, pitch, c, ro, d, prho[i], pux[i], puy[i], pth[i], pes[i],
                         C(0.5) * (qxr - qxl), C(0.5) * (qyu - qyd), v);
         // ghost-slot writes: x edges inline (one thread of a warp), the edge
         // rows (every thread of the row) through the general routine
@@ -310,6 +310,7 @@ __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, c
       pux[i] = cux[i];
       puy[i] = cuy[i];
       pth[i] = cth[i];
+      pes[i] = ces[i];
       pqx[i] = cqx[i];
       pqy[i] = cqy[i];
     }
@@ -323,7 +324,7 @@ __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, c
 // memory of the ring allows as many): the rare wall branches may spill.
 template <class S, int NPT>
 __host__ __device__ constexpr int pr_min_blocks() {
-  return NPT != 1 ? 1 : (sizeof(S) == 8 ? 3 : (sizeof(S) == 4 ? 5 : 6));
+  return NPT != 1 ? 1 : (sizeof(S) == 8 ? 3 : 5);
 }
 
 template <class S, int NPT, int M>

@@ -43,7 +43,8 @@ inline int mode_of(const Grid& g) {
 template <class S, int M>
 __device__ __forceinline__ void moments_m(const Grid& g, const typename Io<S>::C d[NPOP],
                                           typename Io<S>::C& rho, typename Io<S>::C& ux,
-                                          typename Io<S>::C& uy, typename Io<S>::C& th) {
+                                          typename Io<S>::C& uy, typename Io<S>::C& th,
+                                          typename Io<S>::C& Es) {
   using C = typename Io<S>::C;
   using MD = Mode<M>;
   const Phys<C>& k = phys<C>(g);
@@ -66,12 +67,15 @@ __device__ __forceinline__ void moments_m(const Grid& g, const typename Io<S>::C
   uy = jy * inv;
   if constexpr (Io<S>::dev) {
     double e = g.href_sum + (double)sh;
+    Es = (C)e * inv;
     if constexpr (MD::total) e -= 0.5 * (double)(rho * (ux * ux + uy * uy));
     th = k.six_b * (C)e * inv;
   } else if constexpr (MD::total) {
-    th = k.six_b * (sh * inv - C(0.5) * (ux * ux + uy * uy));
+    Es = sh * inv;
+    th = k.six_b * (Es - C(0.5) * (ux * ux + uy * uy));
   } else {
-    th = k.six_b * sh * inv;
+    Es = sh * inv;
+    th = k.six_b * Es;
   }
 }
 
@@ -79,17 +83,18 @@ __device__ __forceinline__ void moments_m(const Grid& g, const typename Io<S>::C
 // Eq. 49 plus the Guo force) of one node and its 18 stores at p (node slot,
 // population stride `pitch`).  v receives f*, h*, h^eq for the wall rules.
 template <class S, int M>
-__device__ __forceinline__ void collide_m(const Grid& g, S* __restrict__ p, int pitch,
+__device__ __forceinline__ void collide_m(const Grid& g, S* __restrict__ p, int pitch, int x, int y,
                                           const typename Io<S>::C d[NPOP], typename Io<S>::C rho,
                                           typename Io<S>::C ux, typename Io<S>::C uy,
-                                          typename Io<S>::C th, typename Io<S>::C dqx,
-                                          typename Io<S>::C dqy, typename Io<S>::C v[27]) {
+                                          typename Io<S>::C th, typename Io<S>::C Es,
+                                          typename Io<S>::C dqx, typename Io<S>::C dqy,
+                                          typename Io<S>::C v[27]) {
   using C = typename Io<S>::C;
   using MD = Mode<M>;
   const Phys<C>& k = phys<C>(g);
   const C wf = k.omega_f, wh = k.omega_h;
   C feq[9], heq[9];
-  equilibria<C>(rho, ux, uy, th, k.b6, MD::total, feq, heq);
+  collision_equilibria<C>(rho, ux, uy, th, Es, k.b6, MD::total, feq, heq);
 
   C cc[9];
 #pragma unroll
@@ -139,12 +144,11 @@ __device__ __forceinline__ void collide_m(const Grid& g, S* __restrict__ p, int 
     v[9 + a] = hs;
     v[18 + a] = heq[a];
   }
+  unsigned r = Io<S>::dev ? sr_hash(g, x, y) : 0u;
 #pragma unroll
   for (int a = 0; a < NPOP; ++a) {
-    if constexpr (Io<S>::dev)
-      p[plane(a) * pitch] = Io<S>::from(v[a] - pref<S>(g, a));
-    else
-      p[plane(a) * pitch] = Io<S>::from(v[a]);
+    if constexpr (Io<S>::dev) r = lcg_next(r);
+    p[plane(a) * pitch] = store_val<S>(v[a] - pref<S>(g, a), r);
   }
 }
 

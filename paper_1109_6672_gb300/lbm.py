@@ -76,6 +76,7 @@ def load() -> ctypes.CDLL:
         "lbm_set_state": (ctypes.c_int, [_H, _DP]),
         "lbm_sync": (ctypes.c_int, [_H]),
         "lbm_steps_done": (ctypes.c_int64, [_H]),
+        "lbm_set_steps_done": (ctypes.c_int, [_H, ctypes.c_int64]),
         "lbm_set_launch": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int32]),
         "lbm_destroy": (None, [_H]),
         "lbm_last_error": (ctypes.c_char_p, [_H]),
@@ -221,6 +222,10 @@ def lbm_steps_done(h) -> int:
     return int(load().lbm_steps_done(h))
 
 
+def lbm_set_steps_done(h, t: int):
+    _check(load().lbm_set_steps_done(h, int(t)), h)
+
+
 def lbm_set_launch(h, threads: int, rows_per_block: int = 0):
     _check(load().lbm_set_launch(h, int(threads), int(rows_per_block)), h)
 
@@ -270,8 +275,12 @@ class Lbm:
     def pops(self) -> np.ndarray:
         return lbm_get_state(self.h, self.shape)
 
-    def set_pops(self, pops: np.ndarray):
+    def set_pops(self, pops: np.ndarray, steps_done: int | None = None):
+        """Load a saved state; steps_done restores the step counter (it seeds
+        the stochastic rounding of the 16-bit precisions)."""
         lbm_set_state(self.h, pops)
+        if steps_done is not None:
+            lbm_set_steps_done(self.h, steps_done)
         return self
 
     def sync(self):

@@ -152,13 +152,14 @@ def test_launch_shape_does_not_change_result(precision):
         assert rel(results[fam], results["pr1"]) <= tol, fam
 
 
-@pytest.mark.parametrize("precision", [lbm.LBM_P_FP64, lbm.LBM_P_FP32, lbm.LBM_P_FP32_FP16])
+@pytest.mark.parametrize("precision", [lbm.LBM_P_FP64, lbm.LBM_P_FP32, lbm.LBM_P_FP32_FP16,
+                                       lbm.LBM_P_FP32_BF16])
 def test_checkpoint_resume_bitwise(precision):
     p, fields = make_case("couette_walls", precision)
     straight = lbm.Lbm(p).init(*fields).step(70).pops()
     a = lbm.Lbm(p).init(*fields).step(30)
     snap = a.pops()
-    b = lbm.Lbm(p).set_pops(snap).step(40)
+    b = lbm.Lbm(p).set_pops(snap, steps_done=a.steps_done).step(40)
     np.testing.assert_array_equal(b.pops(), straight)
 
 
