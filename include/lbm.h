@@ -247,6 +247,16 @@ int lbm_sync(lbm_handle* h);
 /* Time steps taken since the last lbm_init() / lbm_set_state(). */
 int64_t lbm_steps_done(const lbm_handle* h);
 
+/* Self-test of the bounded device-side waits (no counterpart in the paper).
+ * Launches one block on the current device that arms a shared-memory barrier
+ * for a transfer no copy ever completes and waits on it with the same bounded
+ * wait the step kernels use (limit_ns nanoseconds, 1e3 .. 2e9); the block then
+ * records the timeout in a status word and returns, as a step kernel does.
+ * Synchronous.  Returns LBM_ERR_TIMEOUT when the wait ran out (the expected
+ * result), LBM_OK if it did not, LBM_ERR_PARAM for a limit out of range (no
+ * device call is made then), LBM_ERR_OOM / LBM_ERR_CUDA on CUDA failures. */
+int lbm_selftest_wait(int64_t limit_ns);
+
 /* Sets the step counter (no counterpart in the paper).  The 16-bit storage
  * precisions round every stored deviation stochastically with random bits
  * drawn from (step counter, node, population), so a run resumed from a

@@ -77,6 +77,7 @@ def load() -> ctypes.CDLL:
         "lbm_sync": (ctypes.c_int, [_H]),
         "lbm_steps_done": (ctypes.c_int64, [_H]),
         "lbm_set_steps_done": (ctypes.c_int, [_H, ctypes.c_int64]),
+        "lbm_selftest_wait": (ctypes.c_int, [ctypes.c_int64]),
         "lbm_set_launch": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int32]),
         "lbm_destroy": (None, [_H]),
         "lbm_last_error": (ctypes.c_char_p, [_H]),
@@ -220,6 +221,11 @@ def lbm_sync(h):
 
 def lbm_steps_done(h) -> int:
     return int(load().lbm_steps_done(h))
+
+
+def lbm_selftest_wait(limit_ns: int) -> int:
+    """Status of the bounded-wait self-test (LBM_ERR_TIMEOUT expected)."""
+    return int(load().lbm_selftest_wait(int(limit_ns)))
 
 
 def lbm_set_steps_done(h, t: int):

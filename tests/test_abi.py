@@ -62,3 +62,9 @@ def test_state_bytes_and_validation_without_gpu(lib):
 def test_status_strings(lib):
     assert lbm.status_string(lbm.LBM_ERR_NONFINITE) == "LBM_ERR_NONFINITE"
     assert lbm.status_string(0) == "LBM_OK"
+
+
+def test_selftest_wait_validates_without_gpu(lib):
+    # out-of-range limits are rejected before any device call
+    assert lbm.lbm_selftest_wait(10) == lbm.LBM_ERR_PARAM
+    assert lbm.lbm_selftest_wait(3_000_000_000) == lbm.LBM_ERR_PARAM
