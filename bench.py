@@ -136,33 +136,58 @@ def oracle_glups(n_side: int, steps: int, threads: int):
     return n_side * n_side * steps / dt / 1e9, dt
 
 
+def reduce_max(value: float, dist, device) -> float:
+    """Largest value over the ranks (the job's time is the slowest rank's);
+    the value itself without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, nodes: int, steps: int, elapsed: float) -> float:
+    """Whole-job GLUPS: every rank advanced its own replica of `nodes` nodes
+    by `steps` steps within `elapsed` seconds (max over ranks)."""
+    return world * nodes * steps / elapsed / 1e9
+
+
 def run_reference(args, rank, world):
+    """The oracle as it stands on the host cores, on a side x side sample of
+    the benchmark workload (same recipe), W untimed and K timed steps; rank 0
+    only (other ranks of a multi-rank launch exit without work)."""
     if rank != 0:
-        return
+        return None
+    from oracle import oracle
+    from paper_1109_6672_gb300 import inputs
+
     cores = cpu_cores()
     side = args.ref_side
-    glups_per_step = []
-    for _ in range(args.warmup):
-        oracle_glups(side, 1, cores)
-    total_t = 0.0
-    for _ in range(args.steps):
-        g, dt = oracle_glups(side, 1, cores)
-        glups_per_step.append(g)
-        total_t += dt
+    p, fields = inputs.periodic_box(n=side, precision=inputs.P_FP64)
+    o = oracle.Oracle(p).init(*fields)
+    o.step(args.warmup, cores)
+    t0 = time.perf_counter()
+    o.step(args.steps, cores)
+    total_t = time.perf_counter() - t0
     value = side * side * args.steps / total_t / 1e9
+    sample = (f"{side}x{side} periodic box of the same recipe (seed 2), {args.steps} timed "
+              f"steps after {args.warmup} untimed, FP64, OpenMP over rows")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"periodic box {side}x{side} sample of the 4096x4096 box "
-                               "(FP64 CPU oracle, OpenMP over rows)",
-                   "nx": side, "ny": side},
+        "config": {"workload": f"periodic box {args.n}x{args.n}, coupled f+h D2Q9 BGK, total "
+                               "energy, correction on (FP64 CPU oracle on a bounded sample)",
+                   "nx": args.n, "ny": args.n, "sample_side": side},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{side}x{side} periodic box, {args.steps} timed steps"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return line
 
 
 def batch_and_serving(torch, args):
@@ -325,13 +350,11 @@ def run_ours(args, rank, world, local_rank):
     with ClockSampler(gpu_index) as clk:
         elapsed = time_steps(torch, lbm, g, stream, args.steps)
     torch.cuda.synchronize()
+    elapsed = reduce_max(elapsed, dist, "cuda")
     if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
         dist.barrier()
     nodes = n * n
-    value = world * nodes * args.steps / elapsed / 1e9
+    value = job_value(world, nodes, args.steps, elapsed)
     per_launch = elapsed / args.steps
     bpn = lbm.BYTES_PER_NODE_UPDATE[prec]
     hbm, peak_kind = peaks()
@@ -349,12 +372,8 @@ def run_ours(args, rank, world, local_rank):
     rc = lbm.load().lbm_moments(g.h, *[lbm._dp(t.numpy()) for t in out])
     if rc != 0:
         raise lbm.LbmError(rc, lbm.lbm_last_error(g.h))
-    e2e_t = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_t], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e_value = world * nodes * e2e_steps / e2e_t / 1e9
+    e2e_t = reduce_max(time.perf_counter() - t0, dist, "cuda")
+    e2e_value = job_value(world, nodes, e2e_steps, e2e_t)
 
     variants = {}
     if args.variants and world == 1:
