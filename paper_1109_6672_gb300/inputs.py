@@ -95,15 +95,17 @@ def cavity_gravity(H: int, dT_over_T0: float, Ma: float = 0.1, strat: float = 0.
 
 def cavity(n: int = 256, Ra: float = 1e5, Pr: float = 0.71, dT_over_T0: float = 0.01,
            seed: int = 1, noise: float = 1e-4, b: float = 5.0, precision: int = P_FP64,
-           nu_min: float = 0.0, **kw):
+           nu_min: float = 0.0, strat: float = 0.05, **kw):
     """Differentially heated square cavity (natural convection): hot wall at
     x-, cold wall at x+ (isothermal, T0 (1 +- dT/2)), adiabatic top and bottom,
     internal-energy model (Eq. 38), gravity a = (0, -rho g), b = 5
     (gamma = 1.4).  Ra = g beta dT H^3 Pr / nu^2 with beta = 1/T0 (Eq. 57-58),
     hence nu = sqrt(g (dT/T0) H^3 Pr / Ra).  ``nu_min`` floors nu (lowering the
-    effective Ra) for under-resolved members of a batch."""
+    effective Ra) for under-resolved members of a batch.  ``strat`` caps the
+    hydrostatic stratification g H / (R T0); near the Boussinesq limit it has
+    to be small against dT/T0 (0.05 dT/T0 keeps its effect on Nu below 1 %)."""
     H = n
-    g = cavity_gravity(H, dT_over_T0)
+    g = cavity_gravity(H, dT_over_T0, strat=strat)
     nu = math.sqrt(g * dT_over_T0 * H ** 3 * Pr / Ra)
     nu = max(nu, nu_min)
     tau_f = nu / RT0
