@@ -299,6 +299,55 @@ def batch_and_serving(torch, args):
     return out
 
 
+def large_dT_study(torch, args):
+    """Large-dT cavity (1024^2, dT/T0 = 0.6, Ra = 1e6, Pr = 0.71, noise 1e-4,
+    seed 3): FP32 storage and FP16 / BF16 deviation storage against FP64 after
+    `args.config3_steps` steps: max and L2 error of u and T, and the mean
+    wall heat flux (Nusselt number at both walls).  The FP64 run is the CUDA
+    FP64 path (the tests hold it to 1e-12 of the oracle, which is too slow for
+    this size)."""
+    from paper_1109_6672_gb300 import inputs, lbm
+
+    n, steps = 1024, args.config3_steps
+
+    def wall_nu(p, T):
+        Th, Tl = p["T_wall"][0], p["T_wall"][1]
+        cold = ((9 * T[:, -1] - T[:, -2] - 8 * Tl) / 3).mean() * n / (Th - Tl)
+        hot = (-(9 * T[:, 0] - T[:, 1] - 8 * Th) / 3).mean() * n / (Th - Tl)
+        return float(hot), float(cold)
+
+    out = {"grid": f"{n}x{n}", "dT_over_T0": 0.6, "Ra": 1e6, "steps": steps}
+    ref = None
+    for name, q in (("f64", lbm.LBM_P_FP64), ("f32", lbm.LBM_P_FP32),
+                    ("f16", lbm.LBM_P_FP32_FP16), ("bf16", lbm.LBM_P_FP32_BF16)):
+        p, f = inputs.cavity(n=n, Ra=1e6, dT_over_T0=0.6, seed=3, precision=q)
+        g = lbm.Lbm(p).init(*f)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.step(steps)
+        mom = g.moments()
+        dt = time.perf_counter() - t0
+        g.close()
+        hot, cold = wall_nu(p, mom[3])
+        rec = {"seconds": dt, "glups": n * n * steps / dt / 1e9, "Nu_hot": hot, "Nu_cold": cold}
+        if ref is None:
+            ref = mom
+        else:
+            rho0, ux0, uy0, T0_ = ref
+            rho, ux, uy, T = mom
+            du = np.sqrt((ux - ux0) ** 2 + (uy - uy0) ** 2)
+            umax = float(np.sqrt(ux0 ** 2 + uy0 ** 2).max())
+            rec.update({
+                "T_max_rel": float(np.abs(T - T0_).max() / np.abs(T0_).max()),
+                "T_l2_rel": float(np.sqrt(np.mean((T - T0_) ** 2) / np.mean(T0_ ** 2))),
+                "u_max_over_umax": float(du.max() / umax),
+                "u_l2_over_umax": float(np.sqrt(np.mean(du ** 2)) / umax),
+                "Nu_cold_rel": abs(cold - out["f64"]["Nu_cold"]) / abs(out["f64"]["Nu_cold"]),
+            })
+        out[name] = rec
+    return out
+
+
 def time_steps(torch, lbm_mod, g, stream, steps):
     """CUDA-event time of `steps` back-to-back step launches on `stream`."""
     e0 = torch.cuda.Event(enable_timing=True)
@@ -402,6 +451,8 @@ def run_ours(args, rank, world, local_rank):
     extra = {}
     if rank == 0 and world == 1 and args.batch:
         extra = batch_and_serving(torch, args)
+    if rank == 0 and world == 1 and args.config3_steps > 0:
+        extra["large_dT_cavity"] = large_dT_study(torch, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -468,6 +519,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--batch-err-grids", type=int, default=4)
     ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--config3-steps", type=int, default=0,
+                    help="run the large-dT cavity precision study for this many steps")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
