@@ -58,6 +58,7 @@ static const double DIM = 2.0; /* D */
 
 enum { ORC_PERIODIC = 0, ORC_WALL_ISOTHERMAL = 1, ORC_WALL_ADIABATIC = 2 };
 enum { ORC_E_TOTAL = 0, ORC_E_INTERNAL = 1 };
+enum { ORC_BGK = 0, ORC_MRT = 1 };
 
 typedef struct {
   int32_t nx, ny;
@@ -70,6 +71,8 @@ typedef struct {
   int32_t energy_model;
   int32_t correction;
   int32_t z_full;
+  int32_t collision;        /* ORC_BGK: Eq. 34; ORC_MRT: Eqs. 43-45 */
+  double s_e, s_eps, s_q;   /* MRT rates of e, epsilon, q in S (Eq. 40); 0: omega_f */
 } orc_params;
 
 typedef struct {
@@ -136,6 +139,55 @@ void orc_force(double RT0, double ux, double uy, double ax, double ay, double ou
     double ua_ee = (EX[a] * ux + EY[a] * uy) * ea; /* (u.e)(e.a) */
     double ua = ux * ax + uy * ay;
     out[a] = W[a] * (ea / RT0 + (ua_ee - RT0 * ua) / (RT0 * RT0));
+  }
+}
+
+/* Appendix B: the D2Q9 transformation matrix M (B1), moments in the order
+ * (rho, e, epsilon, j_x, q_x, j_y, q_y, p_xx, p_xy), and its inverse (B2). */
+static const double MRT_M[9][9] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1},       {-4, -1, -1, -1, -1, 2, 2, 2, 2},
+    {4, -2, -2, -2, -2, 1, 1, 1, 1},   {0, 1, 0, -1, 0, 1, -1, -1, 1},
+    {0, -2, 0, 2, 0, 1, -1, -1, 1},    {0, 0, 1, 0, -1, 1, 1, -1, -1},
+    {0, 0, -2, 0, 2, 1, 1, -1, -1},    {0, 1, -1, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+static const double MRT_MINV[9][9] = {
+    {1. / 9, -1. / 9, 1. / 9, 0, 0, 0, 0, 0, 0},
+    {1. / 9, -1. / 36, -1. / 18, 1. / 6, -1. / 6, 0, 0, 1. / 4, 0},
+    {1. / 9, -1. / 36, -1. / 18, 0, 0, 1. / 6, -1. / 6, -1. / 4, 0},
+    {1. / 9, -1. / 36, -1. / 18, -1. / 6, 1. / 6, 0, 0, 1. / 4, 0},
+    {1. / 9, -1. / 36, -1. / 18, 0, 0, -1. / 6, 1. / 6, -1. / 4, 0},
+    {1. / 9, 1. / 18, 1. / 36, 1. / 6, 1. / 12, 1. / 6, 1. / 12, 0, 1. / 4},
+    {1. / 9, 1. / 18, 1. / 36, -1. / 6, -1. / 12, 1. / 6, 1. / 12, 0, -1. / 4},
+    {1. / 9, 1. / 18, 1. / 36, -1. / 6, -1. / 12, -1. / 6, -1. / 12, 0, 1. / 4},
+    {1. / 9, 1. / 18, 1. / 36, 1. / 6, 1. / 12, -1. / 6, -1. / 12, 0, -1. / 4}};
+
+void orc_mrt_matrices(double M[81], double Minv[81]) {
+  for (int r = 0; r < 9; ++r)
+    for (int c = 0; c < 9; ++c) {
+      M[9 * r + c] = MRT_M[r][c];
+      Minv[9 * r + c] = MRT_MINV[r][c];
+    }
+}
+
+/* Eq. 41: the moment-space equilibria of the coupled model. */
+void orc_meq(double rho, double ux, double uy, double theta, double out[9]) {
+  double usq = ux * ux + uy * uy;
+  out[0] = rho;
+  out[1] = rho * (-4.0 + 3.0 * usq + 2.0 * theta);
+  out[2] = rho * (3.0 - 3.0 * usq - 2.0 * theta);
+  out[3] = rho * ux;
+  out[4] = rho * (-2.0 * ux + ux * theta);
+  out[5] = rho * uy;
+  out[6] = rho * (-2.0 * uy + uy * theta);
+  out[7] = rho * (ux * ux - uy * uy);
+  out[8] = rho * ux * uy;
+}
+
+static void matvec9(const double A[9][9], const double v[9], double out[9]) {
+  for (int r = 0; r < 9; ++r) {
+    double acc = 0.0;
+    for (int c = 0; c < 9; ++c) acc += A[r][c] * v[c];
+    out[r] = acc;
   }
 }
 
@@ -305,17 +357,43 @@ static void phase2(orc_state* s, int nthreads) {
         orc_heq_internal(RT0, p->b, th, feq, heq);
       }
 
-      /* Collision: Eq. 34 (f, "+(1 - w_f/2) C" from Eqs. 32-33) and Eq. 36 or
-       * Eq. 38 (h). */
+      /* Collision of f.  BGK: Eq. 34 ("+(1 - w_f/2) C" from Eqs. 32-33).  MRT:
+       * Eq. 44 in moment space with m = M f (the stored f is f-hat of
+       * Eq. 43), m^eq of Eq. 41, C-hat = M C and S of Eq. 40; the shear rate
+       * 1/tau_f of Eq. 40 is omega_f (the discrete MRT time is the
+       * continuous tau_f plus 1/2, mu = (tau - 1/2) p), tau_rho = tau_j = 1
+       * (the rates of conserved moments drop out); then f* = M^-1 m*. */
       double fs[9], hs[9];
+      if (p->collision == ORC_MRT) {
+        double fh[9], m[9], meq[9], Ch[9], ms[9];
+        double S[9] = {1.0, p->s_e > 0 ? p->s_e : wf, p->s_eps > 0 ? p->s_eps : wf, 1.0,
+                       p->s_q > 0 ? p->s_q : wf, 1.0, p->s_q > 0 ? p->s_q : wf, wf, wf};
+        for (int a = 0; a < 9; ++a) fh[a] = s->f[a][i];
+        matvec9(MRT_M, fh, m);
+        orc_meq(rho, ux, uy, th, meq);
+        matvec9(MRT_M, C, Ch);
+        for (int k = 0; k < 9; ++k) ms[k] = m[k] - S[k] * (m[k] - meq[k]) + (1.0 - 0.5 * S[k]) * Ch[k];
+        matvec9(MRT_MINV, ms, fs);
+      } else {
+        for (int a = 0; a < 9; ++a) {
+          double fa = s->f[a][i];
+          fs[a] = fa - wf * (fa - feq[a]) + (1.0 - 0.5 * wf) * C[a];
+        }
+      }
+      /* Collision of h: Eq. 36 (BGK) or Eq. 47 (MRT), or Eq. 38 (internal
+       * energy, no coupling).  The Eq. 47 coupling (1 - w_h/2) Z / tau_hf
+       * with tau_hf = tau/(Pr - 1), tau = tau_f + 1/2 the discrete MRT time
+       * and Pr = (tau - 1/2)/tau_h. */
+      const double kz = p->collision == ORC_MRT
+                            ? (1.0 - 0.5 * wh) * (p->tau_f / p->tau_h - 1.0) / (p->tau_f + 0.5)
+                            : wh - wf;
       for (int a = 0; a < 9; ++a) {
         double fa = s->f[a][i], ha = s->h[a][i];
-        fs[a] = fa - wf * (fa - feq[a]) + (1.0 - 0.5 * wf) * C[a];
         hs[a] = ha - wh * (ha - heq[a]);
         if (p->energy_model == ORC_E_TOTAL) {
           double eu = EX[a] * ux + EY[a] * uy;
           double Z = p->z_full ? eu - 0.5 * usq : eu;
-          hs[a] += (wh - wf) * Z * (fa - feq[a] + 0.5 * C[a]);
+          hs[a] += kz * Z * (fa - feq[a] + 0.5 * C[a]);
         }
       }
 

@@ -24,6 +24,7 @@ LIB = BUILD / "liblbm_oracle.so"
 
 PERIODIC, WALL_ISOTHERMAL, WALL_ADIABATIC = 0, 1, 2
 E_TOTAL, E_INTERNAL = 0, 1
+BGK, MRT = 0, 1
 
 
 class OrcParams(ctypes.Structure):
@@ -44,6 +45,10 @@ class OrcParams(ctypes.Structure):
         ("energy_model", ctypes.c_int32),
         ("correction", ctypes.c_int32),
         ("z_full", ctypes.c_int32),
+        ("collision", ctypes.c_int32),
+        ("s_e", ctypes.c_double),
+        ("s_eps", ctypes.c_double),
+        ("s_q", ctypes.c_double),
     ]
 
 
@@ -85,6 +90,8 @@ def lib() -> ctypes.CDLL:
         _lib.orc_correction.argtypes = [ctypes.c_double, ctypes.c_double, dp]
         _lib.orc_force.argtypes = [ctypes.c_double] * 5 + [dp]
         _lib.orc_param_size.restype = ctypes.c_int
+        _lib.orc_meq.argtypes = [ctypes.c_double] * 4 + [dp]
+        _lib.orc_mrt_matrices.argtypes = [dp, dp]
         assert _lib.orc_param_size() == ctypes.sizeof(OrcParams)
     return _lib
 
@@ -109,6 +116,8 @@ def make_params(p: dict) -> OrcParams:
     o.energy_model = int(p.get("energy_model", E_TOTAL))
     o.correction = int(p.get("correction", 1))
     o.z_full = int(p.get("z_full", 1))
+    o.collision = int(p.get("collision", BGK))
+    o.s_e, o.s_eps, o.s_q = (float(p.get(k, 0.0)) for k in ("s_e", "s_eps", "s_q"))
     return o
 
 
@@ -144,6 +153,20 @@ def force(RT0, ux, uy, ax, ay) -> np.ndarray:
     out = np.zeros(9)
     lib().orc_force(RT0, ux, uy, ax, ay, _dp(out))
     return out
+
+
+def meq(rho, ux, uy, theta) -> np.ndarray:
+    """Eq. 41: moment-space equilibria (rho, e, eps, jx, qx, jy, qy, pxx, pxy)."""
+    out = np.zeros(9)
+    lib().orc_meq(rho, ux, uy, theta, _dp(out))
+    return out
+
+
+def mrt_matrices():
+    """The oracle's Appendix B matrices M (B1) and M^-1 (B2)."""
+    M, Minv = np.zeros(81), np.zeros(81)
+    lib().orc_mrt_matrices(_dp(M), _dp(Minv))
+    return M.reshape(9, 9), Minv.reshape(9, 9)
 
 
 # ---- whole-grid state ------------------------------------------------------

@@ -7,7 +7,10 @@ different routes to the same quantities:
   being evaluated from the generic Hermite form;
 * moments use array contractions;
 * streaming is pull-based (``np.roll``), and the wall rules are applied from the
-  receiving node's side instead of the sending node's side.
+  receiving node's side instead of the sending node's side;
+* for the MRT scheme (Sec. III.C.2) the moment basis is built from its
+  defining polynomials of the velocity set and inverted numerically, and
+  m^eq is M f^eq rather than Eq. 41.
 """
 from __future__ import annotations
 
@@ -18,6 +21,12 @@ EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
 OPP = np.array([0, 3, 4, 1, 2, 7, 8, 5, 6])
 W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
 PERIODIC, ISO, ADIA = 0, 1, 2
+
+# moments rho, e, eps, jx, qx, jy, qy, pxx, pxy as polynomials of e_a
+_E2 = EX * EX + EY * EY
+MB = np.array([np.ones(9), 3 * _E2 - 4, (9 * _E2 ** 2 - 21 * _E2 + 8) / 2, EX, (3 * _E2 - 5) * EX,
+               EY, (3 * _E2 - 5) * EY, EX * EX - EY * EY, EX * EY], float)
+MB_INV = np.linalg.inv(MB)
 
 
 def feq_shells(rho, ux, uy, th):
@@ -136,13 +145,25 @@ class Brute:
             heq = heq_internal(th, p["b"], feq)
         wf = 1 / (p["tau_f"] + 0.5)
         wh = 1 / (p["tau_h"] + 0.5)
-        fs = self.F + wf * (feq - self.F) + (1 - wf / 2) * C
+        if p.get("collision", 0) == 1:
+            # rates: conserved moments 1, e / eps / q as given (0: omega_f), shear omega_f
+            r = [p.get(k, 0.0) or wf for k in ("s_e", "s_eps", "s_q")]
+            S = np.array([1, r[0], r[1], 1, r[2], 1, r[2], wf, wf])[:, None, None]
+            m = np.tensordot(MB, self.F, 1)
+            meq = np.tensordot(MB, feq, 1)
+            Ch = np.tensordot(MB, C, 1)
+            fs = np.tensordot(MB_INV, m - S * (m - meq) + (1 - S / 2) * Ch, 1)
+            # Eq. 47: (1 - w_h/2) Z / tau_hf, tau_hf = (tau_f + 1/2)/(Pr - 1)
+            kz = (1 - wh / 2) * (p["tau_f"] / p["tau_h"] - 1) / (p["tau_f"] + 0.5)
+        else:
+            fs = self.F + wf * (feq - self.F) + (1 - wf / 2) * C
+            kz = wh - wf
         hs = self.H + wh * (heq - self.H)
         if p["energy_model"] == 0:
             for a in range(9):
                 eu = EX[a] * ux + EY[a] * uy
                 Z = eu - 0.5 * usq if p["z_full"] else eu
-                hs[a] += (wh - wf) * Z * (self.F[a] - feq[a] + 0.5 * C[a])
+                hs[a] += kz * Z * (self.F[a] - feq[a] + 0.5 * C[a])
         # pull streaming with wrap, then overwrite wall-crossing pulls
         Fn = np.empty_like(fs)
         Hn = np.empty_like(hs)
