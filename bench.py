@@ -426,12 +426,14 @@ def run_ours(args, rank, world, local_rank):
 
     variants = {}
     if args.variants and world == 1:
-        for name, pv in (("f64", lbm.LBM_P_FP64), ("f16dev", lbm.LBM_P_FP32_FP16),
-                         ("bf16dev", lbm.LBM_P_FP32_BF16)):
-            if pv == prec:
+        for name, pv, opts in (("f64", lbm.LBM_P_FP64, {}), ("f16dev", lbm.LBM_P_FP32_FP16, {}),
+                                ("bf16dev", lbm.LBM_P_FP32_BF16, {}),
+                                ("mrt_f32", lbm.LBM_P_FP32,
+                                 dict(collision=lbm.LBM_COLL_MRT, s_e=1.3, s_eps=1.1, s_q=1.6))):
+            if pv == prec and not opts:
                 continue
             g.close()
-            pp = dict(p, precision=pv)
+            pp = dict(p, precision=pv, **opts)
             gv = lbm.Lbm(pp, stream=stream.cuda_stream)
             with torch.cuda.stream(stream):
                 lbm.lbm_init_device(gv.h, *[t.data_ptr() for t in dev_fields])

@@ -70,6 +70,11 @@ enum { LBM_E_TOTAL = 0, LBM_E_INTERNAL = 1 };
  * the random bits are a function of step, node and population only, see
  * lbm_set_steps_done); FP16 holds 256 x the deviation. */
 enum { LBM_P_FP64 = 0, LBM_P_FP32 = 1, LBM_P_FP32_FP16 = 2, LBM_P_FP32_BF16 = 3 };
+/* Collision of f: LBM_COLL_BGK, Eq. 34; LBM_COLL_MRT, Eqs. 43-45: relaxation in
+ * the moment space of Appendix B with S of Eq. 40 and m^eq of Eq. 41 (h keeps
+ * its BGK relaxation with the Eq. 47 coupling, which has the same coefficient
+ * as Eq. 36). */
+enum { LBM_COLL_BGK = 0, LBM_COLL_MRT = 1 };
 
 typedef struct {
   int32_t nx, ny;           /* fluid nodes per axis, >= 1 (>= 3 on a walled axis)  */
@@ -89,6 +94,14 @@ typedef struct {
   int32_t correction;       /* 1: C_a of Eqs. 48-50; 0: omitted                 */
   int32_t z_full;           /* 1: Z = e.u - u^2/2 (Eq. 7b); 0: Z = e.u           */
   int32_t precision;        /* LBM_P_*                                          */
+  int32_t collision;        /* LBM_COLL_BGK (0) or LBM_COLL_MRT                 */
+  double s_e, s_eps, s_q;   /* MRT rates of the moments e, epsilon, q_x / q_y
+                               (Eq. 40: 1/tau_e, 1/tau_eps, 1/tau_q), each in
+                               (0, 2); 0 selects omega_f (the paper's cavity:
+                               s_e = s_eps = omega_f, s_q = 1.5).  The shear
+                               rate is omega_f (the discrete MRT time is tau_f
+                               + 1/2: mu = tau_f p as for BGK); conserved
+                               moments relax at rate 1.  Ignored for BGK.     */
 } lbm_params;
 
 typedef struct lbm_handle lbm_handle;
@@ -274,7 +287,8 @@ int lbm_set_steps_done(lbm_handle* h, int64_t t);
  * storage, 12 otherwise, for the TMA kernel; about one wave of blocks for the
  * register-pull kernel).  rows_per_block (and the block width of the
  * register-pull kernel) never changes a bit of the result; different variants
- * agree to rounding (different FMA contraction). */
+ * agree to rounding (different FMA contraction).  Variant 2 is built for the
+ * BGK collision only (LBM_ERR_PARAM with LBM_COLL_MRT). */
 int lbm_set_launch(lbm_handle* h, int32_t variant, int32_t rows_per_block);
 
 /* Frees the handle and the device memory it owns.  NULL-safe. */

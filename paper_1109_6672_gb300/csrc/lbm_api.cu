@@ -150,6 +150,18 @@ int validate(const lbm_params* p, std::string& why) {
     why = "precision must be one of LBM_P_*";
     return LBM_ERR_PARAM;
   }
+  if (p->collision != LBM_COLL_BGK && p->collision != LBM_COLL_MRT) {
+    why = "collision must be LBM_COLL_BGK or LBM_COLL_MRT";
+    return LBM_ERR_PARAM;
+  }
+  if (p->collision == LBM_COLL_MRT) {
+    for (double r : {p->s_e, p->s_eps, p->s_q}) {
+      if (!(r >= 0.0 && r < 2.0)) {
+        why = "MRT rates s_e, s_eps, s_q must be in (0, 2), or 0 for omega_f";
+        return LBM_ERR_PARAM;
+      }
+    }
+  }
   return LBM_OK;
 }
 
@@ -180,8 +192,17 @@ void fill_grid(const lbm_params* p, Grid& g) {
   g.correction = p->correction;
   g.z_full = p->z_full;
   g.has_force = p->g != 0.0;
+  g.collision = p->collision;
   k.omega_f = 2.0 / (2.0 * p->tau_f + 1.0);
   k.omega_h = 2.0 / (2.0 * p->tau_h + 1.0);
+  // Z coupling of h: w_h - w_f (Eq. 36); for MRT (Eq. 47) (1 - w_h/2) / tau_hf
+  // with tau_hf = tau/(Pr - 1), tau = tau_f + 1/2, Pr = (tau - 1/2)/tau_h
+  k.kz = p->collision == LBM_COLL_MRT
+             ? (1.0 - 0.5 * k.omega_h) * (p->tau_f / p->tau_h - 1.0) / (p->tau_f + 0.5)
+             : k.omega_h - k.omega_f;
+  k.se = p->s_e > 0.0 ? p->s_e : k.omega_f;
+  k.seps = p->s_eps > 0.0 ? p->s_eps : k.omega_f;
+  k.sq = p->s_q > 0.0 ? p->s_q : k.omega_f;
   k.g = p->g;
   k.b6 = p->b / 6.0;
   k.six_b = 6.0 / p->b;
@@ -191,6 +212,10 @@ void fill_grid(const lbm_params* p, Grid& g) {
   f.g = (float)k.g;
   f.b6 = (float)k.b6;
   f.six_b = (float)k.six_b;
+  f.kz = (float)k.kz;
+  f.se = (float)k.se;
+  f.seps = (float)k.seps;
+  f.sq = (float)k.sq;
   for (int s = 0; s < 4; ++s) {
     f.uw[s][0] = (float)k.uw[s][0];
     f.uw[s][1] = (float)k.uw[s][1];
@@ -618,6 +643,8 @@ int lbm_set_launch(lbm_handle* h, int32_t variant, int32_t rows_per_block) {
       rows_per_block < 0)
     return fail(h, LBM_ERR_PARAM,
                 "variant must be 0, 1, 2 or a multiple of 32 in [64, 256]; rows >= 0");
+  if (variant == TMA_PR_2 && h->p.collision == LBM_COLL_MRT)
+    return fail(h, LBM_ERR_PARAM, "variant 2 (two nodes per thread) is built for BGK only");
   h->variant = variant == 0 ? TMA_PR_1 : variant;
   h->rows = rows_per_block;
   return LBM_OK;

@@ -51,7 +51,7 @@ struct lbm_batch {
   int rows = 0;      // 0: per-precision default
   int dynamic = 1;   // atomic work queue
   std::vector<int> modes;        // physics modes present in the work list
-  int occ_mode[16] = {0};        // resident blocks per SM per mode (0: not queried)
+  int occ_mode[BATCH_MODE_SLOTS] = {0};  // resident blocks per SM per mode (0: not queried)
   std::map<std::pair<int64_t, std::vector<int>>, cudaGraphExec_t> graphs;
   std::string err;
 };
@@ -133,8 +133,8 @@ int rebuild_items(lbm_batch* b) {
   });
   const int rows = rows_of(b);
   b->h_items.clear();
-  int begin[8], end[8];
-  for (int m = 0; m < 8; ++m) begin[m] = end[m] = 0;
+  int begin[BATCH_MODE_SLOTS], end[BATCH_MODE_SLOTS];
+  for (int m = 0; m < BATCH_MODE_SLOTS; ++m) begin[m] = end[m] = 0;
   b->modes.clear();
   for (int s : order) {
     const lbm_params& p = b->slots[s].p;
@@ -161,13 +161,14 @@ int rebuild_items(lbm_batch* b) {
       cudaMemcpyAsync(b->d_items, b->h_items.data(), b->h_items.size() * sizeof(WorkItem),
                       cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
     return bfail(b, LBM_ERR_CUDA, "work list upload failed");
-  int hdr[17];
-  for (int m = 0; m < 8; ++m) {
+  int hdr[2 * BATCH_MODE_SLOTS + 1];
+  for (int m = 0; m < BATCH_MODE_SLOTS; ++m) {
     hdr[m] = begin[m];
-    hdr[8 + m] = end[m];
+    hdr[BATCH_MODE_SLOTS + m] = end[m];
   }
-  hdr[16] = b->dynamic;
-  static_assert(offsetof(BatchCtl, dynamic) == 16 * sizeof(int), "control header layout");
+  hdr[2 * BATCH_MODE_SLOTS] = b->dynamic;
+  static_assert(offsetof(BatchCtl, dynamic) == 2 * BATCH_MODE_SLOTS * sizeof(int),
+                "control header layout");
   if (cudaMemcpyAsync(b->d_ctl, hdr, sizeof(hdr), cudaMemcpyHostToDevice, b->stream) !=
       cudaSuccess)
     return bfail(b, LBM_ERR_CUDA, "control upload failed");
@@ -188,7 +189,7 @@ int upload_grids(lbm_batch* b) {
 }
 
 int blocks_of(lbm_batch* b, int mode) {
-  int& occ = b->occ_mode[mode & 15];
+  int& occ = b->occ_mode[mode_slot(mode)];
   if (!occ) {
     by_precision(b->precision, [&](auto* tag) {
       using S = std::remove_pointer_t<decltype(tag)>;
@@ -230,7 +231,8 @@ int graph_for(lbm_batch* b, int64_t k, cudaGraphExec_t* out) {
   cudaGraph_t graph;
   if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return bfail(b, LBM_ERR_CUDA, "stream capture failed to start");
-  cudaError_t e = cudaMemsetAsync(counters_of(b), 0, sizeof(int) * 8 * BATCH_MAX_SEG, b->stream);
+  const size_t counter_bytes = sizeof(int) * BATCH_MODE_SLOTS * BATCH_MAX_SEG;
+  cudaError_t e = cudaMemsetAsync(counters_of(b), 0, counter_bytes, b->stream);
   for (int64_t j = 0; j < k && e == cudaSuccess; ++j) e = launch_all_modes(b, (int)j);
   cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
   if (e != cudaSuccess || e2 != cudaSuccess)
@@ -554,7 +556,8 @@ int lbm_batch_autotune(lbm_batch* b, int32_t reps, int64_t out_best[3]) {
       for (int mode : b->modes) blocks_of(b, mode);
       for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
         if (r == 1) cudaEventRecord(e0, b->stream);
-        e = cudaMemsetAsync(counters_of(b), 0, sizeof(int) * 8 * BATCH_MAX_SEG, b->stream);
+        e = cudaMemsetAsync(counters_of(b), 0, sizeof(int) * BATCH_MODE_SLOTS * BATCH_MAX_SEG,
+                            b->stream);
         if (e == cudaSuccess) e = launch_all_modes(b, 0);
       }
       cudaEventRecord(e1, b->stream);

@@ -73,6 +73,8 @@ __host__ __device__ constexpr int plane(int a) {
 }
 
 // Physical constants in one arithmetic precision (lattice units, R T0 = 1/3).
+enum { COLL_BGK = 0, COLL_MRT = 1 };
+
 template <class C>
 struct Phys {
   C omega_f, omega_h;  // 2 / (2 tau + 1)
@@ -80,6 +82,8 @@ struct Phys {
   C b6, six_b;         // b / 6 and 6 / b
   C uw[4][2];          // wall velocities
   C thw[4];            // wall theta = T_w / T0
+  C kz;                // coefficient of the Z coupling of h (Eq. 36 / Eq. 47)
+  C se, seps, sq;      // MRT rates of e, epsilon, q (Eq. 40)
 };
 
 // Per-grid launch argument.
@@ -89,6 +93,7 @@ struct Grid {
   int nx, ny, pitch, rp;  // rp = 18 * pitch
   int bc[4];              // x-, x+, y-, y+
   int energy_model, correction, z_full, has_force;
+  int collision;          // COLL_BGK or COLL_MRT
   Phys<double> pd;
   Phys<float> pf;
   float fref[9], href[9];  // rest equilibria (deviation storage)
@@ -530,6 +535,57 @@ __device__ __forceinline__ void xedge_writes(const Grid& g, S* __restrict__ dst,
   }
 }
 
+// MRT collision of f (Eq. 44 with the Appendix B matrices): with n = f - f^eq
+// and the correction (plus force) c in velocity space,
+//   f* = f + M^-1 [ -S M n + (I - S/2) M c ],
+// S = diag(1, s_e, s_eps, 1, s_q, 1, s_q, w_f, w_f) (Eq. 40; the rates of
+// the conserved moments rho and j drop out of the result).
+template <class C>
+__device__ __forceinline__ void mrt_collide(const Phys<C>& k, const C f[9], const C n[9],
+                                            const C c[9], C out[9]) {
+  // moments (rho, e, eps, jx, qx, jy, qy, pxx, pxy) of n and c: rows of M
+  C mn[9], mc[9];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const C* q = t ? c : n;
+    C* m = t ? mc : mn;
+    const C sa = (q[1] + q[2]) + (q[3] + q[4]), sd = (q[5] + q[6]) + (q[7] + q[8]);
+    const C dx1 = q[1] - q[3], dy1 = q[2] - q[4];
+    const C dxd = (q[5] - q[6]) - (q[7] - q[8]), dyd = (q[5] + q[6]) - (q[7] + q[8]);
+    m[0] = q[0] + sa + sd;
+    m[1] = C(-4) * q[0] - sa + C(2) * sd;
+    m[2] = C(4) * q[0] - C(2) * sa + sd;
+    m[3] = dx1 + dxd;
+    m[4] = C(-2) * dx1 + dxd;
+    m[5] = dy1 + dyd;
+    m[6] = C(-2) * dy1 + dyd;
+    m[7] = (q[1] + q[3]) - (q[2] + q[4]);
+    m[8] = (q[5] - q[6]) + (q[7] - q[8]);
+  }
+  const C wf = k.omega_f;
+  const C s[9] = {C(1), k.se, k.seps, C(1), k.sq, C(1), k.sq, wf, wf};
+  C dm[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) dm[q] = -s[q] * mn[q] + (C(1) - C(0.5) * s[q]) * mc[q];
+  // M^-1 dm (Eq. B2), grouped by shell
+  const C r0 = dm[0] * C(1.0 / 9.0);
+  const C ax = r0 - dm[1] * C(1.0 / 36.0) - dm[2] * C(1.0 / 18.0);
+  const C dg = r0 + dm[1] * C(1.0 / 18.0) + dm[2] * C(1.0 / 36.0);
+  const C x1 = (dm[3] - dm[4]) * C(1.0 / 6.0), y1 = (dm[5] - dm[6]) * C(1.0 / 6.0);
+  const C x2 = dm[3] * C(1.0 / 6.0) + dm[4] * C(1.0 / 12.0);
+  const C y2 = dm[5] * C(1.0 / 6.0) + dm[6] * C(1.0 / 12.0);
+  const C pp = dm[7] * C(0.25), pq = dm[8] * C(0.25);
+  out[0] = f[0] + (r0 - dm[1] * C(1.0 / 9.0) + dm[2] * C(1.0 / 9.0));
+  out[1] = f[1] + (ax + x1 + pp);
+  out[2] = f[2] + (ax + y1 - pp);
+  out[3] = f[3] + (ax - x1 + pp);
+  out[4] = f[4] + (ax - y1 - pp);
+  out[5] = f[5] + (dg + x2 + y2 + pq);
+  out[6] = f[6] + (dg - x2 + y2 - pq);
+  out[7] = f[7] + (dg - x2 - y2 + pq);
+  out[8] = f[8] + (dg + x2 - y2 - pq);
+}
+
 // Collision of one node (Eq. 34 with +(1 - w_f/2) C, Eq. 36 or Eq. 38) with
 // the correction C_a (Eq. 49) plus the Guo force F_a, then the stores.
 template <class S>
@@ -579,14 +635,23 @@ __device__ __forceinline__ void collide_store(const Grid& g, S* __restrict__ dst
 
   const C usq = ux * ux + uy * uy;
   const C kc = C(1) - C(0.5) * wf;
-  const C kz = wh - wf;
+  const C kz = k.kz;
   C v[27];
+  if (g.collision == COLL_MRT) {
+    C fa[9], fneq[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      fa[a] = pref<S>(g, a) + d[a];
+      fneq[a] = fa[a] - feq[a];
+    }
+    mrt_collide<C>(k, fa, fneq, cc, v);
+  }
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     const C fa = pref<S>(g, a) + d[a];
     const C ha = pref<S>(g, 9 + a) + d[9 + a];
     const C fneq = fa - feq[a];
-    v[a] = fa - wf * fneq + kc * cc[a];
+    if (g.collision != COLL_MRT) v[a] = fa - wf * fneq + kc * cc[a];
     C hs = ha - wh * (ha - heq[a]);
     if (total) {
       const C eu = C(ex(a)) * ux + C(ey(a)) * uy;

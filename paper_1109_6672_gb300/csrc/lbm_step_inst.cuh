@@ -6,6 +6,8 @@
 #include "lbm_batch.cuh"
 #include "lbm_step_pr.cuh"
 
+#include <type_traits>
+
 namespace lbm {
 
 // Kernel pointer, block size and shared memory of one configuration.
@@ -35,28 +37,34 @@ cudaError_t launch_one(const Grid& g, const CUtensorMap& map, int rows, dim3 gri
   return cudaGetLastError();
 }
 
+// Calls fn(std::integral_constant<int, M>{}) for the kernel of physics mode
+// `mode` (one of the BGK modes of mode_of, or with MRT_OK also their MRT
+// twins); cudaErrorInvalidValue for a mode without a kernel.
+template <int I, int OFF, class Fn>
+cudaError_t dispatch_from(int mode, Fn& fn) {
+  if constexpr (I == NUM_BGK_MODES) {
+    return cudaErrorInvalidValue;
+  } else {
+    constexpr int M = BGK_MODES[I] | OFF;
+    if (mode == M) return fn(std::integral_constant<int, M>{});
+    return dispatch_from<I + 1, OFF>(mode, fn);
+  }
+}
+
+template <bool MRT_OK, class Fn>
+cudaError_t dispatch_mode(int mode, Fn&& fn) {
+  if (!(mode & MODE_MRT)) return dispatch_from<0, 0>(mode, fn);
+  if constexpr (MRT_OK) return dispatch_from<0, MODE_MRT>(mode, fn);
+  return cudaErrorInvalidValue;
+}
+
+// The two-node-per-thread variant is built for BGK only.
 template <class S, int NPT>
 cudaError_t launch_mode(const Grid& g, const CUtensorMap& map, int rows, dim3 grid,
                         cudaStream_t stream, int* occ) {
-  switch (mode_of(g)) {
-    case MODE_TOTAL | MODE_ZFULL | MODE_CORR:
-      return launch_one<S, NPT, MODE_TOTAL | MODE_ZFULL | MODE_CORR>(g, map, rows, grid,
-                                                                         stream, occ);
-    case MODE_TOTAL | MODE_ZFULL:
-      return launch_one<S, NPT, MODE_TOTAL | MODE_ZFULL>(g, map, rows, grid, stream, occ);
-    case MODE_TOTAL | MODE_CORR:
-      return launch_one<S, NPT, MODE_TOTAL | MODE_CORR>(g, map, rows, grid, stream, occ);
-    case MODE_TOTAL:
-      return launch_one<S, NPT, MODE_TOTAL>(g, map, rows, grid, stream, occ);
-    case MODE_FORCE | MODE_CORR:
-      return launch_one<S, NPT, MODE_FORCE | MODE_CORR>(g, map, rows, grid, stream, occ);
-    case MODE_FORCE:
-      return launch_one<S, NPT, MODE_FORCE>(g, map, rows, grid, stream, occ);
-    case MODE_CORR:
-      return launch_one<S, NPT, MODE_CORR>(g, map, rows, grid, stream, occ);
-    default:
-      return launch_one<S, NPT, 0>(g, map, rows, grid, stream, occ);
-  }
+  return dispatch_mode<NPT == 1>(mode_of(g), [&](auto m) {
+    return launch_one<S, NPT, decltype(m)::value>(g, map, rows, grid, stream, occ);
+  });
 }
 
 template <class S>
@@ -93,25 +101,9 @@ cudaError_t batch_one(const BatchGrid* grids, const WorkItem* items, BatchCtl* c
 template <class S>
 cudaError_t batch_mode(const BatchGrid* grids, const WorkItem* items, BatchCtl* ctl, int j,
                        int mode, int blocks, cudaStream_t stream, int* occ) {
-  switch (mode) {
-    case MODE_TOTAL | MODE_ZFULL | MODE_CORR:
-      return batch_one<S, MODE_TOTAL | MODE_ZFULL | MODE_CORR>(grids, items, ctl, j, blocks,
-                                                                stream, occ);
-    case MODE_TOTAL | MODE_ZFULL:
-      return batch_one<S, MODE_TOTAL | MODE_ZFULL>(grids, items, ctl, j, blocks, stream, occ);
-    case MODE_TOTAL | MODE_CORR:
-      return batch_one<S, MODE_TOTAL | MODE_CORR>(grids, items, ctl, j, blocks, stream, occ);
-    case MODE_TOTAL:
-      return batch_one<S, MODE_TOTAL>(grids, items, ctl, j, blocks, stream, occ);
-    case MODE_FORCE | MODE_CORR:
-      return batch_one<S, MODE_FORCE | MODE_CORR>(grids, items, ctl, j, blocks, stream, occ);
-    case MODE_FORCE:
-      return batch_one<S, MODE_FORCE>(grids, items, ctl, j, blocks, stream, occ);
-    case MODE_CORR:
-      return batch_one<S, MODE_CORR>(grids, items, ctl, j, blocks, stream, occ);
-    default:
-      return batch_one<S, 0>(grids, items, ctl, j, blocks, stream, occ);
-  }
+  return dispatch_mode<true>(mode, [&](auto m) {
+    return batch_one<S, decltype(m)::value>(grids, items, ctl, j, blocks, stream, occ);
+  });
 }
 
 template <class S>

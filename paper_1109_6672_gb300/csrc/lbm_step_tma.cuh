@@ -14,7 +14,20 @@ namespace lbm {
 
 // ---- compile-time physics mode ---------------------------------------------
 
-enum { MODE_TOTAL = 1, MODE_ZFULL = 2, MODE_CORR = 4, MODE_FORCE = 8 };
+enum { MODE_TOTAL = 1, MODE_ZFULL = 2, MODE_CORR = 4, MODE_FORCE = 8, MODE_MRT = 16 };
+
+// The BGK modes mode_of() produces (total energy with the full or simple Z,
+// internal energy with or without gravity; each with or without the
+// correction); each has an MRT twin (| MODE_MRT).
+constexpr int NUM_BGK_MODES = 8;
+constexpr int BGK_MODES[NUM_BGK_MODES] = {MODE_TOTAL | MODE_ZFULL | MODE_CORR,
+                                          MODE_TOTAL | MODE_ZFULL,
+                                          MODE_TOTAL | MODE_CORR,
+                                          MODE_TOTAL,
+                                          MODE_FORCE | MODE_CORR,
+                                          MODE_FORCE,
+                                          MODE_CORR,
+                                          0};
 
 template <int M>
 struct Mode {
@@ -22,6 +35,7 @@ struct Mode {
   static constexpr bool zfull = (M & MODE_ZFULL) != 0;
   static constexpr bool corr = (M & MODE_CORR) != 0;
   static constexpr bool force = (M & MODE_FORCE) != 0;
+  static constexpr bool mrt = (M & MODE_MRT) != 0;
 };
 
 // The eight modes the validated parameters can produce (Z only matters for
@@ -35,6 +49,7 @@ inline int mode_of(const Grid& g) {
     m |= MODE_FORCE;
   }
   if (g.correction) m |= MODE_CORR;
+  if (g.collision == COLL_MRT) m |= MODE_MRT;
   return m;
 }
 
@@ -125,8 +140,18 @@ __device__ __forceinline__ void collide_m(const Grid& g, S* __restrict__ p, int 
     }
   }
   const C kc = C(1) - C(0.5) * wf;
-  const C kz = wh - wf;
+  const C kz = k.kz;
   const C zc = MD::zfull ? C(0.5) * (ux * ux + uy * uy) : C(0);
+  if constexpr (MD::mrt) {
+    C fa[9], fneq[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      fa[a] = d[a];
+      if constexpr (Io<S>::dev) fa[a] += pref<S>(g, a);
+      fneq[a] = fa[a] - feq[a];
+    }
+    mrt_collide<C>(k, fa, fneq, cc, v);
+  }
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     C fa = d[a], ha = d[9 + a];
@@ -135,7 +160,7 @@ __device__ __forceinline__ void collide_m(const Grid& g, S* __restrict__ p, int 
       ha += pref<S>(g, 9 + a);
     }
     const C fneq = fa - feq[a];
-    v[a] = fa - wf * fneq + kc * cc[a];
+    if constexpr (!MD::mrt) v[a] = fa - wf * fneq + kc * cc[a];
     C hs = ha - wh * (ha - heq[a]);
     if constexpr (MD::total) {
       const C eu = C(ex(a)) * ux + C(ey(a)) * uy;

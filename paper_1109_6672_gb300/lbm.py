@@ -20,6 +20,7 @@ LBM_ERR_NONFINITE, LBM_ERR_TIMEOUT, LBM_ERR_STATE = -4, -5, -6
 LBM_BC_PERIODIC, LBM_BC_WALL_ISOTHERMAL, LBM_BC_WALL_ADIABATIC = 0, 1, 2
 LBM_E_TOTAL, LBM_E_INTERNAL = 0, 1
 LBM_P_FP64, LBM_P_FP32, LBM_P_FP32_FP16, LBM_P_FP32_BF16 = 0, 1, 2, 3
+LBM_COLL_BGK, LBM_COLL_MRT = 0, 1
 PRECISION_NAMES = {LBM_P_FP64: "f64", LBM_P_FP32: "f32", LBM_P_FP32_FP16: "f32/f16dev",
                    LBM_P_FP32_BF16: "f32/bf16dev"}
 BYTES_PER_NODE_UPDATE = {LBM_P_FP64: 288, LBM_P_FP32: 144, LBM_P_FP32_FP16: 72,
@@ -34,7 +35,8 @@ class lbm_params(ctypes.Structure):
         ("u_wall", (ctypes.c_double * 2) * 4), ("T_wall", ctypes.c_double * 4),
         ("g", ctypes.c_double), ("energy_model", ctypes.c_int32),
         ("correction", ctypes.c_int32), ("z_full", ctypes.c_int32),
-        ("precision", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("collision", ctypes.c_int32),
+        ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
     ]
 
 
@@ -130,6 +132,8 @@ def make_params(p: dict) -> lbm_params:
     o.correction = int(p.get("correction", 1))
     o.z_full = int(p.get("z_full", 1))
     o.precision = int(p.get("precision", LBM_P_FP64))
+    o.collision = int(p.get("collision", LBM_COLL_BGK))
+    o.s_e, o.s_eps, o.s_q = (float(p.get(k, 0.0)) for k in ("s_e", "s_eps", "s_q"))
     return o
 
 

@@ -3,6 +3,7 @@ include/*.h; host-only calls (sizes, validation, status strings) work without
 a GPU.  No kernel is launched here."""
 import ctypes
 import re
+import subprocess
 from pathlib import Path
 
 import pytest
@@ -40,9 +41,21 @@ def test_every_declared_symbol_is_exported(lib):
     assert not missing, missing
 
 
-def test_params_struct_size_matches_header(lib):
-    # lbm_params: 2+4 int32, 6 doubles, 8+4 doubles, 1 double, 4 int32
-    assert ctypes.sizeof(lbm.lbm_params) == 4 * 6 + 8 * 6 + 8 * 12 + 8 + 4 * 4
+def test_params_struct_layout_matches_header(lib, tmp_path):
+    """The binding's lbm_params has the C compiler's size and field offsets."""
+    fields = [f for f, _ in lbm.lbm_params._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "lbm.h"\nint main(void) {\n'
+        '  printf("%zu\\n", sizeof(lbm_params));\n'
+        + "".join(f'  printf("%zu\\n", offsetof(lbm_params, {f}));\n' for f in fields)
+        + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", str(ROOT / "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(lbm.lbm_params)
+    assert out[1:] == [getattr(lbm.lbm_params, f).offset for f in fields]
 
 
 def test_state_bytes_and_validation_without_gpu(lib):
@@ -53,7 +66,8 @@ def test_state_bytes_and_validation_without_gpu(lib):
     assert lbm.lbm_state_bytes(dict(p, precision=lbm.LBM_P_FP32_BF16)) * 2 <= n + 4096
     for bad in (dict(p, tau_f=0.0), dict(p, R=1.0), dict(p, b=1.0), dict(p, nx=0),
                 dict(p, bc=[0, 1, 0, 0]), dict(p, g=1e-3), dict(p, Pr=2.0),
-                dict(p, precision=7), dict(p, bc=[1, 1, 0, 0], nx=2)):
+                dict(p, precision=7), dict(p, bc=[1, 1, 0, 0], nx=2), dict(p, collision=2),
+                dict(p, collision=1, s_q=2.0), dict(p, collision=1, s_e=-0.5)):
         with pytest.raises(lbm.LbmError) as e:
             lbm.lbm_state_bytes(bad)
         assert e.value.status == lbm.LBM_ERR_PARAM
