@@ -81,6 +81,7 @@ typedef struct {
   double *f[9], *h[9];   /* current state, pre-collision */
   double *fn[9], *hn[9]; /* next state */
   double *rho, *ux, *uy, *theta, *Qx, *Qy;
+  double* es; /* specific energy sum(hbar)/rho: E (Eq. 37) or b R T / 2 (Eq. 38) */
 } orc_state;
 
 /* ---- pointwise pieces (exported so the tests can pin them one by one) ---- */
@@ -212,6 +213,7 @@ orc_state* orc_new(const orc_params* p) {
   s->theta = (double*)calloc(s->n, sizeof(double));
   s->Qx = (double*)calloc(s->n, sizeof(double));
   s->Qy = (double*)calloc(s->n, sizeof(double));
+  s->es = (double*)calloc(s->n, sizeof(double));
   return s;
 }
 
@@ -229,6 +231,7 @@ void orc_free(orc_state* s) {
   free(s->theta);
   free(s->Qx);
   free(s->Qy);
+  free(s->es);
   free(s);
 }
 
@@ -258,7 +261,7 @@ void orc_init(orc_state* s, const double* rho, const double* ux, const double* u
  * (rho u = sum e fbar + a/2, a = (0, -rho g)), Eq. 37 or the internal-energy
  * temperature under Eq. 38. */
 static void node_moments(const orc_state* s, long i, double* rho, double* ux, double* uy,
-                         double* theta) {
+                         double* theta, double* es) {
   const orc_params* p = &s->p;
   double r = 0, jx = 0, jy = 0, sh = 0;
   for (int a = 0; a < 9; ++a) {
@@ -279,6 +282,7 @@ static void node_moments(const orc_state* s, long i, double* rho, double* ux, do
   *ux = vx;
   *uy = vy;
   *theta = T / p->T0;
+  *es = sh / r;
 }
 
 /* Wall temperature ratio for side `side` seen from node i. */
@@ -315,7 +319,7 @@ static void phase1(orc_state* s, int nthreads) {
   for (int y = 0; y < p->ny; ++y) {
     for (int x = 0; x < p->nx; ++x) {
       long i = (long)y * p->nx + x;
-      node_moments(s, i, &s->rho[i], &s->ux[i], &s->uy[i], &s->theta[i]);
+      node_moments(s, i, &s->rho[i], &s->ux[i], &s->uy[i], &s->theta[i], &s->es[i]);
       s->Qx[i] = s->rho[i] * s->ux[i] * (1.0 - s->theta[i]);
       s->Qy[i] = s->rho[i] * s->uy[i] * (1.0 - s->theta[i]);
     }
@@ -348,13 +352,29 @@ static void phase2(orc_state* s, int nthreads) {
       orc_force(RT0, ux, uy, 0.0, -rho * p->g, F);
       for (int a = 0; a < 9; ++a) C[a] += F[a];
 
+      /* Equilibria at the node's moments.  The energy they carry is the one
+       * recovered from hbar: E = sum(hbar)/rho (Eq. 37) in Eq. 18b, and
+       * b R T / 2 = sum(hbar)/rho (Eq. 38) for the internal-energy model, so
+       * that the relaxation returns exactly the energy it was given; the rest
+       * populations follow from the moment sums of Eqs. 19a/19b,
+       * sum f^eq = rho and sum h^eq = rho E, so that no rounding of the
+       * weights biases mass or energy step after step. */
       double feq[9], heq[9];
+      const double es = s->es[i];
       orc_feq(RT0, rho, ux, uy, th, feq);
       if (p->energy_model == ORC_E_TOTAL) {
-        double E = 0.5 * (p->b * RT0 * th + usq); /* E = (bRT + u^2)/2 */
-        orc_heq(RT0, rho, ux, uy, th, E, feq, heq);
+        orc_heq(RT0, rho, ux, uy, th, es, feq, heq);
       } else {
-        orc_heq_internal(RT0, p->b, th, feq, heq);
+        for (int a = 0; a < 9; ++a) heq[a] = es * feq[a];
+      }
+      {
+        double sf = 0.0, sh = 0.0;
+        for (int a = 1; a < 9; ++a) {
+          sf += feq[a];
+          sh += heq[a];
+        }
+        feq[0] = rho - sf;
+        heq[0] = rho * es - sh;
       }
 
       /* Collision of f.  BGK: Eq. 34 ("+(1 - w_f/2) C" from Eqs. 32-33).  MRT:
@@ -471,8 +491,8 @@ void orc_step(orc_state* s, long nsteps, int nthreads) {
 /* Macroscopic output of the current state: rho, u, T (T = theta T0). */
 void orc_moments(const orc_state* s, double* rho, double* ux, double* uy, double* T) {
   for (long i = 0; i < s->n; ++i) {
-    double r, vx, vy, th;
-    node_moments(s, i, &r, &vx, &vy, &th);
+    double r, vx, vy, th, es;
+    node_moments(s, i, &r, &vx, &vy, &th, &es);
     rho[i] = r;
     ux[i] = vx;
     uy[i] = vy;
@@ -484,8 +504,8 @@ void orc_moments(const orc_state* s, double* rho, double* ux, double* uy, double
 void orc_conserved(const orc_state* s, double out[4]) {
   double m = 0, px = 0, py = 0, e = 0;
   for (long i = 0; i < s->n; ++i) {
-    double r, vx, vy, th;
-    node_moments(s, i, &r, &vx, &vy, &th);
+    double r, vx, vy, th, es;
+    node_moments(s, i, &r, &vx, &vy, &th, &es);
     m += r;
     px += r * vx;
     py += r * vy;

@@ -151,3 +151,23 @@ def test_couette_b_five_percent_rise_and_convergence():
     assert errs[1] < 0.001
     assert rise == pytest.approx(0.05, rel=0.01)
     assert errs[0] / errs[1] > 3.0  # second order in H
+
+
+@pytest.mark.parametrize("model,b,stable_tau,unstable_tau", [(inputs.E_INTERNAL, 5.0, 0.06, 0.03),
+                                                             (inputs.E_TOTAL, 5.0, 0.15, 0.1),
+                                                             (inputs.E_TOTAL, 3.0, 0.25, 0.2)])
+def test_small_tau_stability_range(model, b, stable_tau, unstable_tau):
+    """Where the coupled BGK scheme stays bounded (Pr = 0.71, periodic box
+    seeded with grid-scale velocity noise 1e-4): internal energy down to
+    tau_f = 0.06 (omega_f = 1.79), total energy down to 0.15 at b = 5 and 0.25
+    at b = 3, whose h^eq rest weight is small; below these the thermal
+    coupling (theta in f^eq, tau_h != tau_f) grows.  Every configured workload
+    lies inside these ranges."""
+    n = 32
+    for tau_f, stable in ((stable_tau, True), (unstable_tau, False)):
+        p = inputs.base_params(n, n, tau_f=tau_f, tau_h=tau_f / 0.71, energy_model=model, b=b)
+        o = orc.Oracle(p).init(*inputs.uniform_fields(n, n, seed=1, u_amp=1e-4))
+        o.step(3000)
+        T = o.moments()[3]
+        bounded = bool(np.isfinite(T).all() and np.abs(T - 1).max() < 1e-6)
+        assert bounded == stable, (tau_f, np.abs(T - 1).max())
