@@ -219,6 +219,7 @@ def batch_and_serving(torch, args):
     grids, nodes, glups, tuned = batched(lbm.LBM_P_FP32_BF16)
     sims = glups * 1e9 / (nodes / len(grids) * 10000)
     _, _, glups16, tuned16 = batched(lbm.LBM_P_FP32_FP16)
+    _, _, glups32, tuned32 = batched(lbm.LBM_P_FP32)
     # plain one-grid-per-launch FP64 path
     f64 = [lbm.Lbm(dict(p, precision=lbm.LBM_P_FP64)).init(*f) for p, f in grids]
     for g in f64:
@@ -270,6 +271,8 @@ def batch_and_serving(torch, args):
         "autotune": tuned,
         "f16_storage": {"glups": glups16, "autotune": tuned16,
                         "sims_per_s_10k_steps": glups16 * 1e9 / (nodes / len(grids) * 10000)},
+        "f32_storage": {"glups": glups32, "autotune": tuned32,
+                        "sims_per_s_10k_steps": glups32 * 1e9 / (nodes / len(grids) * 10000)},
         "fp64_one_grid_per_launch": {"glups": glups64, "sims_per_s_10k_steps": sims64,
                                      "steps_timed": k64},
         "speedup_sims_per_s": sims / sims64,
@@ -282,7 +285,8 @@ def batch_and_serving(torch, args):
                              couette_ny=(17, 257), steps_range=(1000, 10000))
     factor = serve.load_factor_scale(trace, glups, load=0.7)
     serve.scale_arrivals(trace, factor)
-    for key, prec in (("serving", lbm.LBM_P_FP32_BF16), ("serving_f16", lbm.LBM_P_FP32_FP16)):
+    for key, prec in (("serving", lbm.LBM_P_FP32_BF16), ("serving_f16", lbm.LBM_P_FP32_FP16),
+                      ("serving_f32", lbm.LBM_P_FP32)):
         for r in trace:  # inputs are materialised per precision
             r.params = r.fields = None
         sb = lbm.Batch(prec, 64, 8 << 30)

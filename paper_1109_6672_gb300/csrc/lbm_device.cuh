@@ -296,16 +296,16 @@ __device__ __forceinline__ void moments(const Grid& g, const typename Io<S>::C d
 // Es is the specific energy the h^eq moment carries: E (total-energy model)
 // or b th / 6 (internal-energy model, h^eq = Es f^eq).
 //
-// In FP32 the rest populations are formed as the remainders of the moment
-// sums, f^eq_0 = rho - sum_{a>0} f^eq_a and h^eq_0 = rho Es - sum_{a>0} h^eq_a
-// (Eq. 19a/19b make this an identity): with the weights rounded to FP32 the
-// direct formula would miss sum f^eq = rho by a fixed 7e-9 relative, which
-// the collision would add to the mass (and energy) of every node at every
-// step.  FP64 keeps the direct formula.
+// The rest populations are formed as the remainders of the moment sums,
+// f^eq_0 = rho - sum_{a>0} f^eq_a and h^eq_0 = rho Es - sum_{a>0} h^eq_a
+// (Eq. 19a/19b make this an identity): with rounded weights the direct
+// formula would miss sum f^eq = rho by a fixed amount (7e-9 relative in FP32,
+// 1e-16 in FP64), which the collision would add to the mass (and energy) of
+// every node at every step.
 template <class C>
 __device__ __forceinline__ void equilibria_es(C rho, C ux, C uy, C th, C Es, bool total, C feq[9],
                                               C heq[9]) {
-  constexpr bool remainder = sizeof(C) == 4;
+  constexpr bool remainder = true;
   const C usq = ux * ux + uy * uy;
   const C tm1 = th - C(1);
   const C A0 = C(1) - C(1.5) * usq;
@@ -356,18 +356,16 @@ __device__ __forceinline__ void equilibria(C rho, C ux, C uy, C th, C b6, bool t
   equilibria_es<C>(rho, ux, uy, th, Es, total, feq, heq);
 }
 
-// Equilibria of the collision.  FP32: h^eq carries the specific energy Es
-// recovered from the node's own sum of h (rho Es = sum h), so that the
-// relaxation conserves energy to rounding; forming it from theta through
-// b / 6 and 6 / b (each rounded to FP32) would bias it by up to 2e-8
-// relative per step.  FP64: from theta.
+// Equilibria of the collision: h^eq carries the specific energy Es
+// recovered from the node's own sum of h (rho Es = sum h, Eq. 37 or the
+// Eq. 38 form), so that the relaxation conserves energy to rounding; forming
+// it from theta through b / 6 and 6 / b (each rounded) would bias it by up to
+// 2e-8 relative per step in FP32 (and 1e-16 in FP64).
 template <class C>
 __device__ __forceinline__ void collision_equilibria(C rho, C ux, C uy, C th, C Es, C b6,
                                                      bool total, C feq[9], C heq[9]) {
-  if constexpr (sizeof(C) == 4)
-    equilibria_es<C>(rho, ux, uy, th, Es, total, feq, heq);
-  else
-    equilibria<C>(rho, ux, uy, th, b6, total, feq, heq);
+  (void)b6;
+  equilibria_es<C>(rho, ux, uy, th, Es, total, feq, heq);
 }
 
 // Wall equilibria: f^eq at (rho, u_w, theta) (halfway bounce-back term) and

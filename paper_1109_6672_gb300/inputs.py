@@ -95,19 +95,25 @@ def cavity_gravity(H: int, dT_over_T0: float, Ma: float = 0.1, strat: float = 0.
 
 def cavity(n: int = 256, Ra: float = 1e5, Pr: float = 0.71, dT_over_T0: float = 0.01,
            seed: int = 1, noise: float = 1e-4, b: float = 5.0, precision: int = P_FP64,
-           nu_min: float = 0.0, strat: float = 0.05, **kw):
+           nu_min: float = 0.02, strat: float = 0.05, **kw):
     """Differentially heated square cavity (natural convection): hot wall at
     x-, cold wall at x+ (isothermal, T0 (1 +- dT/2)), adiabatic top and bottom,
     internal-energy model (Eq. 38), gravity a = (0, -rho g), b = 5
     (gamma = 1.4).  Ra = g beta dT H^3 Pr / nu^2 with beta = 1/T0 (Eq. 57-58),
-    hence nu = sqrt(g (dT/T0) H^3 Pr / Ra).  ``nu_min`` floors nu (lowering the
-    effective Ra) for under-resolved members of a batch.  ``strat`` caps the
-    hydrostatic stratification g H / (R T0); near the Boussinesq limit it has
-    to be small against dT/T0 (0.05 dT/T0 keeps its effect on Nu below 1 %)."""
+    hence nu = sqrt(g (dT/T0) H^3 Pr / Ra).  ``strat`` caps the hydrostatic
+    stratification g H / (R T0); near the Boussinesq limit it has to be small
+    against dT/T0 (0.05 dT/T0 keeps its effect on Nu below 1 %).  A nu below
+    ``nu_min`` (0.02: tau_f = 0.06, where the scheme with the internal-energy
+    model is still stable) is raised by raising g (keeping Ra), up to the
+    Ma = 0.1 free-fall limit; beyond it nu is floored and the effective Ra
+    drops (recorded as Ra_effective)."""
     H = n
     g = cavity_gravity(H, dT_over_T0, strat=strat)
     nu = math.sqrt(g * dT_over_T0 * H ** 3 * Pr / Ra)
-    nu = max(nu, nu_min)
+    if nu < nu_min:
+        g_ma = cavity_gravity(H, dT_over_T0, strat=math.inf)
+        g = min(nu_min * nu_min * Ra / (dT_over_T0 * H ** 3 * Pr), g_ma)
+        nu = max(math.sqrt(g * dT_over_T0 * H ** 3 * Pr / Ra), nu_min)
     tau_f = nu / RT0
     Th, Tl = 1.0 + 0.5 * dT_over_T0, 1.0 - 0.5 * dT_over_T0
     p = base_params(n, n, tau_f=tau_f, tau_h=tau_f / Pr, b=b, g=g, energy_model=E_INTERNAL,
@@ -120,10 +126,8 @@ def cavity(n: int = 256, Ra: float = 1e5, Pr: float = 0.71, dT_over_T0: float = 
 def batch_cavities(count: int = 256, seed: int = 4, sides=tuple(range(64, 513, 32)),
                    precision: int = P_FP32_BF16, nu_min: float = 0.02):
     """Batch of independent cavities: side uniform over ``sides``, dT/T0 ~
-    U[0.01, 0.6], Ra log-uniform in [1e4, 1e6], Pr = 0.71.  nu is floored at
-    nu_min (tau_f >= 0.06, omega_f <= 1.79): small cavities at high Ra are
-    under-resolved and the BGK scheme diverges near omega_f = 2; the floor
-    lowers their effective Ra instead (recorded as Ra_effective)."""
+    U[0.01, 0.6], Ra log-uniform in [1e4, 1e6], Pr = 0.71, nu >= nu_min
+    (see ``cavity``)."""
     rng = np.random.default_rng(seed)
     out = []
     for k in range(count):

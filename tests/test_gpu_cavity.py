@@ -30,7 +30,7 @@ def table2():
 
 
 def steady_cavity(n, Ra, precision, chunk, max_steps, dT=0.2):
-    p, f = inputs.cavity(n=n, Ra=Ra, dT_over_T0=dT, strat=0.05 * dT, seed=1,
+    p, f = inputs.cavity(n=n, Ra=Ra, dT_over_T0=dT, strat=0.05 * dT, nu_min=0.0, seed=1,
                          precision=precision)
     g = lbm.Lbm(p).init(*f)
     Th, Tl = p["T_wall"][0], p["T_wall"][1]

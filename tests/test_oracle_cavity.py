@@ -28,7 +28,7 @@ def table2():
 
 
 def cavity_results(n, Ra, dT=0.1, chunk=20000, max_steps=240000):
-    p, f = inputs.cavity(n=n, Ra=Ra, dT_over_T0=dT, strat=0.05 * dT, seed=1)
+    p, f = inputs.cavity(n=n, Ra=Ra, dT_over_T0=dT, strat=0.05 * dT, nu_min=0.0, seed=1)
     o = orc.Oracle(p).init(*f)
     Th, Tl = p["T_wall"][0], p["T_wall"][1]
     chi = p["tau_h"] * inputs.RT0  # thermal diffusivity tau_h R T0
