@@ -533,20 +533,42 @@ __device__ __forceinline__ void xedge_writes(const Grid& g, S* __restrict__ dst,
   }
 }
 
+// Moment-space source C-hat of the MRT collision: the correction of Eq. 48,
+// (0, phi_x, 0, 0, 0, 0, 0, phi_y, 0), plus the force of Eq. 51 with
+// a = (0, a_y) (its seventh entry read as 2 (u_x a_x - u_y a_y)).
+template <class C>
+__device__ __forceinline__ void mrt_source(bool corr, C phx, C phy, bool force, C ux, C uy, C ay,
+                                           C mc[9]) {
+#pragma unroll
+  for (int q = 0; q < 9; ++q) mc[q] = C(0);
+  if (corr) {
+    mc[1] = phx;
+    mc[7] = phy;
+  }
+  if (force) {
+    const C uay = uy * ay;
+    mc[1] += C(6) * uay;
+    mc[2] = C(-6) * uay;
+    mc[5] = ay;
+    mc[6] = -ay;
+    mc[7] -= C(2) * uay;
+    mc[8] = ux * ay;
+  }
+}
+
 // MRT collision of f (Eq. 44 with the Appendix B matrices): with n = f - f^eq
-// and the correction (plus force) c in velocity space,
-//   f* = f + M^-1 [ -S M n + (I - S/2) M c ],
+// and the moment-space source mc (mrt_source),
+//   f* = f + M^-1 [ -S M n + (I - S/2) mc ],
 // S = diag(1, s_e, s_eps, 1, s_q, 1, s_q, w_f, w_f) (Eq. 40; the rates of
 // the conserved moments rho and j drop out of the result).
 template <class C>
 __device__ __forceinline__ void mrt_collide(const Phys<C>& k, const C f[9], const C n[9],
-                                            const C c[9], C out[9]) {
-  // moments (rho, e, eps, jx, qx, jy, qy, pxx, pxy) of n and c: rows of M
-  C mn[9], mc[9];
-#pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    const C* q = t ? c : n;
-    C* m = t ? mc : mn;
+                                            const C mc[9], C out[9]) {
+  // moments (rho, e, eps, jx, qx, jy, qy, pxx, pxy) of n: rows of M
+  C mn[9];
+  {
+    const C* q = n;
+    C* m = mn;
     const C sa = (q[1] + q[2]) + (q[3] + q[4]), sd = (q[5] + q[6]) + (q[7] + q[8]);
     const C dx1 = q[1] - q[3], dy1 = q[2] - q[4];
     const C dxd = (q[5] - q[6]) - (q[7] - q[8]), dyd = (q[5] + q[6]) - (q[7] + q[8]);
@@ -636,13 +658,15 @@ __device__ __forceinline__ void collide_store(const Grid& g, S* __restrict__ dst
   const C kz = k.kz;
   C v[27];
   if (g.collision == COLL_MRT) {
-    C fa[9], fneq[9];
+    C fa[9], fneq[9], mc[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       fa[a] = pref<S>(g, a) + d[a];
       fneq[a] = fa[a] - feq[a];
     }
-    mrt_collide<C>(k, fa, fneq, cc, v);
+    mrt_source<C>(g.correction != 0, C(3) * (dqx + dqy), dqx - dqy, g.has_force != 0, ux, uy,
+                  -rho * k.g, mc);
+    mrt_collide<C>(k, fa, fneq, mc, v);
   }
 #pragma unroll
   for (int a = 0; a < 9; ++a) {

@@ -321,14 +321,15 @@ __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, c
 }
 
 // Resident blocks per SM that the register budget is sized for (the shared
-// memory of the ring allows as many): the rare wall branches may spill.
-template <class S, int NPT>
+// memory of the ring allows as many): the rare wall branches may spill.  The
+// MRT collision holds the moment vectors as well and gets a larger budget.
+template <class S, int NPT, int M = 0>
 __host__ __device__ constexpr int pr_min_blocks() {
-  return NPT != 1 ? 1 : (sizeof(S) == 8 ? 3 : 5);
+  return NPT != 1 ? 1 : (sizeof(S) == 8 ? 3 : ((M & MODE_MRT) ? 4 : 5));
 }
 
 template <class S, int NPT, int M>
-__global__ void __launch_bounds__(PR_THREADS, (pr_min_blocks<S, NPT>())) step_pr_kernel(
+__global__ void __launch_bounds__(PR_THREADS, (pr_min_blocks<S, NPT, M>())) step_pr_kernel(
     const Grid g, const __grid_constant__ CUtensorMap map, int rows) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int y0 = blockIdx.y * rows;

@@ -114,8 +114,8 @@ __device__ __forceinline__ void collide_m(const Grid& g, S* __restrict__ p, int 
   C cc[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) cc[a] = C(0);
+  const C phx = C(3) * (dqx + dqy), phy = dqx - dqy;
   if constexpr (MD::corr) {
-    const C phx = C(3) * (dqx + dqy), phy = dqx - dqy;
     const C c13 = phx * C(-1.0 / 36.0) + phy * C(0.25);
     const C c24 = phx * C(-1.0 / 36.0) - phy * C(0.25);
     const C cd = phx * C(1.0 / 18.0);
@@ -143,14 +143,15 @@ __device__ __forceinline__ void collide_m(const Grid& g, S* __restrict__ p, int 
   const C kz = k.kz;
   const C zc = MD::zfull ? C(0.5) * (ux * ux + uy * uy) : C(0);
   if constexpr (MD::mrt) {
-    C fa[9], fneq[9];
+    C fa[9], fneq[9], mc[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       fa[a] = d[a];
       if constexpr (Io<S>::dev) fa[a] += pref<S>(g, a);
       fneq[a] = fa[a] - feq[a];
     }
-    mrt_collide<C>(k, fa, fneq, cc, v);
+    mrt_source<C>(MD::corr, phx, phy, MD::force, ux, uy, -rho * k.g, mc);
+    mrt_collide<C>(k, fa, fneq, mc, v);
   }
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
