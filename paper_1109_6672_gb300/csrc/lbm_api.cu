@@ -235,6 +235,7 @@ void fill_grid(const lbm_params* p, Grid& g) {
     hs += (double)g.href[a];
   }
   g.href_sum = hs;
+  g.dref = hs - p->b / 6.0;
 }
 
 }  // namespace lbm_host

@@ -98,6 +98,7 @@ struct Grid {
   Phys<float> pf;
   float fref[9], href[9];  // rest equilibria (deviation storage)
   double href_sum;         // sum of href in FP64
+  double dref;             // href_sum - b/6 (rounding of the references)
   int* status;             // device error word (bounded waits), may be NULL
   unsigned t;              // time step being taken (stochastic rounding counter)
 };
@@ -114,10 +115,13 @@ __host__ __device__ __forceinline__ const Phys<C>& phys(const Grid& g) {
 
 template <class S>
 struct Io;
+// dev: the buffer holds deviations from the rest equilibria (pref); sr: the
+// stores round stochastically (from_sr).
 template <>
 struct Io<double> {
   using C = double;
   static constexpr bool dev = false;
+  static constexpr bool sr = false;
   __device__ static double ld(const double* p) { return __ldg(p); }
   __device__ static double to(double v) { return v; }
   __device__ static double from(double v) { return v; }
@@ -126,6 +130,7 @@ template <>
 struct Io<float> {
   using C = float;
   static constexpr bool dev = false;
+  static constexpr bool sr = false;
   __device__ static float ld(const float* p) { return __ldg(p); }
   __device__ static float to(float v) { return v; }
   __device__ static float from(float v) { return v; }
@@ -140,6 +145,7 @@ template <>
 struct Io<__half> {
   using C = float;
   static constexpr bool dev = true;
+  static constexpr bool sr = true;
   __device__ static __half ld(const __half* p) { return __ldg(p); }
   __device__ static float to(__half v) { return __half2float(v) * (1.0f / 256.0f); }
   __device__ static __half from(float v) { return __float2half_rn(v * 256.0f); }
@@ -156,6 +162,7 @@ template <>
 struct Io<__nv_bfloat16> {
   using C = float;
   static constexpr bool dev = true;
+  static constexpr bool sr = true;
   __device__ static __nv_bfloat16 ld(const __nv_bfloat16* p) { return __ldg(p); }
   __device__ static float to(__nv_bfloat16 v) { return __bfloat162float(v); }
   __device__ static __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
@@ -203,7 +210,7 @@ __device__ __forceinline__ unsigned sr_bits(unsigned h, int k) {
 // with the random word r).
 template <class S>
 __device__ __forceinline__ S store_val(typename Io<S>::C v, unsigned r) {
-  if constexpr (Io<S>::dev)
+  if constexpr (Io<S>::sr)
     return Io<S>::from_sr(v, r);
   else
     return Io<S>::from(v);
@@ -348,6 +355,56 @@ __device__ __forceinline__ void equilibria_es(C rho, C ux, C uy, C th, C Es, boo
   }
 }
 
+// Equilibria of deviation storage as deviations from the rest equilibria
+// (rho = 1, u = 0, theta = 1, Es = b/6): fd_a = f^eq_a - w_a and
+// hd_a = h^eq_a - href_a from drho = rho - 1, dth = theta - 1 and
+// dEs = Es - b/6, so that only small quantities are rounded:
+//   f^eq_a - w_a = w_a [drho + rho (even_a - 1 + odd_a)],
+//   h^eq_a - href_a = Es (f^eq_a - w_a) + dEs w_a
+//                     + w_a [p (9 eu^2 - 3 u^2 +- 3 eu) + (p th - 1/3)(3 e^2 - 2)/2]
+// (the last line for the total-energy model; p th - 1/3 = (drho + rho dth
+// (2 + dth))/3).  The rest populations are the remainders of the sums
+// sum fd = drho and sum hd = sdh (the sum of the node's h deviations, since
+// rho Es = sum href + sdh), as in equilibria_es.
+template <class C>
+__device__ __forceinline__ void equilibria_dev(C drho, C ux, C uy, C dth, C dEs, C b6, bool total,
+                                               C sdh, C fd[9], C hd[9]) {
+  const C rho = C(1) + drho;
+  const C Es = b6 + dEs;
+  const C usq = ux * ux + uy * uy;
+  const C em1 = C(-1.5) * usq + C(0.5) * dth;  // even part - 1 without 9/2 eu^2: axis
+  const C em2 = C(-1.5) * usq + C(2) * dth;    // diagonal
+  const C lin1 = C(3) - C(1.5) * dth, lin2 = C(3) * (C(1) + dth);
+  const C p = rho * (C(1) + dth) * (C(1) / C(3));
+  const C pt = (drho + rho * dth * (C(2) + dth)) * (C(1) / C(3));  // p th - 1/3
+  const C hu = C(-3) * usq;
+  const C eus[4] = {ux, uy, ux + uy, uy - ux};  // e.u for a = 1, 2, 5, 6
+  const int ia[4] = {1, 2, 5, 6};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int a = ia[k], o = opp(a);
+    const C eu = eus[k];
+    const C w = wgt<C>(a);
+    const C evenm = (k < 2 ? em1 : em2) + C(4.5) * eu * eu;
+    const C odd = (k < 2 ? lin1 : lin2) * eu;
+    fd[a] = w * (drho + rho * (evenm + odd));
+    fd[o] = w * (drho + rho * (evenm - odd));
+    if (total) {
+      const C he = p * (hu + C(9) * eu * eu) + (k < 2 ? C(0.5) : C(2)) * pt;
+      const C ho = p * C(3) * eu;
+      hd[a] = Es * fd[a] + w * (dEs + he + ho);
+      hd[o] = Es * fd[o] + w * (dEs + he - ho);
+    } else {
+      hd[a] = Es * fd[a] + w * dEs;
+      hd[o] = Es * fd[o] + w * dEs;
+    }
+  }
+  const C sf = ((fd[1] + fd[2]) + (fd[3] + fd[4])) + ((fd[5] + fd[6]) + (fd[7] + fd[8]));
+  const C sh = ((hd[1] + hd[2]) + (hd[3] + hd[4])) + ((hd[5] + hd[6]) + (hd[7] + hd[8]));
+  fd[0] = drho - sf;
+  hd[0] = sdh - sh;
+}
+
 // The same from theta alone (Es from b / 6).
 template <class C>
 __device__ __forceinline__ void equilibria(C rho, C ux, C uy, C th, C b6, bool total, C feq[9],
@@ -390,7 +447,7 @@ __device__ void wall_equilibria(const Grid& g, int side, C rho, C ux, C uy, C th
 template <class S>
 __device__ __forceinline__ void put(const Grid& g, S* dst, int a, int x, int y,
                                     typename Io<S>::C v, unsigned h, int k) {
-  dst[slot(g, a, x, y)] = store_val<S>(v - pref<S>(g, a), Io<S>::dev ? sr_bits(h, k) : 0u);
+  dst[slot(g, a, x, y)] = store_val<S>(v - pref<S>(g, a), Io<S>::sr ? sr_bits(h, k) : 0u);
 }
 
 // Ghost-slot writes of a boundary node (x, y): periodic copies and the wall
@@ -406,7 +463,7 @@ __device__ __noinline__ void boundary_writes(const Grid& g, S* __restrict__ dst,
   using C = typename Io<S>::C;
   C fw[9], hw[9];
   int have = -1;
-  const unsigned hs = Io<S>::dev ? sr_hash(g, x, y) : 0u;
+  const unsigned hs = Io<S>::sr ? sr_hash(g, x, y) : 0u;
   for (int a = 1; a < 9; ++a) {
     const int dx = x + ex(a), dy = y + ey(a);
     const int ox = dx < 0 ? 0 : (dx >= g.nx ? 1 : -1);
@@ -486,7 +543,7 @@ __device__ __forceinline__ void xedge_one(const Grid& g, S* __restrict__ dst, in
     const C w = wgt<C>(A);
     const C lin = diag ? C(3) * th : C(3) - C(1.5) * (th - C(1));
     const C fodd = rho * w * lin * euw;  // odd part of f^eq_A at (rho, u_w, theta)
-    const unsigned hs = Io<S>::dev ? sr_hash(g, x, y) : 0u;
+    const unsigned hs = Io<S>::sr ? sr_hash(g, x, y) : 0u;
     put<S>(g, dst, B, dx, dy, v[A] - C(2) * fodd, hs, 18 + B);
     C hin;
     if (g.bc[XS] == BC_ISO) {
@@ -510,7 +567,7 @@ __device__ __forceinline__ void xedge_one(const Grid& g, S* __restrict__ dst, in
   }
   if (EY != 0 && (dy < 0 || dy >= g.ny) && g.bc[dy < 0 ? 2 : 3] != BC_PERIODIC) return;
   const int wx = (dx + g.nx) % g.nx, wy = (dy + g.ny) % g.ny;
-  const unsigned hs = Io<S>::dev ? sr_hash(g, x, y) : 0u;
+  const unsigned hs = Io<S>::sr ? sr_hash(g, x, y) : 0u;
   put<S>(g, dst, A, wx - EX, wy - EY, v[A], hs, A);
   put<S>(g, dst, 9 + A, wx - EX, wy - EY, v[9 + A], hs, 9 + A);
 }
@@ -684,10 +741,10 @@ __device__ __forceinline__ void collide_store(const Grid& g, S* __restrict__ dst
     v[18 + a] = heq[a];
   }
   S* p = dst + slot(g, 0, x, y);
-  unsigned r = Io<S>::dev ? sr_hash(g, x, y) : 0u;
+  unsigned r = Io<S>::sr ? sr_hash(g, x, y) : 0u;
 #pragma unroll
   for (int a = 0; a < NPOP; ++a) {
-    if constexpr (Io<S>::dev) r = lcg_next(r);
+    if constexpr (Io<S>::sr) r = lcg_next(r);
     p[(plane(a) - plane(0)) * g.pitch] = store_val<S>(v[a] - pref<S>(g, a), r);
   }
   if (x == 0 || y == 0 || x == g.nx - 1 || y == g.ny - 1) {

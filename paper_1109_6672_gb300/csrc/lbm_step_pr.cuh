@@ -130,6 +130,7 @@ __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, c
   using C = typename Io<S>::C;
   using G = PrGeom<S, NPT, DD>;
   using SM = PrSmem<S, NPT, DD>;
+  constexpr bool DEV = Io<S>::dev;  // moments carried as deviations (moments_m)
   constexpr int D = G::D, TWC = G::TWC;
   constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
   S* ring = SM::ring(smem);
@@ -205,18 +206,18 @@ __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, c
   C prho[NPT], pux[NPT], puy[NPT], pth[NPT], pes[NPT], pqx[NPT], pqy[NPT], qymm[NPT];
 #pragma unroll
   for (int i = 0; i < NPT; ++i) {
-    prho[i] = 1;
+    prho[i] = DEV ? C(0) : C(1);
     pux[i] = puy[i] = pqx[i] = pqy[i] = qymm[i] = pes[i] = 0;
-    pth[i] = 1;
+    pth[i] = DEV ? C(0) : C(1);
   }
   int qs = 0;  // Q_x slot of the current row
   for (int r = y0 - 1; r <= y1; ++r) {
     C crho[NPT], cux[NPT], cuy[NPT], cth[NPT], ces[NPT], cqx[NPT], cqy[NPT];
 #pragma unroll
     for (int i = 0; i < NPT; ++i) {
-      crho[i] = 1;
+      crho[i] = DEV ? C(0) : C(1);
       cux[i] = cuy[i] = cqx[i] = cqy[i] = ces[i] = 0;
-      cth[i] = 1;
+      cth[i] = DEV ? C(0) : C(1);
     }
     bool ok = true;
     const int k = r - rs;
@@ -244,8 +245,12 @@ __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, c
         else
           pull<S>(g, src, gx, nr, d);
         moments_m<S, M>(g, d, crho[i], cux[i], cuy[i], cth[i], ces[i]);
-        cqx[i] = crho[i] * cux[i] * (C(1) - cth[i]);
-        cqy[i] = crho[i] * cuy[i] * (C(1) - cth[i]);
+        // Q = rho u (1 - theta) (Eq. 48); deviation storage carries rho - 1
+        // and theta - 1 instead of rho and theta
+        const C rq = DEV ? C(1) + crho[i] : crho[i];
+        const C om = DEV ? -cth[i] : C(1) - cth[i];
+        cqx[i] = rq * cux[i] * om;
+        cqy[i] = rq * cuy[i] * om;
       }
     }
     C* qrow = qxs + qs * (TWC + 2);
@@ -269,26 +274,36 @@ __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, c
         C d[NPOP];
         pull_pr<S, NPT>(slot, co[i], d);
         const int lq = t + PR_COMPUTE * i + 1;
+        const C rho_n = DEV ? C(1) + prho[i] : prho[i];
+        const C th_n = DEV ? C(1) + pth[i] : pth[i];
         const C qxl =
-            (c > 0 || !wall_l) ? qprev[lq - 1] : ghost_q<C>(g, 0, 0, prho[i], pth[i], pqx[i]);
+            (c > 0 || !wall_l) ? qprev[lq - 1] : ghost_q<C>(g, 0, 0, rho_n, th_n, pqx[i]);
         const C qxr = (c < nx - 1 || !wall_r) ? qprev[lq + 1]
-                                              : ghost_q<C>(g, 1, 0, prho[i], pth[i], pqx[i]);
+                                              : ghost_q<C>(g, 1, 0, rho_n, th_n, pqx[i]);
         const C qyu =
-            (ro < ny - 1 || !wall_t) ? cqy[i] : ghost_q<C>(g, 3, 1, prho[i], pth[i], pqy[i]);
+            (ro < ny - 1 || !wall_t) ? cqy[i] : ghost_q<C>(g, 3, 1, rho_n, th_n, pqy[i]);
         const C qyd =
-            (ro > 0 || !wall_b) ? qymm[i] : ghost_q<C>(g, 2, 1, prho[i], pth[i], pqy[i]);
+            (ro > 0 || !wall_b) ? qymm[i] : ghost_q<C>(g, 2, 1, rho_n, th_n, pqy[i]);
         C v[27];
         collide_m<S, M>(g, prow + c, pitch, c, ro, d, prho[i], pux[i], puy[i], pth[i], pes[i],
                         C(0.5) * (qxr - qxl), C(0.5) * (qyu - qyd), v);
-        // ghost-slot writes: x edges inline (one thread of a warp), the edge
-        // rows (every thread of the row) through the general routine
-        if (c == 0) xedge_writes<S, 0>(g, dst, c, ro, v, prho[i], pux[i], puy[i], pth[i]);
-        if (c == nx - 1) xedge_writes<S, 1>(g, dst, c, ro, v, prho[i], pux[i], puy[i], pth[i]);
-        if (ro == 0 || ro == ny - 1) {
-          C tmp[27];
+        // ghost-slot writes (from absolute values): x edges inline (one
+        // thread of a warp), the edge rows (every thread of the row) through
+        // the general routine
+        const bool xedge = c == 0 || c == nx - 1, yedge = ro == 0 || ro == ny - 1;
+        if (xedge || yedge) {
+          if constexpr (DEV) {
 #pragma unroll
-          for (int a = 0; a < 27; ++a) tmp[a] = v[a];
-          boundary_writes<S, true>(g, dst, c, ro, tmp, prho[i], pux[i], puy[i], pth[i]);
+            for (int a = 0; a < 27; ++a) v[a] += pref<S>(g, a < 18 ? a : a - 9);
+          }
+          if (c == 0) xedge_writes<S, 0>(g, dst, c, ro, v, rho_n, pux[i], puy[i], th_n);
+          if (c == nx - 1) xedge_writes<S, 1>(g, dst, c, ro, v, rho_n, pux[i], puy[i], th_n);
+          if (yedge) {
+            C tmp[27];
+#pragma unroll
+            for (int a = 0; a < 27; ++a) tmp[a] = v[a];
+            boundary_writes<S, true>(g, dst, c, ro, tmp, rho_n, pux[i], puy[i], th_n);
+          }
         }
       }
     }

@@ -55,11 +55,18 @@ inline int mode_of(const Grid& g) {
 
 // Moments (Eq. 35 with the force shift, Eq. 37 or the Eq. 38 form); deviation
 // storage forms rho E - rho u^2 / 2 in FP64.
+// Moments of the pulled populations d (Eq. 35 with the force shift under
+// Eq. 51; Eq. 37 or the Eq. 38 form for theta).  Absolute storage returns
+// r0 = rho, rth = theta, res = Es (= sum h / rho); deviation storage returns
+// the deviations from the rest state, r0 = rho - 1, rth = theta - 1,
+// res = Es - b/6, formed from the sums of the stored deviations so that
+// nothing is rounded at the scale of the populations.  16-bit storage forms
+// the energy balance rho (Es - b/6) - rho u^2 / 2 in FP64.
 template <class S, int M>
 __device__ __forceinline__ void moments_m(const Grid& g, const typename Io<S>::C d[NPOP],
-                                          typename Io<S>::C& rho, typename Io<S>::C& ux,
-                                          typename Io<S>::C& uy, typename Io<S>::C& th,
-                                          typename Io<S>::C& Es) {
+                                          typename Io<S>::C& r0, typename Io<S>::C& ux,
+                                          typename Io<S>::C& uy, typename Io<S>::C& rth,
+                                          typename Io<S>::C& res) {
   using C = typename Io<S>::C;
   using MD = Mode<M>;
   const Phys<C>& k = phys<C>(g);
@@ -67,11 +74,7 @@ __device__ __forceinline__ void moments_m(const Grid& g, const typename Io<S>::C
   const C sh = (d[9] + d[10]) + (d[11] + d[12]) + (d[13] + d[14]) + (d[15] + d[16]) + d[17];
   const C jx = (d[1] - d[3]) + (d[5] - d[7]) + (d[8] - d[6]);
   C jy = (d[2] - d[4]) + (d[5] - d[7]) + (d[6] - d[8]);
-  if constexpr (Io<S>::dev) {
-    rho = C(1) + sf;  // the f references sum to 1
-  } else {
-    rho = sf;
-  }
+  const C rho = Io<S>::dev ? C(1) + sf : sf;  // the f references sum to 1
   if constexpr (MD::force) jy -= C(0.5) * rho * k.g;
   C inv;
   if constexpr (sizeof(C) == 4)
@@ -81,35 +84,53 @@ __device__ __forceinline__ void moments_m(const Grid& g, const typename Io<S>::C
   ux = jx * inv;
   uy = jy * inv;
   if constexpr (Io<S>::dev) {
-    double e = g.href_sum + (double)sh;
-    Es = (C)e * inv;
-    if constexpr (MD::total) e -= 0.5 * (double)(rho * (ux * ux + uy * uy));
-    th = k.six_b * (C)e * inv;
+    r0 = sf;
+    if constexpr (sizeof(S) == 2) {
+      double e = g.dref + (double)sh - g.pd.b6 * (double)sf;  // rho (Es - b/6)
+      res = (C)e * inv;
+      if constexpr (MD::total) e -= 0.5 * (double)(rho * (ux * ux + uy * uy));
+      rth = k.six_b * (C)e * inv;
+    } else {
+      res = ((C)g.dref + sh - k.b6 * sf) * inv;
+      rth = k.six_b * (MD::total ? res - C(0.5) * (ux * ux + uy * uy) : res);
+    }
   } else if constexpr (MD::total) {
-    Es = sh * inv;
-    th = k.six_b * (Es - C(0.5) * (ux * ux + uy * uy));
+    r0 = rho;
+    res = sh * inv;
+    rth = k.six_b * (res - C(0.5) * (ux * ux + uy * uy));
   } else {
-    Es = sh * inv;
-    th = k.six_b * Es;
+    r0 = rho;
+    res = sh * inv;
+    rth = k.six_b * res;
   }
 }
 
 // Collision (Eq. 34 with +(1 - w_f/2) C', Eq. 36 or Eq. 38; C' = C_a of
-// Eq. 49 plus the Guo force) of one node and its 18 stores at p (node slot,
-// population stride `pitch`).  v receives f*, h*, h^eq for the wall rules.
+// Eq. 49 plus the Guo force; MRT: Eq. 44) of one node and its 18 stores at p
+// (node slot, population stride `pitch`).  (r0, rth, res) as moments_m
+// returns them.  v receives f*, h*, h^eq for the wall rules: absolute values
+// for absolute storage, deviations from the rest equilibria for deviation
+// storage (whose arithmetic then runs on deviations throughout).
 template <class S, int M>
 __device__ __forceinline__ void collide_m(const Grid& g, S* __restrict__ p, int pitch, int x, int y,
-                                          const typename Io<S>::C d[NPOP], typename Io<S>::C rho,
+                                          const typename Io<S>::C d[NPOP], typename Io<S>::C r0,
                                           typename Io<S>::C ux, typename Io<S>::C uy,
-                                          typename Io<S>::C th, typename Io<S>::C Es,
+                                          typename Io<S>::C rth, typename Io<S>::C res,
                                           typename Io<S>::C dqx, typename Io<S>::C dqy,
                                           typename Io<S>::C v[27]) {
   using C = typename Io<S>::C;
   using MD = Mode<M>;
+  constexpr bool DEV = Io<S>::dev;
   const Phys<C>& k = phys<C>(g);
   const C wf = k.omega_f, wh = k.omega_h;
+  const C rho = DEV ? C(1) + r0 : r0;
   C feq[9], heq[9];
-  collision_equilibria<C>(rho, ux, uy, th, Es, k.b6, MD::total, feq, heq);
+  if constexpr (DEV) {
+    const C sdh = (d[9] + d[10]) + (d[11] + d[12]) + (d[13] + d[14]) + (d[15] + d[16]) + d[17];
+    equilibria_dev<C>(r0, ux, uy, rth, res, k.b6, MD::total, sdh, feq, heq);
+  } else {
+    collision_equilibria<C>(rho, ux, uy, rth, res, k.b6, MD::total, feq, heq);
+  }
 
   C cc[9];
 #pragma unroll
@@ -142,12 +163,13 @@ __device__ __forceinline__ void collide_m(const Grid& g, S* __restrict__ p, int 
   const C kc = C(1) - C(0.5) * wf;
   const C kz = k.kz;
   const C zc = MD::zfull ? C(0.5) * (ux * ux + uy * uy) : C(0);
+  // fa, ha: the stored quantity (absolute value or deviation); the
+  // non-equilibrium parts f - f^eq, h - h^eq are the same either way
   if constexpr (MD::mrt) {
     C fa[9], fneq[9], mc[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       fa[a] = d[a];
-      if constexpr (Io<S>::dev) fa[a] += pref<S>(g, a);
       fneq[a] = fa[a] - feq[a];
     }
     mrt_source<C>(MD::corr, phx, phy, MD::force, ux, uy, -rho * k.g, mc);
@@ -155,11 +177,7 @@ __device__ __forceinline__ void collide_m(const Grid& g, S* __restrict__ p, int 
   }
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
-    C fa = d[a], ha = d[9 + a];
-    if constexpr (Io<S>::dev) {
-      fa += pref<S>(g, a);
-      ha += pref<S>(g, 9 + a);
-    }
+    const C fa = d[a], ha = d[9 + a];
     const C fneq = fa - feq[a];
     if constexpr (!MD::mrt) v[a] = fa - wf * fneq + kc * cc[a];
     C hs = ha - wh * (ha - heq[a]);
@@ -170,11 +188,11 @@ __device__ __forceinline__ void collide_m(const Grid& g, S* __restrict__ p, int 
     v[9 + a] = hs;
     v[18 + a] = heq[a];
   }
-  unsigned r = Io<S>::dev ? sr_hash(g, x, y) : 0u;
+  unsigned r = Io<S>::sr ? sr_hash(g, x, y) : 0u;
 #pragma unroll
   for (int a = 0; a < NPOP; ++a) {
-    if constexpr (Io<S>::dev) r = lcg_next(r);
-    p[plane(a) * pitch] = store_val<S>(v[a] - pref<S>(g, a), r);
+    if constexpr (Io<S>::sr) r = lcg_next(r);
+    p[plane(a) * pitch] = store_val<S>(v[a], r);
   }
 }
 
