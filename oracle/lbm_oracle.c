@@ -59,6 +59,7 @@ static const double DIM = 2.0; /* D */
 enum { ORC_PERIODIC = 0, ORC_WALL_ISOTHERMAL = 1, ORC_WALL_ADIABATIC = 2 };
 enum { ORC_E_TOTAL = 0, ORC_E_INTERNAL = 1 };
 enum { ORC_BGK = 0, ORC_MRT = 1 };
+enum { ORC_MU_TAU = 0, ORC_MU_POWER = 1, ORC_MU_SUTHERLAND = 2 };
 
 typedef struct {
   int32_t nx, ny;
@@ -73,6 +74,11 @@ typedef struct {
   int32_t z_full;
   int32_t collision;        /* ORC_BGK: Eq. 34; ORC_MRT: Eqs. 43-45 */
   double s_e, s_eps, s_q;   /* MRT rates of e, epsilon, q in S (Eq. 40); 0: omega_f */
+  int32_t mu_law;           /* ORC_MU_TAU: constant tau (mu = tau_f p, Eq. 30);
+                               ORC_MU_POWER: mu = mu0 theta^n (Eq. 52 premise);
+                               ORC_MU_SUTHERLAND: Eq. 59 referred to T0 */
+  double mu_n;              /* power-law exponent n */
+  double mu_S;              /* Sutherland constant S / T0 */
 } orc_params;
 
 typedef struct {
@@ -326,12 +332,33 @@ static void phase1(orc_state* s, int nthreads) {
   }
 }
 
+/* Relaxation times of a node.  Constant: the given tau_f, tau_h.  With a
+ * temperature-dependent viscosity mu(T) (power law mu0 theta^n, the premise
+ * of Eq. 52; or Sutherland's law, Eq. 59, written relative to T0:
+ * mu = mu0 theta^{3/2} (1 + S/T0)/(theta + S/T0)), mu0 = tau_f R T0 is the
+ * viscosity at rho = 1, T = T0, the BGK relation mu = tau_f p (Eq. 30) gives
+ * tau_f = mu / (rho R T), and the Prandtl number stays tau_f / tau_h. */
+static void node_taus(const orc_params* p, double rho, double th, double* tf, double* tq) {
+  if (p->mu_law == ORC_MU_TAU) {
+    *tf = p->tau_f;
+    *tq = p->tau_h;
+    return;
+  }
+  const double RT0 = p->R * p->T0;
+  const double mu0 = p->tau_f * RT0;
+  double mu;
+  if (p->mu_law == ORC_MU_POWER)
+    mu = mu0 * pow(th, p->mu_n);
+  else
+    mu = mu0 * pow(th, 1.5) * (1.0 + p->mu_S) / (th + p->mu_S);
+  *tf = mu / (rho * RT0 * th);
+  *tq = *tf * (p->tau_h / p->tau_f);
+}
+
 static void phase2(orc_state* s, int nthreads) {
   const orc_params* p = &s->p;
   const int nx = p->nx, ny = p->ny;
   const double RT0 = p->R * p->T0;
-  const double wf = 2.0 / (2.0 * p->tau_f + 1.0); /* omega_f below Eq. 34, dt = 1 */
-  const double wh = 2.0 / (2.0 * p->tau_h + 1.0); /* omega_h below Eq. 36 */
   (void)nthreads;
 #pragma omp parallel for num_threads(nthreads) schedule(static)
   for (int y = 0; y < ny; ++y) {
@@ -339,6 +366,10 @@ static void phase2(orc_state* s, int nthreads) {
       long i = (long)y * nx + x;
       double rho = s->rho[i], ux = s->ux[i], uy = s->uy[i], th = s->theta[i];
       double usq = ux * ux + uy * uy;
+      double tau_f, tau_h;
+      node_taus(p, rho, th, &tau_f, &tau_h);
+      const double wf = 2.0 / (2.0 * tau_f + 1.0); /* omega_f below Eq. 34, dt = 1 */
+      const double wh = 2.0 / (2.0 * tau_h + 1.0); /* omega_h below Eq. 36 */
 
       /* Eq. 50: central differences of Q; Eq. 48-49: C_a. */
       double C[9] = {0};
@@ -405,7 +436,7 @@ static void phase2(orc_state* s, int nthreads) {
        * with tau_hf = tau/(Pr - 1), tau = tau_f + 1/2 the discrete MRT time
        * and Pr = (tau - 1/2)/tau_h. */
       const double kz = p->collision == ORC_MRT
-                            ? (1.0 - 0.5 * wh) * (p->tau_f / p->tau_h - 1.0) / (p->tau_f + 0.5)
+                            ? (1.0 - 0.5 * wh) * (tau_f / tau_h - 1.0) / (tau_f + 0.5)
                             : wh - wf;
       for (int a = 0; a < 9; ++a) {
         double fa = s->f[a][i], ha = s->h[a][i];

@@ -25,6 +25,7 @@ LIB = BUILD / "liblbm_oracle.so"
 PERIODIC, WALL_ISOTHERMAL, WALL_ADIABATIC = 0, 1, 2
 E_TOTAL, E_INTERNAL = 0, 1
 BGK, MRT = 0, 1
+MU_TAU, MU_POWER, MU_SUTHERLAND = 0, 1, 2
 
 
 class OrcParams(ctypes.Structure):
@@ -49,6 +50,9 @@ class OrcParams(ctypes.Structure):
         ("s_e", ctypes.c_double),
         ("s_eps", ctypes.c_double),
         ("s_q", ctypes.c_double),
+        ("mu_law", ctypes.c_int32),
+        ("mu_n", ctypes.c_double),
+        ("mu_S", ctypes.c_double),
     ]
 
 
@@ -118,6 +122,8 @@ def make_params(p: dict) -> OrcParams:
     o.z_full = int(p.get("z_full", 1))
     o.collision = int(p.get("collision", BGK))
     o.s_e, o.s_eps, o.s_q = (float(p.get(k, 0.0)) for k in ("s_e", "s_eps", "s_q"))
+    o.mu_law = int(p.get("mu_law", MU_TAU))
+    o.mu_n, o.mu_S = float(p.get("mu_n", 1.0)), float(p.get("mu_S", 0.0))
     return o
 
 
