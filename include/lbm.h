@@ -76,6 +76,7 @@ enum { LBM_P_FP64 = 0, LBM_P_FP32 = 1, LBM_P_FP32_FP16 = 2, LBM_P_FP32_BF16 = 3 
  * its BGK relaxation with the Eq. 47 coupling, which has the same coefficient
  * as Eq. 36). */
 enum { LBM_COLL_BGK = 0, LBM_COLL_MRT = 1 };
+enum { LBM_MU_TAU = 0, LBM_MU_POWER = 1, LBM_MU_SUTHERLAND = 2 };
 
 typedef struct {
   int32_t nx, ny;           /* fluid nodes per axis, >= 1 (>= 3 on a walled axis)  */
@@ -103,6 +104,16 @@ typedef struct {
                                rate is omega_f (the discrete MRT time is tau_f
                                + 1/2: mu = tau_f p as for BGK); conserved
                                moments relax at rate 1.  Ignored for BGK.     */
+  int32_t mu_law;           /* viscosity: LBM_MU_TAU (0): constant tau_f, tau_h
+                               (mu = tau_f p, Eq. 30); LBM_MU_POWER: mu = mu0
+                               theta^mu_n (the premise of Eq. 52); LBM_MU_SUTHERLAND:
+                               Eq. 59 referred to T0, mu = mu0 theta^(3/2)
+                               (1 + mu_S)/(theta + mu_S).  mu0 = tau_f R T0 (tau_f
+                               is the value at rho = 1, T = T0); per node
+                               tau_f = mu / (rho R T) and tau_h = tau_f / Pr with
+                               Pr = tau_f / tau_h fixed (text before Eq. 52).   */
+  double mu_n;              /* power-law exponent (finite)                      */
+  double mu_S;              /* Sutherland constant S / T0 (> 0 for that law)    */
 } lbm_params;
 
 typedef struct lbm_handle lbm_handle;
@@ -289,7 +300,8 @@ int lbm_set_steps_done(lbm_handle* h, int64_t t);
  * register-pull kernel).  rows_per_block (and the block width of the
  * register-pull kernel) never changes a bit of the result; different variants
  * agree to rounding (different FMA contraction).  Variant 2 is built for the
- * BGK collision only (LBM_ERR_PARAM with LBM_COLL_MRT). */
+ * BGK collision with constant relaxation times only (LBM_ERR_PARAM with
+ * LBM_COLL_MRT or a viscosity law). */
 int lbm_set_launch(lbm_handle* h, int32_t variant, int32_t rows_per_block);
 
 /* Frees the handle and the device memory it owns.  NULL-safe. */

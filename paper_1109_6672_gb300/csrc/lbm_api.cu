@@ -154,6 +154,11 @@ int validate(const lbm_params* p, std::string& why) {
     why = "collision must be LBM_COLL_BGK or LBM_COLL_MRT";
     return LBM_ERR_PARAM;
   }
+  if (p->mu_law < LBM_MU_TAU || p->mu_law > LBM_MU_SUTHERLAND || !std::isfinite(p->mu_n) ||
+      (p->mu_law == LBM_MU_SUTHERLAND && !(p->mu_S > 0.0 && std::isfinite(p->mu_S)))) {
+    why = "mu_law must be LBM_MU_* with a finite mu_n (and mu_S > 0 for Sutherland)";
+    return LBM_ERR_PARAM;
+  }
   if (p->collision == LBM_COLL_MRT) {
     for (double r : {p->s_e, p->s_eps, p->s_q}) {
       if (!(r >= 0.0 && r < 2.0)) {
@@ -200,9 +205,14 @@ void fill_grid(const lbm_params* p, Grid& g) {
   k.kz = p->collision == LBM_COLL_MRT
              ? (1.0 - 0.5 * k.omega_h) * (p->tau_f / p->tau_h - 1.0) / (p->tau_f + 0.5)
              : k.omega_h - k.omega_f;
-  k.se = p->s_e > 0.0 ? p->s_e : k.omega_f;
-  k.seps = p->s_eps > 0.0 ? p->s_eps : k.omega_f;
-  k.sq = p->s_q > 0.0 ? p->s_q : k.omega_f;
+  k.se = p->s_e;
+  k.seps = p->s_eps;
+  k.sq = p->s_q;
+  g.mu_law = p->mu_law;
+  k.tau_f0 = p->tau_f;
+  k.tau_ratio = p->tau_h / p->tau_f;
+  k.mu_n = p->mu_n;
+  k.mu_s = p->mu_S;
   k.g = p->g;
   k.b6 = p->b / 6.0;
   k.six_b = 6.0 / p->b;
@@ -216,6 +226,10 @@ void fill_grid(const lbm_params* p, Grid& g) {
   f.se = (float)k.se;
   f.seps = (float)k.seps;
   f.sq = (float)k.sq;
+  f.tau_f0 = (float)k.tau_f0;
+  f.tau_ratio = (float)k.tau_ratio;
+  f.mu_n = (float)k.mu_n;
+  f.mu_s = (float)k.mu_s;
   for (int s = 0; s < 4; ++s) {
     f.uw[s][0] = (float)k.uw[s][0];
     f.uw[s][1] = (float)k.uw[s][1];
@@ -644,8 +658,9 @@ int lbm_set_launch(lbm_handle* h, int32_t variant, int32_t rows_per_block) {
       rows_per_block < 0)
     return fail(h, LBM_ERR_PARAM,
                 "variant must be 0, 1, 2 or a multiple of 32 in [64, 256]; rows >= 0");
-  if (variant == TMA_PR_2 && h->p.collision == LBM_COLL_MRT)
-    return fail(h, LBM_ERR_PARAM, "variant 2 (two nodes per thread) is built for BGK only");
+  if (variant == TMA_PR_2 && (h->p.collision == LBM_COLL_MRT || h->p.mu_law != LBM_MU_TAU))
+    return fail(h, LBM_ERR_PARAM,
+                "variant 2 (two nodes per thread) is built for BGK with constant tau only");
   h->variant = variant == 0 ? TMA_PR_1 : variant;
   h->rows = rows_per_block;
   return LBM_OK;

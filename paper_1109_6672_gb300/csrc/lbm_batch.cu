@@ -403,7 +403,8 @@ int lbm_batch_add(lbm_batch* b, const lbm_params* p, const double* rho, const do
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
     pool_free(b, off, 2 * buf);
-    return bfail(b, LBM_ERR_CUDA, std::string("grid initialisation failed: ") + cudaGetErrorString(e));
+    return bfail(b, LBM_ERR_CUDA,
+                 std::string("grid initialisation failed: ") + cudaGetErrorString(e));
   }
   lbm_batch::Slot& sl = b->slots[s];
   sl.used = true;

@@ -28,16 +28,17 @@ struct WorkItem {
   int grid, x0, y0, rows;
 };
 
-// Items are grouped by physics mode; group m (0 .. 15, see mode_slot) holds
+// Items are grouped by physics mode; group m (0 .. 31, see mode_slot) holds
 // items [begin[m], end[m]) and is advanced by the kernel instantiated for it.
-constexpr int BATCH_MODE_SLOTS = 2 * NUM_BGK_MODES;
+constexpr int BATCH_MODE_SLOTS = 4 * NUM_BGK_MODES;
 struct BatchCtl {
   int begin[BATCH_MODE_SLOTS], end[BATCH_MODE_SLOTS];
   int dynamic;  // 1: atomic work queue, 0: round-robin
   int counters[BATCH_MODE_SLOTS][BATCH_MAX_SEG];
 };
 
-// Compact index of the physics modes: position in BGK_MODES, + 8 for MRT.
+// Compact index of the physics modes: position in BGK_MODES, + 8 for MRT,
+// + 16 for a temperature-dependent viscosity.
 __host__ __device__ constexpr int bgk_index(int m) {
   return m == (MODE_TOTAL | MODE_ZFULL | MODE_CORR) ? 0
          : m == (MODE_TOTAL | MODE_ZFULL)           ? 1
@@ -49,7 +50,8 @@ __host__ __device__ constexpr int bgk_index(int m) {
                                                     : 7;
 }
 __host__ __device__ constexpr int mode_slot(int m) {
-  return bgk_index(m & ~MODE_MRT) + ((m & MODE_MRT) ? NUM_BGK_MODES : 0);
+  return bgk_index(m & ~(MODE_MRT | MODE_VARMU)) + ((m & MODE_MRT) ? NUM_BGK_MODES : 0) +
+         ((m & MODE_VARMU) ? 2 * NUM_BGK_MODES : 0);
 }
 static_assert(bgk_index(BGK_MODES[0]) == 0 && bgk_index(BGK_MODES[3]) == 3 &&
                   bgk_index(BGK_MODES[5]) == 5 && bgk_index(BGK_MODES[7]) == 7,

@@ -1,0 +1,9 @@
+// Instantiation of the batched step kernels for double storage (a translation
+// unit of its own, so that the step and the batch kernels compile in parallel).
+#include "lbm_step_inst.cuh"
+
+namespace lbm {
+template cudaError_t launch_batch_step<double>(const BatchGrid*, const WorkItem*, BatchCtl*,
+                                           int, int, int, cudaStream_t);
+template int occupancy_batch<double>(int);
+}  // namespace lbm

@@ -74,6 +74,7 @@ __host__ __device__ constexpr int plane(int a) {
 
 // Physical constants in one arithmetic precision (lattice units, R T0 = 1/3).
 enum { COLL_BGK = 0, COLL_MRT = 1 };
+enum { MU_TAU = 0, MU_POWER = 1, MU_SUTHERLAND = 2 };
 
 template <class C>
 struct Phys {
@@ -83,7 +84,9 @@ struct Phys {
   C uw[4][2];          // wall velocities
   C thw[4];            // wall theta = T_w / T0
   C kz;                // coefficient of the Z coupling of h (Eq. 36 / Eq. 47)
-  C se, seps, sq;      // MRT rates of e, epsilon, q (Eq. 40)
+  C se, seps, sq;      // MRT rates of e, epsilon, q (Eq. 40); 0: the node's omega_f
+  C tau_f0, tau_ratio; // tau_f at rho = 1, T = T0 and tau_h / tau_f (viscosity laws)
+  C mu_n, mu_s;        // power-law exponent, Sutherland S / T0
 };
 
 // Per-grid launch argument.
@@ -94,6 +97,7 @@ struct Grid {
   int bc[4];              // x-, x+, y-, y+
   int energy_model, correction, z_full, has_force;
   int collision;          // COLL_BGK or COLL_MRT
+  int mu_law;             // MU_TAU, MU_POWER or MU_SUTHERLAND
   Phys<double> pd;
   Phys<float> pf;
   float fref[9], href[9];  // rest equilibria (deviation storage)
@@ -613,13 +617,40 @@ __device__ __forceinline__ void mrt_source(bool corr, C phx, C phy, bool force, 
   }
 }
 
+// Relaxation rates of a node: the constants for constant tau; with a
+// temperature-dependent viscosity mu(theta) (power law mu0 theta^n, the
+// premise of Eq. 52, or Sutherland's law, Eq. 59 referred to T0) the BGK
+// relation mu = tau_f p (Eq. 30) gives tau_f = tau_f0 (mu / mu0) / (rho theta)
+// and tau_h = tau_f tau_h0 / tau_f0 (constant Pr).  kz: the Z coupling of h
+// (w_h - w_f, Eq. 36; (1 - w_h/2)(Pr - 1)/(tau_f + 1/2), Eq. 47).
+template <class C>
+__device__ __forceinline__ void node_rates(const Grid& g, const Phys<C>& k, C rho, C th, bool mrt,
+                                           C& wf, C& wh, C& kz) {
+  if (g.mu_law == MU_TAU) {
+    wf = k.omega_f;
+    wh = k.omega_h;
+    kz = k.kz;
+    return;
+  }
+  C law;
+  if (g.mu_law == MU_POWER)
+    law = pow(th, k.mu_n);
+  else
+    law = th * sqrt(th) * (C(1) + k.mu_s) / (th + k.mu_s);
+  const C tf = k.tau_f0 * law / (rho * th);
+  const C tq = tf * k.tau_ratio;
+  wf = C(2) / (C(2) * tf + C(1));
+  wh = C(2) / (C(2) * tq + C(1));
+  kz = mrt ? (C(1) - C(0.5) * wh) * (tf / tq - C(1)) / (tf + C(0.5)) : wh - wf;
+}
+
 // MRT collision of f (Eq. 44 with the Appendix B matrices): with n = f - f^eq
 // and the moment-space source mc (mrt_source),
 //   f* = f + M^-1 [ -S M n + (I - S/2) mc ],
 // S = diag(1, s_e, s_eps, 1, s_q, 1, s_q, w_f, w_f) (Eq. 40; the rates of
 // the conserved moments rho and j drop out of the result).
 template <class C>
-__device__ __forceinline__ void mrt_collide(const Phys<C>& k, const C f[9], const C n[9],
+__device__ __forceinline__ void mrt_collide(const Phys<C>& k, C wf, const C f[9], const C n[9],
                                             const C mc[9], C out[9]) {
   // moments (rho, e, eps, jx, qx, jy, qy, pxx, pxy) of n: rows of M
   C mn[9];
@@ -639,8 +670,9 @@ __device__ __forceinline__ void mrt_collide(const Phys<C>& k, const C f[9], cons
     m[7] = (q[1] + q[3]) - (q[2] + q[4]);
     m[8] = (q[5] - q[6]) + (q[7] - q[8]);
   }
-  const C wf = k.omega_f;
-  const C s[9] = {C(1), k.se, k.seps, C(1), k.sq, C(1), k.sq, wf, wf};
+  const C se = k.se > C(0) ? k.se : wf, seps = k.seps > C(0) ? k.seps : wf;
+  const C sq = k.sq > C(0) ? k.sq : wf;
+  const C s[9] = {C(1), se, seps, C(1), sq, C(1), sq, wf, wf};
   C dm[9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) dm[q] = -s[q] * mn[q] + (C(1) - C(0.5) * s[q]) * mc[q];
@@ -675,7 +707,8 @@ __device__ __forceinline__ void collide_store(const Grid& g, S* __restrict__ dst
   using C = typename Io<S>::C;
   const bool total = g.energy_model == E_TOTAL;
   const Phys<C>& k = phys<C>(g);
-  const C wf = k.omega_f, wh = k.omega_h;
+  C wf, wh, kz;
+  node_rates<C>(g, k, rho, th, g.collision == COLL_MRT, wf, wh, kz);
   C feq[9], heq[9];
   collision_equilibria<C>(rho, ux, uy, th, Es, k.b6, total, feq, heq);
 
@@ -712,7 +745,6 @@ __device__ __forceinline__ void collide_store(const Grid& g, S* __restrict__ dst
 
   const C usq = ux * ux + uy * uy;
   const C kc = C(1) - C(0.5) * wf;
-  const C kz = k.kz;
   C v[27];
   if (g.collision == COLL_MRT) {
     C fa[9], fneq[9], mc[9];
@@ -723,7 +755,7 @@ __device__ __forceinline__ void collide_store(const Grid& g, S* __restrict__ dst
     }
     mrt_source<C>(g.correction != 0, C(3) * (dqx + dqy), dqx - dqy, g.has_force != 0, ux, uy,
                   -rho * k.g, mc);
-    mrt_collide<C>(k, fa, fneq, mc, v);
+    mrt_collide<C>(k, wf, fa, fneq, mc, v);
   }
 #pragma unroll
   for (int a = 0; a < 9; ++a) {

@@ -3,9 +3,6 @@
 
 namespace lbm {
 template cudaError_t launch_step_tma<__half>(const Grid&, const CUtensorMap&, int, int, dim3,
-                                          cudaStream_t);
+                                             cudaStream_t);
 template int occupancy_step_tma<__half>(const Grid&, int);
-template cudaError_t launch_batch_step<__half>(const BatchGrid*, const WorkItem*, BatchCtl*, int,
-                                         int, int, cudaStream_t);
-template int occupancy_batch<__half>(int);
 }  // namespace lbm

@@ -3,9 +3,6 @@
 
 namespace lbm {
 template cudaError_t launch_step_tma<double>(const Grid&, const CUtensorMap&, int, int, dim3,
-                                          cudaStream_t);
+                                             cudaStream_t);
 template int occupancy_step_tma<double>(const Grid&, int);
-template cudaError_t launch_batch_step<double>(const BatchGrid*, const WorkItem*, BatchCtl*, int,
-                                         int, int, cudaStream_t);
-template int occupancy_batch<double>(int);
 }  // namespace lbm

@@ -51,14 +51,19 @@ cudaError_t dispatch_from(int mode, Fn& fn) {
   }
 }
 
-template <bool MRT_OK, class Fn>
+template <bool ALL, class Fn>
 cudaError_t dispatch_mode(int mode, Fn&& fn) {
-  if (!(mode & MODE_MRT)) return dispatch_from<0, 0>(mode, fn);
-  if constexpr (MRT_OK) return dispatch_from<0, MODE_MRT>(mode, fn);
+  const int twin = mode & (MODE_MRT | MODE_VARMU);
+  if (twin == 0) return dispatch_from<0, 0>(mode, fn);
+  if constexpr (ALL) {
+    if (twin == MODE_MRT) return dispatch_from<0, MODE_MRT>(mode, fn);
+    if (twin == MODE_VARMU) return dispatch_from<0, MODE_VARMU>(mode, fn);
+    return dispatch_from<0, MODE_MRT | MODE_VARMU>(mode, fn);
+  }
   return cudaErrorInvalidValue;
 }
 
-// The two-node-per-thread variant is built for BGK only.
+// The two-node-per-thread variant is built for BGK with constant tau only.
 template <class S, int NPT>
 cudaError_t launch_mode(const Grid& g, const CUtensorMap& map, int rows, dim3 grid,
                         cudaStream_t stream, int* occ) {

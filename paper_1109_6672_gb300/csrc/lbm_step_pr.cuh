@@ -125,7 +125,8 @@ struct PrNext {
 template <class S, int NPT, int M, int DD = 0>
 __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, const void* src_v,
                                         void* dst_v, int x0, int y0, int rows, unsigned char* smem,
-                                        int kbase, int pre = 0, PrNext next = PrNext{nullptr, 0, 0, 0, 0},
+                                        int kbase, int pre = 0,
+                                        PrNext next = PrNext{nullptr, 0, 0, 0, 0},
                                         int* pre_out = nullptr) {
   using C = typename Io<S>::C;
   using G = PrGeom<S, NPT, DD>;
@@ -337,10 +338,11 @@ __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, c
 
 // Resident blocks per SM that the register budget is sized for (the shared
 // memory of the ring allows as many): the rare wall branches may spill.  The
-// MRT collision holds the moment vectors as well and gets a larger budget.
+// MRT collision (moment vectors) and the per-node relaxation times of a
+// viscosity law get a larger budget.
 template <class S, int NPT, int M = 0>
 __host__ __device__ constexpr int pr_min_blocks() {
-  return NPT != 1 ? 1 : (sizeof(S) == 8 ? 3 : ((M & MODE_MRT) ? 4 : 5));
+  return NPT != 1 ? 1 : (sizeof(S) == 8 ? 3 : ((M & (MODE_MRT | MODE_VARMU)) ? 4 : 5));
 }
 
 template <class S, int NPT, int M>

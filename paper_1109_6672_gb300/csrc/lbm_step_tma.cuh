@@ -14,11 +14,13 @@ namespace lbm {
 
 // ---- compile-time physics mode ---------------------------------------------
 
-enum { MODE_TOTAL = 1, MODE_ZFULL = 2, MODE_CORR = 4, MODE_FORCE = 8, MODE_MRT = 16 };
+enum { MODE_TOTAL = 1, MODE_ZFULL = 2, MODE_CORR = 4, MODE_FORCE = 8, MODE_MRT = 16,
+       MODE_VARMU = 32 };
 
 // The BGK modes mode_of() produces (total energy with the full or simple Z,
 // internal energy with or without gravity; each with or without the
-// correction); each has an MRT twin (| MODE_MRT).
+// correction); each has an MRT twin (| MODE_MRT), and each of those a twin
+// with a temperature-dependent viscosity (| MODE_VARMU).
 constexpr int NUM_BGK_MODES = 8;
 constexpr int BGK_MODES[NUM_BGK_MODES] = {MODE_TOTAL | MODE_ZFULL | MODE_CORR,
                                           MODE_TOTAL | MODE_ZFULL,
@@ -36,6 +38,7 @@ struct Mode {
   static constexpr bool corr = (M & MODE_CORR) != 0;
   static constexpr bool force = (M & MODE_FORCE) != 0;
   static constexpr bool mrt = (M & MODE_MRT) != 0;
+  static constexpr bool varmu = (M & MODE_VARMU) != 0;
 };
 
 // The eight modes the validated parameters can produce (Z only matters for
@@ -50,6 +53,7 @@ inline int mode_of(const Grid& g) {
   }
   if (g.correction) m |= MODE_CORR;
   if (g.collision == COLL_MRT) m |= MODE_MRT;
+  if (g.mu_law != MU_TAU) m |= MODE_VARMU;
   return m;
 }
 
@@ -122,8 +126,9 @@ __device__ __forceinline__ void collide_m(const Grid& g, S* __restrict__ p, int 
   using MD = Mode<M>;
   constexpr bool DEV = Io<S>::dev;
   const Phys<C>& k = phys<C>(g);
-  const C wf = k.omega_f, wh = k.omega_h;
   const C rho = DEV ? C(1) + r0 : r0;
+  C wf = k.omega_f, wh = k.omega_h, kz = k.kz;
+  if constexpr (MD::varmu) node_rates<C>(g, k, rho, DEV ? C(1) + rth : rth, MD::mrt, wf, wh, kz);
   C feq[9], heq[9];
   if constexpr (DEV) {
     const C sdh = (d[9] + d[10]) + (d[11] + d[12]) + (d[13] + d[14]) + (d[15] + d[16]) + d[17];
@@ -161,7 +166,6 @@ __device__ __forceinline__ void collide_m(const Grid& g, S* __restrict__ p, int 
     }
   }
   const C kc = C(1) - C(0.5) * wf;
-  const C kz = k.kz;
   const C zc = MD::zfull ? C(0.5) * (ux * ux + uy * uy) : C(0);
   // fa, ha: the stored quantity (absolute value or deviation); the
   // non-equilibrium parts f - f^eq, h - h^eq are the same either way
@@ -173,7 +177,7 @@ __device__ __forceinline__ void collide_m(const Grid& g, S* __restrict__ p, int 
       fneq[a] = fa[a] - feq[a];
     }
     mrt_source<C>(MD::corr, phx, phy, MD::force, ux, uy, -rho * k.g, mc);
-    mrt_collide<C>(k, fa, fneq, mc, v);
+    mrt_collide<C>(k, wf, fa, fneq, mc, v);
   }
 #pragma unroll
   for (int a = 0; a < 9; ++a) {

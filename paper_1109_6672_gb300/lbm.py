@@ -21,6 +21,7 @@ LBM_BC_PERIODIC, LBM_BC_WALL_ISOTHERMAL, LBM_BC_WALL_ADIABATIC = 0, 1, 2
 LBM_E_TOTAL, LBM_E_INTERNAL = 0, 1
 LBM_P_FP64, LBM_P_FP32, LBM_P_FP32_FP16, LBM_P_FP32_BF16 = 0, 1, 2, 3
 LBM_COLL_BGK, LBM_COLL_MRT = 0, 1
+LBM_MU_TAU, LBM_MU_POWER, LBM_MU_SUTHERLAND = 0, 1, 2
 PRECISION_NAMES = {LBM_P_FP64: "f64", LBM_P_FP32: "f32", LBM_P_FP32_FP16: "f32/f16dev",
                    LBM_P_FP32_BF16: "f32/bf16dev"}
 BYTES_PER_NODE_UPDATE = {LBM_P_FP64: 288, LBM_P_FP32: 144, LBM_P_FP32_FP16: 72,
@@ -37,6 +38,7 @@ class lbm_params(ctypes.Structure):
         ("correction", ctypes.c_int32), ("z_full", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("collision", ctypes.c_int32),
         ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
+        ("mu_law", ctypes.c_int32), ("mu_n", ctypes.c_double), ("mu_S", ctypes.c_double),
     ]
 
 
@@ -134,6 +136,8 @@ def make_params(p: dict) -> lbm_params:
     o.precision = int(p.get("precision", LBM_P_FP64))
     o.collision = int(p.get("collision", LBM_COLL_BGK))
     o.s_e, o.s_eps, o.s_q = (float(p.get(k, 0.0)) for k in ("s_e", "s_eps", "s_q"))
+    o.mu_law = int(p.get("mu_law", LBM_MU_TAU))
+    o.mu_n, o.mu_S = float(p.get("mu_n", 1.0)), float(p.get("mu_S", 0.0))
     return o
 
 
