@@ -65,7 +65,7 @@ inline int mode_of(const Grid& g) {
 // the deviations from the rest state, r0 = rho - 1, rth = theta - 1,
 // res = Es - b/6, formed from the sums of the stored deviations so that
 // nothing is rounded at the scale of the populations.  16-bit storage forms
-// the energy balance rho (Es - b/6) - rho u^2 / 2 in FP64.
+// the balance of internal energy, rho (Es - b/6) - rho u^2 / 2, in FP64.
 template <class S, int M>
 __device__ __forceinline__ void moments_m(const Grid& g, const typename Io<S>::C d[NPOP],
                                           typename Io<S>::C& r0, typename Io<S>::C& ux,
@@ -90,10 +90,14 @@ __device__ __forceinline__ void moments_m(const Grid& g, const typename Io<S>::C
   if constexpr (Io<S>::dev) {
     r0 = sf;
     if constexpr (sizeof(S) == 2) {
-      double e = g.dref + (double)sh - g.pd.b6 * (double)sf;  // rho (Es - b/6)
-      res = (C)e * inv;
-      if constexpr (MD::total) e -= 0.5 * (double)(rho * (ux * ux + uy * uy));
-      rth = k.six_b * (C)e * inv;
+      const C e = (C)g.dref + sh - k.b6 * sf;  // rho (Es - b/6): small terms only
+      res = e * inv;
+      if constexpr (MD::total) {
+        const double ei = (double)e - 0.5 * (double)(rho * (ux * ux + uy * uy));
+        rth = k.six_b * (C)ei * inv;
+      } else {
+        rth = k.six_b * res;
+      }
     } else {
       res = ((C)g.dref + sh - k.b6 * sf) * inv;
       rth = k.six_b * (MD::total ? res - C(0.5) * (ux * ux + uy * uy) : res);
