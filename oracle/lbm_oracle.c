@@ -42,6 +42,20 @@
  *     x-side wall's rule;
  *   - Eq. 50 across a wall uses the mirror ghost Q_g = 2 Q_w - Q(node),
  *     Q_w = rho(node) u_w (1 - theta_w).
+ *
+ * Open x sides for the acoustic set-up of Sec. IV.B (y must be periodic):
+ *   - inlet (side x-): the ghost node one spacing outside (the source of
+ *     the wave) is reset every step to the equilibria of the state of
+ *     Eq. 53 at time t, rho = rho_in + d_rho sin(w t), u = u_wall[0] +
+ *     (d_u sin(w t), 0), T = T_wall[0] + d_T sin(w t); it emits them into the
+ *     first column (populations with e_x = +1), and what leaves the first
+ *     column through that side is dropped;
+ *   - outlet (side x+): zero-gradient extrapolation of (rho, u, T) into the
+ *     ghost column, then non-equilibrium extrapolation; the ghost's
+ *     equilibria equal the last column's, so its post-collision populations
+ *     are those of the last column, which it emits back (e_x = -1);
+ *   - Eq. 50 at the inlet uses the inlet node's Q = rho u (1 - theta), at the
+ *     outlet the last column's own Q (zero gradient).
  */
 #include <math.h>
 #include <stdint.h>
@@ -56,7 +70,8 @@ static const double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 /
                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 static const double DIM = 2.0; /* D */
 
-enum { ORC_PERIODIC = 0, ORC_WALL_ISOTHERMAL = 1, ORC_WALL_ADIABATIC = 2 };
+enum { ORC_PERIODIC = 0, ORC_WALL_ISOTHERMAL = 1, ORC_WALL_ADIABATIC = 2, ORC_INLET = 3,
+       ORC_OUTLET = 4 };
 enum { ORC_E_TOTAL = 0, ORC_E_INTERNAL = 1 };
 enum { ORC_BGK = 0, ORC_MRT = 1 };
 enum { ORC_MU_TAU = 0, ORC_MU_POWER = 1, ORC_MU_SUTHERLAND = 2 };
@@ -79,6 +94,9 @@ typedef struct {
                                ORC_MU_SUTHERLAND: Eq. 59 referred to T0 */
   double mu_n;              /* power-law exponent n */
   double mu_S;              /* Sutherland constant S / T0 */
+  /* inlet (side x-, Eq. 53): rho_in + d_rho sin(w t), u_wall[0] + (d_u sin(w t), 0),
+     T_wall[0] + d_T sin(w t) */
+  double in_rho, in_drho, in_du, in_dT, in_omega;
 } orc_params;
 
 typedef struct {
@@ -88,6 +106,7 @@ typedef struct {
   double *fn[9], *hn[9]; /* next state */
   double *rho, *ux, *uy, *theta, *Qx, *Qy;
   double* es; /* specific energy sum(hbar)/rho: E (Eq. 37) or b R T / 2 (Eq. 38) */
+  long t;     /* steps taken: the time of the current state */
 } orc_state;
 
 /* ---- pointwise pieces (exported so the tests can pin them one by one) ---- */
@@ -246,6 +265,7 @@ void orc_init(orc_state* s, const double* rho, const double* ux, const double* u
               const double* T) {
   const orc_params* p = &s->p;
   double RT0 = p->R * p->T0;
+  s->t = 0;
   for (long i = 0; i < s->n; ++i) {
     double th = T[i] / p->T0;
     double feq[9], heq[9];
@@ -298,6 +318,16 @@ static double wall_theta(const orc_state* s, int side, long i) {
   return s->theta[i];
 }
 
+/* State of the inlet node at time t, Eq. 53 (theta = T / T0). */
+static void inlet_state(const orc_params* p, long t, double* rho, double* ux, double* uy,
+                        double* theta) {
+  double sn = sin(p->in_omega * (double)t);
+  *rho = p->in_rho + p->in_drho * sn;
+  *ux = p->u_wall[0][0] + p->in_du * sn;
+  *uy = p->u_wall[0][1];
+  *theta = (p->T_wall[0] + p->in_dT * sn) / p->T0;
+}
+
 /* Q of the neighbour across one side of node i (Eq. 50 stencil). */
 static double neighbour_Q(const orc_state* s, int x, int y, int side, int comp) {
   const orc_params* p = &s->p;
@@ -312,6 +342,12 @@ static double neighbour_Q(const orc_state* s, int x, int y, int side, int comp) 
     xx = (xx + nx) % nx;
     yy = (yy + ny) % ny;
     return Q[(long)yy * nx + xx];
+  }
+  if (p->bc[side] == ORC_OUTLET) return Q[i]; /* zero gradient */
+  if (p->bc[side] == ORC_INLET) {
+    double r, vx, vy, th;
+    inlet_state(p, s->t, &r, &vx, &vy, &th);
+    return r * (comp == 0 ? vx : vy) * (1.0 - th);
   }
   /* mirror ghost across the wall: Q_g = 2 Q_w - Q(node) */
   double Qw = s->rho[i] * p->u_wall[side][comp] * (1.0 - wall_theta(s, side, i));
@@ -359,6 +395,17 @@ static void phase2(orc_state* s, int nthreads) {
   const orc_params* p = &s->p;
   const int nx = p->nx, ny = p->ny;
   const double RT0 = p->R * p->T0;
+  /* equilibria of the inlet node at this step's time (Eq. 53) */
+  double fin[9], hin[9];
+  if (p->bc[0] == ORC_INLET) {
+    double r, vx, vy, th;
+    inlet_state(p, s->t, &r, &vx, &vy, &th);
+    orc_feq(RT0, r, vx, vy, th, fin);
+    if (p->energy_model == ORC_E_TOTAL)
+      orc_heq(RT0, r, vx, vy, th, 0.5 * (p->b * RT0 * th + vx * vx + vy * vy), fin, hin);
+    else
+      orc_heq_internal(RT0, p->b, th, fin, hin);
+  }
   (void)nthreads;
 #pragma omp parallel for num_threads(nthreads) schedule(static)
   for (int y = 0; y < ny; ++y) {
@@ -455,6 +502,18 @@ static void phase2(orc_state* s, int nthreads) {
 
       /* Streaming (LHS of Eqs. 34 and 36: x + e_a at t + 1). */
       for (int a = 0; a < 9; ++a) {
+        /* open x sides: the inlet node emits its equilibria into the first
+         * column, the outlet ghost (a copy of the last column) emits the
+         * last column's own post-collision values back into it */
+        if (x == 0 && EX[a] == 1 && p->bc[0] == ORC_INLET) {
+          s->fn[a][i] = fin[a];
+          s->hn[a][i] = hin[a];
+        }
+        if (x == nx - 1 && EX[a] == -1 && p->bc[1] == ORC_OUTLET) {
+          long j = (long)((y + EY[a] + ny) % ny) * nx + x;
+          s->fn[a][j] = fs[a];
+          s->hn[a][j] = hs[a];
+        }
         int dx = x + EX[a], dy = y + EY[a];
         int ox = dx < 0 ? 0 : (dx >= nx ? 1 : -1);
         int oy = dy < 0 ? 2 : (dy >= ny ? 3 : -1);
@@ -469,6 +528,7 @@ static void phase2(orc_state* s, int nthreads) {
           s->hn[a][j] = hs[a];
           continue;
         }
+        if (p->bc[side] == ORC_INLET || p->bc[side] == ORC_OUTLET) continue; /* leaves */
         double uwx = p->u_wall[side][0], uwy = p->u_wall[side][1];
         int iso = p->bc[side] == ORC_WALL_ISOTHERMAL;
         if (!have[side]) {
@@ -508,6 +568,7 @@ void orc_step(orc_state* s, long nsteps, int nthreads) {
   for (long t = 0; t < nsteps; ++t) {
     phase1(s, nthreads);
     phase2(s, nthreads);
+    ++s->t;
     for (int a = 0; a < 9; ++a) {
       double* tf = s->f[a];
       s->f[a] = s->fn[a];
@@ -564,3 +625,7 @@ void orc_set_pops(orc_state* s, const double* in) {
 }
 
 int orc_param_size(void) { return (int)sizeof(orc_params); }
+
+/* Time of the current state (steps taken), and setting it (resume). */
+long orc_time(const orc_state* s) { return s->t; }
+void orc_set_time(orc_state* s, long t) { s->t = t; }

@@ -22,7 +22,7 @@ SRC = HERE / "lbm_oracle.c"
 BUILD = HERE / "_build"
 LIB = BUILD / "liblbm_oracle.so"
 
-PERIODIC, WALL_ISOTHERMAL, WALL_ADIABATIC = 0, 1, 2
+PERIODIC, WALL_ISOTHERMAL, WALL_ADIABATIC, INLET, OUTLET = 0, 1, 2, 3, 4
 E_TOTAL, E_INTERNAL = 0, 1
 BGK, MRT = 0, 1
 MU_TAU, MU_POWER, MU_SUTHERLAND = 0, 1, 2
@@ -53,6 +53,11 @@ class OrcParams(ctypes.Structure):
         ("mu_law", ctypes.c_int32),
         ("mu_n", ctypes.c_double),
         ("mu_S", ctypes.c_double),
+        ("in_rho", ctypes.c_double),
+        ("in_drho", ctypes.c_double),
+        ("in_du", ctypes.c_double),
+        ("in_dT", ctypes.c_double),
+        ("in_omega", ctypes.c_double),
     ]
 
 
@@ -94,6 +99,9 @@ def lib() -> ctypes.CDLL:
         _lib.orc_correction.argtypes = [ctypes.c_double, ctypes.c_double, dp]
         _lib.orc_force.argtypes = [ctypes.c_double] * 5 + [dp]
         _lib.orc_param_size.restype = ctypes.c_int
+        _lib.orc_time.restype = ctypes.c_long
+        _lib.orc_time.argtypes = [ctypes.c_void_p]
+        _lib.orc_set_time.argtypes = [ctypes.c_void_p, ctypes.c_long]
         _lib.orc_meq.argtypes = [ctypes.c_double] * 4 + [dp]
         _lib.orc_mrt_matrices.argtypes = [dp, dp]
         assert _lib.orc_param_size() == ctypes.sizeof(OrcParams)
@@ -124,6 +132,9 @@ def make_params(p: dict) -> OrcParams:
     o.s_e, o.s_eps, o.s_q = (float(p.get(k, 0.0)) for k in ("s_e", "s_eps", "s_q"))
     o.mu_law = int(p.get("mu_law", MU_TAU))
     o.mu_n, o.mu_S = float(p.get("mu_n", 1.0)), float(p.get("mu_S", 0.0))
+    o.in_rho = float(p.get("in_rho", 1.0))
+    o.in_drho, o.in_du, o.in_dT, o.in_omega = (
+        float(p.get(k, 0.0)) for k in ("in_drho", "in_du", "in_dT", "in_omega"))
     return o
 
 
@@ -204,6 +215,15 @@ class Oracle:
 
     def step(self, n: int = 1, threads: int = 1):
         lib().orc_step(self._h, int(n), int(threads))
+        return self
+
+    @property
+    def t(self) -> int:
+        """Steps taken (the time of the current state; the inlet of Eq. 53 uses it)."""
+        return int(lib().orc_time(self._h))
+
+    def set_time(self, t: int):
+        lib().orc_set_time(self._h, int(t))
         return self
 
     def moments(self):

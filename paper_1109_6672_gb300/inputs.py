@@ -18,7 +18,7 @@ import math
 
 import numpy as np
 
-PERIODIC, WALL_ISOTHERMAL, WALL_ADIABATIC = 0, 1, 2
+PERIODIC, WALL_ISOTHERMAL, WALL_ADIABATIC, INLET, OUTLET = 0, 1, 2, 3, 4
 E_TOTAL, E_INTERNAL = 0, 1
 P_FP64, P_FP32, P_FP32_FP16, P_FP32_BF16 = 0, 1, 2, 3
 RT0 = 1.0 / 3.0
@@ -138,3 +138,28 @@ def batch_cavities(count: int = 256, seed: int = 4, sides=tuple(range(64, 513, 3
                            nu_min=nu_min)
         out.append((p, fields))
     return out
+
+
+def acoustic_channel(Pr: float = 2.0, gamma: float = 5.0 / 3.0, nx: int = 600, ny: int = 4,
+                     mu: float = 0.1, wavelength: float = 50.0, drho: float = 0.01,
+                     precision: int = P_FP64, **kw):
+    """Attenuation-driven acoustic streaming (Sec. IV.B): a plane sound wave
+    enters a channel periodic in y through an inlet at x- and leaves through a
+    zero-gradient outlet at x+ (600 x 4 nodes).  rho0 = T0 = 1, mu = 0.1
+    (tau_f = mu / p0), wavelength 50, b = 2 / (gamma - 1), total-energy model;
+    the correction term is off, as the paper runs it.  The inlet state is
+    Eq. 53, rho0 + drho sin(w t) and T0 (1 + (gamma - 1) drho/rho0 sin(w t)),
+    with w = 2 pi c_s / wavelength, c_s = sqrt(gamma R T0), and the velocity of
+    the travelling wave, c_s drho/rho0 sin(w t) (the amplitude U of Eq. 54).
+    Starts from uniform rest.  The returned parameters also carry c_s, w and U
+    (keys cs, omega, U) for the analysis."""
+    cs = math.sqrt(gamma * RT0)
+    omega = 2.0 * math.pi * cs / wavelength
+    tau_f = mu / RT0
+    kw.setdefault("correction", 0)
+    p = base_params(nx, ny, tau_f=tau_f, tau_h=tau_f / Pr, b=2.0 / (gamma - 1.0),
+                    bc=[INLET, OUTLET, PERIODIC, PERIODIC], energy_model=E_TOTAL,
+                    precision=precision, in_rho=1.0, in_drho=drho, in_du=cs * drho,
+                    in_dT=(gamma - 1.0) * drho, in_omega=omega, cs=cs, omega=omega,
+                    U=cs * drho, **kw)
+    return p, uniform_fields(nx, ny, seed=0)

@@ -10,7 +10,12 @@ different routes to the same quantities:
   receiving node's side instead of the sending node's side;
 * for the MRT scheme (Sec. III.C.2) the moment basis is built from its
   defining polynomials of the velocity set and inverted numerically, and
-  m^eq is M f^eq rather than Eq. 41.
+  m^eq is M f^eq rather than Eq. 41;
+* the open sides of the acoustic set-up (Sec. IV.B) are applied on the pull:
+  a first-column node takes its e_x = +1 populations from the inlet state of
+  Eq. 53, a last-column node takes its e_x = -1 populations from the ghost
+  column x = nx, whose state is the last column's (zero gradient) and whose
+  non-equilibrium part is the last column's too.
 """
 from __future__ import annotations
 
@@ -20,7 +25,7 @@ EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
 EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
 OPP = np.array([0, 3, 4, 1, 2, 7, 8, 5, 6])
 W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
-PERIODIC, ISO, ADIA = 0, 1, 2
+PERIODIC, ISO, ADIA, INLET, OUTLET = 0, 1, 2, 3, 4
 
 # moments rho, e, eps, jx, qx, jy, qy, pxx, pxy as polynomials of e_a
 _E2 = EX * EX + EY * EY
@@ -69,7 +74,16 @@ class Brute:
     def __init__(self, p: dict):
         self.p = p
         self.nx, self.ny = p["nx"], p["ny"]
+        self.t = 0
         assert abs(p["R"] * p["T0"] - 1 / 3) < 1e-14
+
+    def inlet(self):
+        """Eq. 53 at the current time: rho, u_x, u_y, theta of the inlet node."""
+        p = self.p
+        s = np.sin(p.get("in_omega", 0.0) * self.t)
+        return (p.get("in_rho", 1.0) + p.get("in_drho", 0.0) * s,
+                p["u_wall"][0][0] + p.get("in_du", 0.0) * s, p["u_wall"][0][1],
+                (p["T_wall"][0] + p.get("in_dT", 0.0) * s) / p["T0"])
 
     def init(self, rho, ux, uy, T):
         p = self.p
@@ -109,6 +123,13 @@ class Brute:
             sl = [slice(None), slice(None)]
             sl[axis] = idx
             sl = tuple(sl)
+            if self.p["bc"][side] == OUTLET:
+                arr[sl] = Q[sl]
+                continue
+            if self.p["bc"][side] == INLET:
+                ri, uxi, uyi, ti = self.inlet()
+                arr[sl] = ri * (uxi, uyi)[comp] * (1 - ti)
+                continue
             thw = self._wall_theta(side, th[sl])
             Qw = rho[sl] * self.p["u_wall"][side][comp] * (1 - thw)
             arr[sl] = 2 * Qw - Q[sl]
@@ -117,6 +138,7 @@ class Brute:
     def step(self, n=1):
         for _ in range(n):
             self._step()
+            self.t += 1
         return self
 
     def _step(self):
@@ -171,6 +193,10 @@ class Brute:
             Fn[a] = np.roll(fs[a], (EY[a], EX[a]), axis=(0, 1))
             Hn[a] = np.roll(hs[a], (EY[a], EX[a]), axis=(0, 1))
         nx, ny = self.nx, self.ny
+        ri, uxi, uyi, ti = self.inlet()
+        fin = feq_shells(ri, uxi, uyi, ti)
+        hin = heq_total(ri, uxi, uyi, ti, p["b"], fin) if p["energy_model"] == 0 else heq_internal(
+            ti, p["b"], fin)
         for y in range(ny):
             for x in range(nx):
                 if 0 < x < nx - 1 and 0 < y < ny - 1:
@@ -185,6 +211,13 @@ class Brute:
                     elif out_y >= 0 and p["bc"][out_y] != PERIODIC:
                         side = out_y
                     if side < 0:
+                        continue
+                    if p["bc"][side] == INLET:
+                        Fn[a, y, x], Hn[a, y, x] = fin[a], hin[a]
+                        continue
+                    if p["bc"][side] == OUTLET:
+                        Fn[a, y, x] = fs[a, (y - EY[a]) % ny, nx - 1]
+                        Hn[a, y, x] = hs[a, (y - EY[a]) % ny, nx - 1]
                         continue
                     r, t = rho[y, x], th[y, x]
                     uw = p["u_wall"][side]
