@@ -38,6 +38,20 @@
  *         boundary node's (rho, theta) and the wall velocity;
  *      corners: a population leaving across two walls uses the x-side wall;
  *      Eq. 50 across a wall: mirror ghost Q_g = 2 rho u_w (1 - theta_w) - Q.
+ *  - Open x sides, for the attenuation-driven acoustic streaming of Sec. IV.B
+ *    (y must then be periodic, and correction = 0, as the paper runs it):
+ *      LBM_BC_INLET (x- only): the node one spacing outside the first column
+ *         is reset every step to the equilibria (Eq. 18a, Eq. 18b or the
+ *         Eq. 38 form) of the state of Eq. 53 at the current step t:
+ *         rho = in_rho + in_drho s, u = u_wall[0] + (in_du s, 0),
+ *         T = T_wall[0] + in_dT s, s = sin(in_omega t); it feeds the first
+ *         column, and what leaves the first column through x- is dropped;
+ *      LBM_BC_OUTLET (x+ only): zero-gradient extrapolation of (rho, u, T)
+ *         into the ghost column, then non-equilibrium extrapolation; the
+ *         ghost's equilibria equal the last column's, so the ghost emits the
+ *         last column's own post-collision populations back.
+ *    Each step that touches them ends with a second, small kernel that
+ *    writes these ghost slots.
  */
 #ifndef LBM_H_
 #define LBM_H_
@@ -58,7 +72,13 @@ enum {
   LBM_ERR_STATE = -6      /* call out of order (e.g. lbm_step before lbm_init) */
 };
 
-enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL_ISOTHERMAL = 1, LBM_BC_WALL_ADIABATIC = 2 };
+enum {
+  LBM_BC_PERIODIC = 0,
+  LBM_BC_WALL_ISOTHERMAL = 1,
+  LBM_BC_WALL_ADIABATIC = 2,
+  LBM_BC_INLET = 3, /* x- only, see above */
+  LBM_BC_OUTLET = 4 /* x+ only, see above */
+};
 /* LBM_E_TOTAL: total-energy h, Eq. 18b and Eq. 36 (viscous heating and
  * compression work, Z = e.u - u^2/2 or e.u).  LBM_E_INTERNAL: internal-energy
  * h of Eq. 38 with h^eq = b R T f^eq / 2 and T = 2 sum h / (rho b R). */
@@ -114,6 +134,11 @@ typedef struct {
                                Pr = tau_f / tau_h fixed (text before Eq. 52).   */
   double mu_n;              /* power-law exponent (finite)                      */
   double mu_S;              /* Sutherland constant S / T0 (> 0 for that law)    */
+  double in_rho;            /* LBM_BC_INLET: mean density (> in_drho)           */
+  double in_drho, in_du;    /* density and x-velocity amplitudes (Eq. 53, Eq. 54) */
+  double in_dT;             /* temperature amplitude (< T_wall[0] in magnitude) */
+  double in_omega;          /* angular frequency per step; the phase is taken
+                               from the step count modulo 2^32              */
 } lbm_params;
 
 typedef struct lbm_handle lbm_handle;

@@ -15,6 +15,7 @@
 #include "lbm_device.cuh"
 #include "lbm_host.h"
 #include "lbm_launch.h"
+#include "lbm_open.cuh"
 
 using namespace lbm;
 
@@ -80,8 +81,35 @@ int validate(const lbm_params* p, std::string& why) {
     return LBM_ERR_PARAM;
   }
   for (int s = 0; s < 4; ++s) {
-    if (p->bc[s] < 0 || p->bc[s] > 2) {
-      why = "bc values must be LBM_BC_PERIODIC, LBM_BC_WALL_ISOTHERMAL or LBM_BC_WALL_ADIABATIC";
+    if (p->bc[s] < 0 || p->bc[s] > LBM_BC_OUTLET) {
+      why = "bc values must be one of LBM_BC_*";
+      return LBM_ERR_PARAM;
+    }
+  }
+  const bool inlet = p->bc[0] == LBM_BC_INLET, outlet = p->bc[1] == LBM_BC_OUTLET;
+  if (p->bc[1] == LBM_BC_INLET || p->bc[0] == LBM_BC_OUTLET || p->bc[2] >= LBM_BC_INLET ||
+      p->bc[3] >= LBM_BC_INLET) {
+    why = "LBM_BC_INLET is an x- side only, LBM_BC_OUTLET an x+ side only";
+    return LBM_ERR_PARAM;
+  }
+  if ((inlet || outlet) && p->bc[2] != LBM_BC_PERIODIC) {
+    why = "open x sides (inlet / outlet) need a periodic y axis";
+    return LBM_ERR_PARAM;
+  }
+  if ((inlet || outlet) && p->correction != 0) {
+    why = "open x sides (inlet / outlet) need correction = 0 (as the paper runs them)";
+    return LBM_ERR_PARAM;
+  }
+  if (inlet) {
+    for (double v : {p->in_rho, p->in_drho, p->in_du, p->in_dT, p->in_omega}) {
+      if (!std::isfinite(v)) {
+        why = "inlet parameters must be finite";
+        return LBM_ERR_PARAM;
+      }
+    }
+    if (!(p->in_rho - std::fabs(p->in_drho) > 0.0) ||
+        !(p->T_wall[0] - std::fabs(p->in_dT) > 0.0)) {
+      why = "inlet density and temperature must stay > 0 (in_rho > |in_drho|, T_wall[0] > |in_dT|)";
       return LBM_ERR_PARAM;
     }
   }
@@ -250,6 +278,11 @@ void fill_grid(const lbm_params* p, Grid& g) {
   }
   g.href_sum = hs;
   g.dref = hs - p->b / 6.0;
+  g.in_rho = p->in_rho;
+  g.in_drho = p->in_drho;
+  g.in_du = p->in_du;
+  g.in_dth = p->in_dT / p->T0;
+  g.in_omega = p->in_omega;
 }
 
 }  // namespace lbm_host
@@ -506,6 +539,12 @@ int lbm_step(lbm_handle* h, int64_t n) {
         e = cudaGetLastError();
       } else {
         e = launch_step_tma<S>(g, map, variant, rows, grid, h->stream);
+      }
+      if (e == cudaSuccess && (g.bc[0] == BC_INLET || g.bc[1] == BC_OUTLET)) {
+        // open x sides: their ghost slots of the state just written
+        const int blocks = std::min((h->p.ny + 127) / 128, 1024);
+        open_fixup_kernel<S><<<blocks, 128, 0, h->stream>>>(g, static_cast<S*>(g.dst));
+        e = cudaGetLastError();
       }
       return 0;
     });

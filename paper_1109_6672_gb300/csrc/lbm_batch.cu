@@ -14,6 +14,7 @@
 
 #include "lbm.h"
 #include "lbm_batch.cuh"
+#include "lbm_open.cuh"
 #include "lbm_host.h"
 #include "lbm_launch.h"
 
@@ -51,12 +52,33 @@ struct lbm_batch {
   int rows = 0;      // 0: per-precision default
   int dynamic = 1;   // atomic work queue
   std::vector<int> modes;        // physics modes present in the work list
+  bool has_open = false;         // a grid with an open x side is active
   int occ_mode[BATCH_MODE_SLOTS] = {0};  // resident blocks per SM per mode (0: not queried)
   std::map<std::pair<int64_t, std::vector<int>>, cudaGraphExec_t> graphs;
   std::string err;
 };
 
 namespace {
+
+// A batch at step j of its segment: block b takes grid b if it has an open
+// side and steps at j (the state it wrote is buffer (t0 + j + 1) mod 2).
+template <class S>
+__global__ void __launch_bounds__(128)
+    batch_open_fixup_kernel(const BatchGrid* __restrict__ grids, int j) {
+  __shared__ Grid s_grid;
+  const BatchGrid& bg = grids[blockIdx.x];
+  if (j >= bg.seg_steps || (bg.g.bc[0] != BC_INLET && bg.g.bc[1] != BC_OUTLET)) return;
+  const int* gsrc = reinterpret_cast<const int*>(&bg.g);
+  int* gdst = reinterpret_cast<int*>(&s_grid);
+  for (int i = threadIdx.x; i < (int)(sizeof(Grid) / sizeof(int)); i += blockDim.x)
+    gdst[i] = gsrc[i];
+  __syncthreads();
+  if (threadIdx.x == 0) s_grid.t = (unsigned)(bg.t0 + j);
+  __syncthreads();
+  S* dst = static_cast<S*>(bg.buf[(int)((bg.t0 + j + 1) & 1)]);
+  open_rows<S>(s_grid, dst, threadIdx.x, blockDim.x);
+}
+
 
 thread_local std::string g_batch_create_error;
 
@@ -136,7 +158,9 @@ int rebuild_items(lbm_batch* b) {
   int begin[BATCH_MODE_SLOTS], end[BATCH_MODE_SLOTS];
   for (int m = 0; m < BATCH_MODE_SLOTS; ++m) begin[m] = end[m] = 0;
   b->modes.clear();
+  b->has_open = false;
   for (int s : order) {
+    b->has_open |= b->slots[s].p.bc[0] == LBM_BC_INLET || b->slots[s].p.bc[1] == LBM_BC_OUTLET;
     const lbm_params& p = b->slots[s].p;
     const int mode = b->h_grids[s].mode, ms = mode_slot(mode);
     if (b->modes.empty() || b->modes.back() != mode) {
@@ -211,6 +235,14 @@ cudaError_t launch_all_modes(lbm_batch* b, int j) {
     });
     if (e != cudaSuccess) break;
   }
+  if (e == cudaSuccess && b->has_open) {
+    // open x sides: their ghost slots, once every grid has taken step j
+    e = by_precision(b->precision, [&](auto* tag) {
+      using S = std::remove_pointer_t<decltype(tag)>;
+      batch_open_fixup_kernel<S><<<b->max_grids, 128, 0, b->stream>>>(b->d_grids, j);
+      return cudaGetLastError();
+    });
+  }
   return e;
 }
 
@@ -218,10 +250,12 @@ int* counters_of(lbm_batch* b) {
   return reinterpret_cast<int*>(reinterpret_cast<char*>(b->d_ctl) + offsetof(BatchCtl, counters));
 }
 
-// Graph of k steps (j = 0 .. k-1; one launch per physics mode present)
-// preceded by a reset of the counters.  Cached per (k, modes present).
+// Graph of k steps (j = 0 .. k-1; one launch per physics mode present, plus
+// the open-side fix-up when a grid has one) preceded by a reset of the
+// counters.  Cached per (k, modes present, open sides present).
 int graph_for(lbm_batch* b, int64_t k, cudaGraphExec_t* out) {
-  const auto key = std::make_pair(k, b->modes);
+  auto key = std::make_pair(k, b->modes);
+  if (b->has_open) key.second.push_back(-1);
   auto it = b->graphs.find(key);
   if (it != b->graphs.end()) {
     *out = it->second;

@@ -42,7 +42,10 @@ namespace lbm {
 constexpr int NPOP = 18;
 constexpr int XOFF = 32;  // element offset of x = 0 within a population row
 
-enum { BC_PERIODIC = 0, BC_ISO = 1, BC_ADIA = 2 };
+// BC_INLET / BC_OUTLET: open x sides (x- / x+ only, y periodic).  The step
+// kernels treat them as walls; open_fixup_kernel (lbm_open.cuh) then rewrites
+// their ghost slots.
+enum { BC_PERIODIC = 0, BC_ISO = 1, BC_ADIA = 2, BC_INLET = 3, BC_OUTLET = 4 };
 enum { E_TOTAL = 0, E_INTERNAL = 1 };
 
 // D2Q9 velocities (Eq. 6 with c = 1) and weights (below Eq. 8).
@@ -103,6 +106,9 @@ struct Grid {
   float fref[9], href[9];  // rest equilibria (deviation storage)
   double href_sum;         // sum of href in FP64
   double dref;             // href_sum - b/6 (rounding of the references)
+  // inlet (x-, Eq. 53): rho = in_rho + in_drho s, u = uw[0] + (in_du s, 0),
+  // theta = thw[0] + in_dth s, s = sin(in_omega t)
+  double in_rho, in_drho, in_du, in_dth, in_omega;
   int* status;             // device error word (bounded waits), may be NULL
   unsigned t;              // time step being taken (stochastic rounding counter)
 };

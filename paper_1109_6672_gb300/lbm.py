@@ -18,6 +18,7 @@ LIB_PATH = PKG / "liblbm.so"
 LBM_OK, LBM_ERR_PARAM, LBM_ERR_OOM, LBM_ERR_CUDA = 0, -1, -2, -3
 LBM_ERR_NONFINITE, LBM_ERR_TIMEOUT, LBM_ERR_STATE = -4, -5, -6
 LBM_BC_PERIODIC, LBM_BC_WALL_ISOTHERMAL, LBM_BC_WALL_ADIABATIC = 0, 1, 2
+LBM_BC_INLET, LBM_BC_OUTLET = 3, 4
 LBM_E_TOTAL, LBM_E_INTERNAL = 0, 1
 LBM_P_FP64, LBM_P_FP32, LBM_P_FP32_FP16, LBM_P_FP32_BF16 = 0, 1, 2, 3
 LBM_COLL_BGK, LBM_COLL_MRT = 0, 1
@@ -39,6 +40,8 @@ class lbm_params(ctypes.Structure):
         ("precision", ctypes.c_int32), ("collision", ctypes.c_int32),
         ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
         ("mu_law", ctypes.c_int32), ("mu_n", ctypes.c_double), ("mu_S", ctypes.c_double),
+        ("in_rho", ctypes.c_double), ("in_drho", ctypes.c_double), ("in_du", ctypes.c_double),
+        ("in_dT", ctypes.c_double), ("in_omega", ctypes.c_double),
     ]
 
 
@@ -138,6 +141,9 @@ def make_params(p: dict) -> lbm_params:
     o.s_e, o.s_eps, o.s_q = (float(p.get(k, 0.0)) for k in ("s_e", "s_eps", "s_q"))
     o.mu_law = int(p.get("mu_law", LBM_MU_TAU))
     o.mu_n, o.mu_S = float(p.get("mu_n", 1.0)), float(p.get("mu_S", 0.0))
+    o.in_rho = float(p.get("in_rho", 1.0))
+    o.in_drho, o.in_du, o.in_dT, o.in_omega = (
+        float(p.get(k, 0.0)) for k in ("in_drho", "in_du", "in_dT", "in_omega"))
     return o
 
 

@@ -73,6 +73,22 @@ def test_state_bytes_and_validation_without_gpu(lib):
         assert e.value.status == lbm.LBM_ERR_PARAM
 
 
+def test_open_side_validation_without_gpu(lib):
+    """Inlet x- only, outlet x+ only, periodic y, correction off, inlet state
+    positive."""
+    lbm.load()
+    p, _ = inputs.acoustic_channel(precision=lbm.LBM_P_FP32)
+    assert lbm.lbm_state_bytes(p) > 0
+    assert lbm.lbm_state_bytes(dict(p, bc=[3, 1, 0, 0])) > 0  # inlet facing a wall
+    for bad in (dict(p, bc=[4, 3, 0, 0]), dict(p, bc=[3, 4, 1, 1]), dict(p, bc=[0, 0, 3, 4]),
+                dict(p, bc=[3, 4, 2, 2], ny=8), dict(p, bc=[5, 4, 0, 0]),
+                dict(p, in_drho=1.5), dict(p, in_dT=-1.0), dict(p, in_omega=float("nan")),
+                dict(p, correction=1)):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_state_bytes(bad)
+        assert e.value.status == lbm.LBM_ERR_PARAM
+
+
 def test_status_strings(lib):
     assert lbm.status_string(lbm.LBM_ERR_NONFINITE) == "LBM_ERR_NONFINITE"
     assert lbm.status_string(0) == "LBM_OK"

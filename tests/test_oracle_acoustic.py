@@ -149,3 +149,21 @@ def test_resume_with_time_equals_straight_run():
     third = O.Oracle(p).init(*f)
     third.set_pops(first.pops()).step(13)
     assert not np.array_equal(third.pops(), straight)
+
+
+@pytest.mark.parametrize("Pr,gamma,grows", [(0.2, 5 / 3, False), (2.0, 9 / 7, False),
+                                            (2.0, 5 / 3, True)])
+def test_transverse_stability_of_the_channel(Pr, gamma, grows):
+    """The channel's 1-D wave is stable against a transverse disturbance only
+    where the scheme is stable in 2-D: with b = 3 the total-energy h needs
+    tau_h above about 0.3 at tau_f = 0.3, so the paper's Pr >= 1, gamma = 5/3
+    cases hold only while every row stays identical (FP64, FP32; not 16-bit
+    storage, whose stochastic rounding differs from node to node)."""
+    p, (rho, ux, uy, T) = inputs.acoustic_channel(Pr=Pr, gamma=gamma, nx=200)
+    uy = uy + 1e-7 * np.random.default_rng(3).standard_normal(uy.shape)
+    o = O.Oracle(p).init(rho, ux, uy, T).step(300, threads=4)
+    v = o.moments()[2]
+    if grows:
+        assert not np.isfinite(v).all() or np.abs(v).max() > 1e-3
+    else:
+        assert np.abs(v).max() < 1e-7
