@@ -32,7 +32,8 @@
  *      f: halfway bounce-back plus twice the odd part of Eq. 18a evaluated at
  *         the boundary node's rho and theta and the wall velocity;
  *      h, isothermal wall: non-equilibrium extrapolation from a ghost node one
- *         spacing outside, with u_g = 2 u_w - u, theta_g = 2 theta_w - theta,
+ *         spacing outside, with u_g = 2 u_w - u, theta_g = max(2 theta_w - theta,
+ *         theta_w / 2),
  *         rho_g = rho theta / theta_g;
  *      h, adiabatic wall: bounce-back plus twice the odd part of h^eq at the
  *         boundary node's (rho, theta) and the wall velocity;

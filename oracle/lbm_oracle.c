@@ -33,8 +33,9 @@
  *   - h on isothermal walls: non-equilibrium extrapolation (the paper's wall
  *     method, ref. [45]) from a ghost node one spacing outside the node, with
  *     u_g = 2 u_w - u, theta_g = 2 theta_w - theta (linear through the wall
- *     value at the halfway point) and rho_g = rho theta / theta_g (equal
- *     pressure across the wall): h_in = h^eq(ghost) + (h* - h^eq)(node);
+ *     value at the halfway point), floored at theta_w / 2, and
+ *     rho_g = rho theta / theta_g (equal pressure across the wall):
+ *     h_in = h^eq(ghost) + (h* - h^eq)(node);
  *   - h on adiabatic walls: bounce-back plus twice the odd part of h^eq at
  *     (rho, u_w, theta) of the node (zero total-energy flux through a wall at
  *     rest);
@@ -535,7 +536,11 @@ static void phase2(orc_state* s, int nthreads) {
           double thw = wall_theta(s, side, i);
           orc_feq(RT0, rho, uwx, uwy, th, fw[side]);
           /* h: ghost state for isothermal walls, wall state for adiabatic. */
-          double thg = iso ? 2.0 * thw - th : th;
+          /* linear through the wall value, floored at half of it: a node
+           * more than 1.5 times hotter than the wall would otherwise give
+           * the ghost a vanishing or negative temperature, where the
+           * equal-pressure ghost density diverges */
+          double thg = iso ? fmax(2.0 * thw - th, 0.5 * thw) : th;
           double rg = iso ? rho * th / thg : rho;
           double ugx = iso ? 2.0 * uwx - ux : uwx;
           double ugy = iso ? 2.0 * uwy - uy : uwy;

@@ -446,7 +446,7 @@ __device__ void wall_equilibria(const Grid& g, int side, C rho, C ux, C uy, C th
   C tmp[9];
   equilibria<C>(rho, uwx, uwy, th, k.b6, total, fw, tmp);
   if (g.bc[side] == BC_ISO) {
-    const C thg = C(2) * k.thw[side] - th;
+    const C thg = fmax(C(2) * k.thw[side] - th, C(0.5) * k.thw[side]);  // floored: see xedge_one
     const C rg = rho * th / thg;
     equilibria<C>(rg, C(2) * uwx - ux, C(2) * uwy - uy, thg, k.b6, total, tmp, hw);
   } else {
@@ -557,7 +557,9 @@ __device__ __forceinline__ void xedge_one(const Grid& g, S* __restrict__ dst, in
     put<S>(g, dst, B, dx, dy, v[A] - C(2) * fodd, hs, 18 + B);
     C hin;
     if (g.bc[XS] == BC_ISO) {
-      const C thg = C(2) * k.thw[XS] - th;
+      // ghost temperature linear through the wall value, floored at half of
+      // it (the equal-pressure ghost density diverges as it vanishes)
+      const C thg = fmax(C(2) * k.thw[XS] - th, C(0.5) * k.thw[XS]);
       C fg, hg;
       eq_dir<C, ex(B), ey(B)>(rho * th / thg, C(2) * uwx - ux, C(2) * uwy - uy, thg, k.b6, total,
                               fg, hg);

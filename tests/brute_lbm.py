@@ -229,7 +229,7 @@ class Brute:
                     if iso:
                         # ghost node one spacing outside: linear in u and theta
                         # through the wall, equal pressure
-                        tg = 2 * thw - t
+                        tg = max(2 * thw - t, 0.5 * thw)
                         rg, ugx, ugy = r * t / tg, 2 * uw[0] - ux[y, x], 2 * uw[1] - uy[y, x]
                         fg = feq_shells(rg, ugx, ugy, tg)
                         hg = (heq_total(rg, ugx, ugy, tg, p["b"], fg) if p["energy_model"] == 0
