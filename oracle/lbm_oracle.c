@@ -57,6 +57,24 @@
  *     are those of the last column, which it emits back (e_x = -1);
  *   - Eq. 50 at the inlet uses the inlet node's Q = rho u (1 - theta), at the
  *     outlet the last column's own Q (zero gradient).
+ *
+ * Walls of non-equilibrium extrapolation (the paper's wall method, ref. [45];
+ * a side whose bit is set in wall_nee): the wall sits on the ghost node G one
+ * spacing outside the boundary node F.  G's state is the wall velocity,
+ * theta_G (theta_w on an isothermal wall; on an adiabatic one zero normal
+ * gradient at G to second order, (4 theta_F - theta_F2)/3 with F2 the next
+ * node inward) and F's pressure (rho_G = rho_F theta_F / theta_G: p = rho R T,
+ * so equal density would push mass through the wall).  Its pre-collision
+ * populations are its equilibria plus F's non-equilibrium part
+ * fbar(F) - f^eq(F) (likewise for h), and it collides like any node, with
+ * the Guo force of its own density and no correction term; G emits the
+ * post-collision populations pointing into the domain, and what leaves
+ * through the side is dropped.
+ * Along an axis that is not periodic the corner ghost at the end of an x
+ * side's column emits its one inward diagonal into the corner node from that
+ * node's values (the x side wins, as for the halfway rules); a y side's
+ * ghosts emit nothing across an x side that is not periodic.  Eq. 50 across
+ * such a wall keeps the mirror ghost of the halfway rules.
  */
 #include <math.h>
 #include <stdint.h>
@@ -98,6 +116,9 @@ typedef struct {
   /* inlet (side x-, Eq. 53): rho_in + d_rho sin(w t), u_wall[0] + (d_u sin(w t), 0),
      T_wall[0] + d_T sin(w t) */
   double in_rho, in_drho, in_du, in_dT, in_omega;
+  /* bit s set: side s is a wall of non-equilibrium extrapolation on the
+     ghost node one spacing outside (instead of the halfway rules) */
+  int32_t wall_nee;
 } orc_params;
 
 typedef struct {
@@ -392,6 +413,87 @@ static void node_taus(const orc_params* p, double rho, double th, double* tf, do
   *tq = *tf * (p->tau_h / p->tau_f);
 }
 
+/* Equilibria a node relaxes to: Eq. 18a and Eq. 18b with the specific
+ * energy es (or es f^eq, Eq. 38), rest populations from the moment sums. */
+static void node_equilibria(const orc_params* p, double rho, double ux, double uy, double th,
+                            double es, double feq[9], double heq[9]) {
+  const double RT0 = p->R * p->T0;
+  orc_feq(RT0, rho, ux, uy, th, feq);
+  if (p->energy_model == ORC_E_TOTAL) {
+    orc_heq(RT0, rho, ux, uy, th, es, feq, heq);
+  } else {
+    for (int a = 0; a < 9; ++a) heq[a] = es * feq[a];
+  }
+  double sf = 0.0, sh = 0.0;
+  for (int a = 1; a < 9; ++a) {
+    sf += feq[a];
+    sh += heq[a];
+  }
+  feq[0] = rho - sf;
+  heq[0] = rho * es - sh;
+}
+
+/* Collision of one node (phase 2 below): from its pre-collision fbar, hbar,
+ * moments (rho, u, theta, es = sum(hbar)/rho) and source C (correction plus
+ * force), the equilibria feq, heq it relaxes to and its post-collision fs, hs. */
+static void collide(const orc_params* p, double rho, double ux, double uy, double th, double es,
+                    const double fb[9], const double hb[9], const double C[9], double feq[9],
+                    double heq[9], double fs[9], double hs[9]) {
+  double usq = ux * ux + uy * uy;
+  double tau_f, tau_h;
+  node_taus(p, rho, th, &tau_f, &tau_h);
+  const double wf = 2.0 / (2.0 * tau_f + 1.0); /* omega_f below Eq. 34, dt = 1 */
+  const double wh = 2.0 / (2.0 * tau_h + 1.0); /* omega_h below Eq. 36 */
+
+  /* Equilibria at the node's moments.  The energy they carry is the one
+   * recovered from hbar: E = sum(hbar)/rho (Eq. 37) in Eq. 18b, and
+   * b R T / 2 = sum(hbar)/rho (Eq. 38) for the internal-energy model, so
+   * that the relaxation returns exactly the energy it was given; the rest
+   * populations follow from the moment sums of Eqs. 19a/19b,
+   * sum f^eq = rho and sum h^eq = rho E, so that no rounding of the
+   * weights biases mass or energy step after step. */
+  node_equilibria(p, rho, ux, uy, th, es, feq, heq);
+
+  /* Collision of f.  BGK: Eq. 34 ("+(1 - w_f/2) C" from Eqs. 32-33).  MRT:
+   * Eq. 44 in moment space with m = M f (the stored f is f-hat of
+   * Eq. 43), m^eq of Eq. 41, C-hat = M C and S of Eq. 40; the shear rate
+   * 1/tau_f of Eq. 40 is omega_f (the discrete MRT time is the
+   * continuous tau_f plus 1/2, mu = (tau - 1/2) p), tau_rho = tau_j = 1
+   * (the rates of conserved moments drop out); then f* = M^-1 m*. */
+  if (p->collision == ORC_MRT) {
+    double fh[9], m[9], meq[9], Ch[9], ms[9];
+    double S[9] = {1.0, p->s_e > 0 ? p->s_e : wf, p->s_eps > 0 ? p->s_eps : wf, 1.0,
+                   p->s_q > 0 ? p->s_q : wf, 1.0, p->s_q > 0 ? p->s_q : wf, wf, wf};
+    for (int a = 0; a < 9; ++a) fh[a] = fb[a];
+    matvec9(MRT_M, fh, m);
+    orc_meq(rho, ux, uy, th, meq);
+    matvec9(MRT_M, C, Ch);
+    for (int k = 0; k < 9; ++k) ms[k] = m[k] - S[k] * (m[k] - meq[k]) + (1.0 - 0.5 * S[k]) * Ch[k];
+    matvec9(MRT_MINV, ms, fs);
+  } else {
+    for (int a = 0; a < 9; ++a) {
+      double fa = fb[a];
+      fs[a] = fa - wf * (fa - feq[a]) + (1.0 - 0.5 * wf) * C[a];
+    }
+  }
+  /* Collision of h: Eq. 36 (BGK) or Eq. 47 (MRT), or Eq. 38 (internal
+   * energy, no coupling).  The Eq. 47 coupling (1 - w_h/2) Z / tau_hf
+   * with tau_hf = tau/(Pr - 1), tau = tau_f + 1/2 the discrete MRT time
+   * and Pr = (tau - 1/2)/tau_h. */
+  const double kz = p->collision == ORC_MRT
+                        ? (1.0 - 0.5 * wh) * (tau_f / tau_h - 1.0) / (tau_f + 0.5)
+                        : wh - wf;
+  for (int a = 0; a < 9; ++a) {
+    double fa = fb[a], ha = hb[a];
+    hs[a] = ha - wh * (ha - heq[a]);
+    if (p->energy_model == ORC_E_TOTAL) {
+      double eu = EX[a] * ux + EY[a] * uy;
+      double Z = p->z_full ? eu - 0.5 * usq : eu;
+      hs[a] += kz * Z * (fa - feq[a] + 0.5 * C[a]);
+    }
+  }
+}
+
 static void phase2(orc_state* s, int nthreads) {
   const orc_params* p = &s->p;
   const int nx = p->nx, ny = p->ny;
@@ -413,12 +515,6 @@ static void phase2(orc_state* s, int nthreads) {
     for (int x = 0; x < nx; ++x) {
       long i = (long)y * nx + x;
       double rho = s->rho[i], ux = s->ux[i], uy = s->uy[i], th = s->theta[i];
-      double usq = ux * ux + uy * uy;
-      double tau_f, tau_h;
-      node_taus(p, rho, th, &tau_f, &tau_h);
-      const double wf = 2.0 / (2.0 * tau_f + 1.0); /* omega_f below Eq. 34, dt = 1 */
-      const double wh = 2.0 / (2.0 * tau_h + 1.0); /* omega_h below Eq. 36 */
-
       /* Eq. 50: central differences of Q; Eq. 48-49: C_a. */
       double C[9] = {0};
       if (p->correction) {
@@ -431,70 +527,13 @@ static void phase2(orc_state* s, int nthreads) {
       orc_force(RT0, ux, uy, 0.0, -rho * p->g, F);
       for (int a = 0; a < 9; ++a) C[a] += F[a];
 
-      /* Equilibria at the node's moments.  The energy they carry is the one
-       * recovered from hbar: E = sum(hbar)/rho (Eq. 37) in Eq. 18b, and
-       * b R T / 2 = sum(hbar)/rho (Eq. 38) for the internal-energy model, so
-       * that the relaxation returns exactly the energy it was given; the rest
-       * populations follow from the moment sums of Eqs. 19a/19b,
-       * sum f^eq = rho and sum h^eq = rho E, so that no rounding of the
-       * weights biases mass or energy step after step. */
-      double feq[9], heq[9];
-      const double es = s->es[i];
-      orc_feq(RT0, rho, ux, uy, th, feq);
-      if (p->energy_model == ORC_E_TOTAL) {
-        orc_heq(RT0, rho, ux, uy, th, es, feq, heq);
-      } else {
-        for (int a = 0; a < 9; ++a) heq[a] = es * feq[a];
-      }
-      {
-        double sf = 0.0, sh = 0.0;
-        for (int a = 1; a < 9; ++a) {
-          sf += feq[a];
-          sh += heq[a];
-        }
-        feq[0] = rho - sf;
-        heq[0] = rho * es - sh;
-      }
-
-      /* Collision of f.  BGK: Eq. 34 ("+(1 - w_f/2) C" from Eqs. 32-33).  MRT:
-       * Eq. 44 in moment space with m = M f (the stored f is f-hat of
-       * Eq. 43), m^eq of Eq. 41, C-hat = M C and S of Eq. 40; the shear rate
-       * 1/tau_f of Eq. 40 is omega_f (the discrete MRT time is the
-       * continuous tau_f plus 1/2, mu = (tau - 1/2) p), tau_rho = tau_j = 1
-       * (the rates of conserved moments drop out); then f* = M^-1 m*. */
-      double fs[9], hs[9];
-      if (p->collision == ORC_MRT) {
-        double fh[9], m[9], meq[9], Ch[9], ms[9];
-        double S[9] = {1.0, p->s_e > 0 ? p->s_e : wf, p->s_eps > 0 ? p->s_eps : wf, 1.0,
-                       p->s_q > 0 ? p->s_q : wf, 1.0, p->s_q > 0 ? p->s_q : wf, wf, wf};
-        for (int a = 0; a < 9; ++a) fh[a] = s->f[a][i];
-        matvec9(MRT_M, fh, m);
-        orc_meq(rho, ux, uy, th, meq);
-        matvec9(MRT_M, C, Ch);
-        for (int k = 0; k < 9; ++k) ms[k] = m[k] - S[k] * (m[k] - meq[k]) + (1.0 - 0.5 * S[k]) * Ch[k];
-        matvec9(MRT_MINV, ms, fs);
-      } else {
-        for (int a = 0; a < 9; ++a) {
-          double fa = s->f[a][i];
-          fs[a] = fa - wf * (fa - feq[a]) + (1.0 - 0.5 * wf) * C[a];
-        }
-      }
-      /* Collision of h: Eq. 36 (BGK) or Eq. 47 (MRT), or Eq. 38 (internal
-       * energy, no coupling).  The Eq. 47 coupling (1 - w_h/2) Z / tau_hf
-       * with tau_hf = tau/(Pr - 1), tau = tau_f + 1/2 the discrete MRT time
-       * and Pr = (tau - 1/2)/tau_h. */
-      const double kz = p->collision == ORC_MRT
-                            ? (1.0 - 0.5 * wh) * (tau_f / tau_h - 1.0) / (tau_f + 0.5)
-                            : wh - wf;
+      /* equilibria and collision of the node */
+      double fb[9], hb[9], feq[9], heq[9], fs[9], hs[9];
       for (int a = 0; a < 9; ++a) {
-        double fa = s->f[a][i], ha = s->h[a][i];
-        hs[a] = ha - wh * (ha - heq[a]);
-        if (p->energy_model == ORC_E_TOTAL) {
-          double eu = EX[a] * ux + EY[a] * uy;
-          double Z = p->z_full ? eu - 0.5 * usq : eu;
-          hs[a] += kz * Z * (fa - feq[a] + 0.5 * C[a]);
-        }
+        fb[a] = s->f[a][i];
+        hb[a] = s->h[a][i];
       }
+      collide(p, rho, ux, uy, th, s->es[i], fb, hb, C, feq, heq, fs, hs);
 
       /* Wall (f, adiabatic h) and ghost (isothermal h) equilibria for the up
        * to two sides this node touches. */
@@ -530,6 +569,7 @@ static void phase2(orc_state* s, int nthreads) {
           continue;
         }
         if (p->bc[side] == ORC_INLET || p->bc[side] == ORC_OUTLET) continue; /* leaves */
+        if (p->wall_nee >> side & 1) continue; /* leaves; the ghost node emits below */
         double uwx = p->u_wall[side][0], uwy = p->u_wall[side][1];
         int iso = p->bc[side] == ORC_WALL_ISOTHERMAL;
         if (!have[side]) {
@@ -562,6 +602,69 @@ static void phase2(orc_state* s, int nthreads) {
         } else {
           double B = 0.5 * (hw[side][b] - hw[side][a]); /* odd part of h^eq */
           s->hn[b][i] = hs[a] + 2.0 * B;
+        }
+      }
+
+      /* Walls of non-equilibrium extrapolation touching this node. */
+      for (int side = 0; side < 4; ++side) {
+        if (!(p->wall_nee >> side & 1)) continue;
+        const int on = side == 0 ? x == 0 : side == 1 ? x == nx - 1 : side == 2 ? y == 0 : y == ny - 1;
+        if (!on) continue;
+        const int nxo = side == 0 ? -1 : side == 1 ? 1 : 0; /* outward normal */
+        const int nyo = side == 2 ? -1 : side == 3 ? 1 : 0;
+        /* wall temperature: given (isothermal), or zero normal gradient at
+         * the wall node to second order, from F and the next node inward */
+        double thG;
+        if (p->bc[side] == ORC_WALL_ISOTHERMAL) {
+          thG = p->T_wall[side] / p->T0;
+        } else {
+          const long i2 = (long)(y - nyo) * nx + (x - nxo);
+          thG = (4.0 * th - s->theta[i2]) / 3.0;
+        }
+        const double uwx = p->u_wall[side][0], uwy = p->u_wall[side][1];
+        /* the wall node: F's pressure, the wall's velocity, theta_G; its
+         * pre-collision populations are its equilibria plus F's
+         * non-equilibrium part, and it collides like any node, with the
+         * force of its own density (no correction term) */
+        const double rG = rho * th / thG;
+        const double esG = 0.5 * (p->b * RT0 * thG +
+                                  (p->energy_model == ORC_E_TOTAL ? uwx * uwx + uwy * uwy : 0.0));
+        double eqfG[9], eqhG[9], fbG[9], hbG[9], CG[9], fG[9], hG[9], dummyf[9], dummyh[9];
+        node_equilibria(p, rG, uwx, uwy, thG, esG, eqfG, eqhG);
+        for (int a = 0; a < 9; ++a) {
+          fbG[a] = eqfG[a] + (fb[a] - feq[a]);
+          hbG[a] = eqhG[a] + (hb[a] - heq[a]);
+        }
+        orc_force(RT0, uwx, uwy, 0.0, -rG * p->g, CG);
+        collide(p, rG, uwx, uwy, thG, esG, fbG, hbG, CG, dummyf, dummyh, fG, hG);
+        /* ghosts emitting into the domain: G = F - n (every inward a), and
+         * for an x side along a walled y axis the corner ghost beyond F */
+        for (int k = 0; k < 3; ++k) {
+          const int gx = x + nxo, gy = y + nyo + (k == 1 ? -1 : k == 2 ? 1 : 0) * (side < 2);
+          if (k > 0 && side >= 2) break;
+          for (int a = 1; a < 9; ++a) {
+            if (EX[a] * nxo + EY[a] * nyo >= 0) continue; /* not inward */
+            int dx = gx + EX[a], dy = gy + EY[a];
+            if (k > 0) {
+              /* corner ghost: only its diagonal into F, and only across a
+               * walled y side */
+              if (dx != x || dy != y) continue;
+              const int ys = gy < 0 ? 2 : 3;
+              if ((gy >= 0 && gy < ny) || p->bc[ys] == ORC_PERIODIC) continue;
+            } else {
+              if (dx < 0 || dx >= nx) {
+                if (p->bc[dx < 0 ? 0 : 1] != ORC_PERIODIC) continue;
+                dx = (dx + nx) % nx;
+              }
+              if (dy < 0 || dy >= ny) {
+                if (p->bc[dy < 0 ? 2 : 3] != ORC_PERIODIC) continue;
+                dy = (dy + ny) % ny;
+              }
+            }
+            const long j = (long)dy * nx + dx;
+            s->fn[a][j] = fG[a];
+            s->hn[a][j] = hG[a];
+          }
         }
       }
     }

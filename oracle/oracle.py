@@ -58,6 +58,7 @@ class OrcParams(ctypes.Structure):
         ("in_du", ctypes.c_double),
         ("in_dT", ctypes.c_double),
         ("in_omega", ctypes.c_double),
+        ("wall_nee", ctypes.c_int32),
     ]
 
 
@@ -135,6 +136,7 @@ def make_params(p: dict) -> OrcParams:
     o.in_rho = float(p.get("in_rho", 1.0))
     o.in_drho, o.in_du, o.in_dT, o.in_omega = (
         float(p.get(k, 0.0)) for k in ("in_drho", "in_du", "in_dT", "in_omega"))
+    o.wall_nee = int(p.get("wall_nee", 0))
     return o
 
 

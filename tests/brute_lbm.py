@@ -15,7 +15,10 @@ different routes to the same quantities:
   a first-column node takes its e_x = +1 populations from the inlet state of
   Eq. 53, a last-column node takes its e_x = -1 populations from the ghost
   column x = nx, whose state is the last column's (zero gradient) and whose
-  non-equilibrium part is the last column's too.
+  non-equilibrium part is the last column's too;
+* walls of non-equilibrium extrapolation are applied on the pull as well: the
+  ghost node a population comes from, and the fluid node next to it (the
+  x side's for a corner ghost), are found from the receiving node.
 """
 from __future__ import annotations
 
@@ -135,6 +138,39 @@ class Brute:
             arr[sl] = 2 * Qw - Q[sl]
         return 0.5 * (plus - minus)
 
+    def _collide(self, F, H, rho, ux, uy, th, C):
+        """Equilibria and post-collision populations of nodes (arrays over
+        the grid, or one node with scalar moments)."""
+        p = self.p
+        usq = ux * ux + uy * uy
+        feq = feq_shells(rho, ux, uy, th)
+        if p["energy_model"] == 0:
+            heq = heq_total(rho, ux, uy, th, p["b"], feq)
+        else:
+            heq = heq_internal(th, p["b"], feq)
+        wf = 1 / (p["tau_f"] + 0.5)
+        wh = 1 / (p["tau_h"] + 0.5)
+        if p.get("collision", 0) == 1:
+            # rates: conserved moments 1, e / eps / q as given (0: omega_f), shear omega_f
+            r = [p.get(k, 0.0) or wf for k in ("s_e", "s_eps", "s_q")]
+            S = np.array([1, r[0], r[1], 1, r[2], 1, r[2], wf, wf]).reshape((9,) + (1,) * (F.ndim - 1))
+            m = np.tensordot(MB, F, 1)
+            meq = np.tensordot(MB, feq, 1)
+            Ch = np.tensordot(MB, C, 1)
+            fs = np.tensordot(MB_INV, m - S * (m - meq) + (1 - S / 2) * Ch, 1)
+            # Eq. 47: (1 - w_h/2) Z / tau_hf, tau_hf = (tau_f + 1/2)/(Pr - 1)
+            kz = (1 - wh / 2) * (p["tau_f"] / p["tau_h"] - 1) / (p["tau_f"] + 0.5)
+        else:
+            fs = F + wf * (feq - F) + (1 - wf / 2) * C
+            kz = wh - wf
+        hs = H + wh * (heq - H)
+        if p["energy_model"] == 0:
+            for a in range(9):
+                eu = EX[a] * ux + EY[a] * uy
+                Z = eu - 0.5 * usq if p["z_full"] else eu
+                hs[a] = hs[a] + kz * Z * (F[a] - feq[a] + 0.5 * C[a])
+        return np.asarray(feq), np.asarray(heq), fs, hs
+
     def step(self, n=1):
         for _ in range(n):
             self._step()
@@ -160,32 +196,7 @@ class Brute:
             ea = EY[a] * ay
             eu = EX[a] * ux + EY[a] * uy
             C[a] += W[a] * (3 * ea + 9 * (eu * ea - (uy * ay) / 3))
-        feq = feq_shells(rho, ux, uy, th)
-        if p["energy_model"] == 0:
-            heq = heq_total(rho, ux, uy, th, p["b"], feq)
-        else:
-            heq = heq_internal(th, p["b"], feq)
-        wf = 1 / (p["tau_f"] + 0.5)
-        wh = 1 / (p["tau_h"] + 0.5)
-        if p.get("collision", 0) == 1:
-            # rates: conserved moments 1, e / eps / q as given (0: omega_f), shear omega_f
-            r = [p.get(k, 0.0) or wf for k in ("s_e", "s_eps", "s_q")]
-            S = np.array([1, r[0], r[1], 1, r[2], 1, r[2], wf, wf])[:, None, None]
-            m = np.tensordot(MB, self.F, 1)
-            meq = np.tensordot(MB, feq, 1)
-            Ch = np.tensordot(MB, C, 1)
-            fs = np.tensordot(MB_INV, m - S * (m - meq) + (1 - S / 2) * Ch, 1)
-            # Eq. 47: (1 - w_h/2) Z / tau_hf, tau_hf = (tau_f + 1/2)/(Pr - 1)
-            kz = (1 - wh / 2) * (p["tau_f"] / p["tau_h"] - 1) / (p["tau_f"] + 0.5)
-        else:
-            fs = self.F + wf * (feq - self.F) + (1 - wf / 2) * C
-            kz = wh - wf
-        hs = self.H + wh * (heq - self.H)
-        if p["energy_model"] == 0:
-            for a in range(9):
-                eu = EX[a] * ux + EY[a] * uy
-                Z = eu - 0.5 * usq if p["z_full"] else eu
-                hs[a] += kz * Z * (self.F[a] - feq[a] + 0.5 * C[a])
+        feq, heq, fs, hs = self._collide(self.F, self.H, rho, ux, uy, th, C)
         # pull streaming with wrap, then overwrite wall-crossing pulls
         Fn = np.empty_like(fs)
         Hn = np.empty_like(hs)
@@ -218,6 +229,35 @@ class Brute:
                     if p["bc"][side] == OUTLET:
                         Fn[a, y, x] = fs[a, (y - EY[a]) % ny, nx - 1]
                         Hn[a, y, x] = hs[a, (y - EY[a]) % ny, nx - 1]
+                        continue
+                    if p.get("wall_nee", 0) >> side & 1:
+                        # ghost G = (sx, sy); its fluid node F is the first
+                        # node inward along the side's normal (wrapped along
+                        # a periodic axis, clamped at a corner)
+                        if side < 2:
+                            fx = 0 if side == 0 else nx - 1
+                            fy = sy % ny if p["bc"][2] == PERIODIC else min(max(sy, 0), ny - 1)
+                        else:
+                            fy = 0 if side == 2 else ny - 1
+                            fx = sx % nx
+                        r, t = rho[fy, fx], th[fy, fx]
+                        uw = p["u_wall"][side]
+                        if p["bc"][side] == ISO:
+                            tG = p["T_wall"][side] / p["T0"]
+                        else:  # zero slope at the wall node: quadratic through F, F2
+                            nxo, nyo = [(-1, 0), (1, 0), (0, -1), (0, 1)][side]
+                            tG = (4 * t - th[fy - nyo, fx - nxo]) / 3
+                        rG = r * t / tG
+                        fG = feq_shells(rG, uw[0], uw[1], tG)
+                        hG = (heq_total(rG, uw[0], uw[1], tG, p["b"], fG) if p["energy_model"] == 0
+                              else heq_internal(tG, p["b"], fG))
+                        fbG = np.array(fG) + self.F[:, fy, fx] - feq[:, fy, fx]
+                        hbG = np.array(hG) + self.H[:, fy, fx] - heq[:, fy, fx]
+                        CG = np.array([W[k] * (3 * EY[k] * (-rG * p["g"]) + 9 * (
+                            (EX[k] * uw[0] + EY[k] * uw[1]) * EY[k] * (-rG * p["g"]) -
+                            (uw[1] * (-rG * p["g"])) / 3)) for k in range(9)])
+                        _, _, fsG, hsG = self._collide(fbG, hbG, rG, uw[0], uw[1], tG, CG)
+                        Fn[a, y, x], Hn[a, y, x] = fsG[a], hsG[a]
                         continue
                     r, t = rho[y, x], th[y, x]
                     uw = p["u_wall"][side]
