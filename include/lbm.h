@@ -53,6 +53,17 @@
  *         last column's own post-collision populations back.
  *    Each step that touches them ends with a second, small kernel that
  *    writes these ghost slots.
+ *  - Walls of non-equilibrium extrapolation (wall_nee): the wall node G sits
+ *    one spacing outside the boundary node F.  Its state is the wall
+ *    velocity, theta_G (the wall's; adiabatic: zero slope at G to second
+ *    order, (4 theta_F - theta_F2)/3, F2 the next node inward) and F's
+ *    pressure (rho_G = rho_F theta_F / theta_G, since p = rho R T); its
+ *    pre-collision populations are its equilibria plus F's non-equilibrium
+ *    part; it collides like a fluid node (force of its own density, no
+ *    correction term) and sends its populations into the domain.  A corner
+ *    ghost at the end of an x side's column feeds the corner node (the x side
+ *    wins); Eq. 50 across such a wall keeps the mirror ghost above.  Written
+ *    by the same second kernel.
  */
 #ifndef LBM_H_
 #define LBM_H_
@@ -140,6 +151,13 @@ typedef struct {
   double in_dT;             /* temperature amplitude (< T_wall[0] in magnitude) */
   double in_omega;          /* angular frequency per step; the phase is taken
                                from the step count modulo 2^32              */
+  int32_t wall_nee;         /* bit s (side s): that wall (isothermal or
+                               adiabatic) is one of non-equilibrium
+                               extrapolation, the paper's wall method (ref.
+                               [45]), sitting ON the ghost node one spacing
+                               outside the boundary node (so H = n + 1
+                               between two of them) instead of halfway; see
+                               the conventions above.  0: halfway walls.    */
 } lbm_params;
 
 typedef struct lbm_handle lbm_handle;

@@ -96,6 +96,17 @@ int validate(const lbm_params* p, std::string& why) {
     why = "open x sides (inlet / outlet) need a periodic y axis";
     return LBM_ERR_PARAM;
   }
+  if (p->wall_nee < 0 || p->wall_nee > 15) {
+    why = "wall_nee is a bit mask of the four sides";
+    return LBM_ERR_PARAM;
+  }
+  for (int s = 0; s < 4; ++s) {
+    if ((p->wall_nee >> s & 1) && p->bc[s] != LBM_BC_WALL_ISOTHERMAL &&
+        p->bc[s] != LBM_BC_WALL_ADIABATIC) {
+      why = "wall_nee flags only isothermal or adiabatic wall sides";
+      return LBM_ERR_PARAM;
+    }
+  }
   if ((inlet || outlet) && p->correction != 0) {
     why = "open x sides (inlet / outlet) need correction = 0 (as the paper runs them)";
     return LBM_ERR_PARAM;
@@ -283,6 +294,7 @@ void fill_grid(const lbm_params* p, Grid& g) {
   g.in_du = p->in_du;
   g.in_dth = p->in_dT / p->T0;
   g.in_omega = p->in_omega;
+  g.nee = p->wall_nee;
 }
 
 }  // namespace lbm_host
@@ -540,10 +552,13 @@ int lbm_step(lbm_handle* h, int64_t n) {
       } else {
         e = launch_step_tma<S>(g, map, variant, rows, grid, h->stream);
       }
-      if (e == cudaSuccess && (g.bc[0] == BC_INLET || g.bc[1] == BC_OUTLET)) {
-        // open x sides: their ghost slots of the state just written
-        const int blocks = std::min((h->p.ny + 127) / 128, 1024);
-        open_fixup_kernel<S><<<blocks, 128, 0, h->stream>>>(g, static_cast<S*>(g.dst));
+      if (e == cudaSuccess && (g.bc[0] == BC_INLET || g.bc[1] == BC_OUTLET || g.nee)) {
+        // open sides and walls of NEE: their ghost slots of the state just
+        // written
+        const int units = std::max(h->p.ny, g.nee ? nee_ghosts(g) : 0);
+        const int blocks = std::min((units + 127) / 128, 1024);
+        side_fixup_kernel<S><<<blocks, 128, 0, h->stream>>>(g, static_cast<const S*>(g.src),
+                                                            static_cast<S*>(g.dst));
         e = cudaGetLastError();
       }
       return 0;

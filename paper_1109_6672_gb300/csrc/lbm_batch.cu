@@ -52,7 +52,7 @@ struct lbm_batch {
   int rows = 0;      // 0: per-precision default
   int dynamic = 1;   // atomic work queue
   std::vector<int> modes;        // physics modes present in the work list
-  bool has_open = false;         // a grid with an open x side is active
+  bool has_fix = false;          // a grid with an open side or a wall of NEE is active
   int occ_mode[BATCH_MODE_SLOTS] = {0};  // resident blocks per SM per mode (0: not queried)
   std::map<std::pair<int64_t, std::vector<int>>, cudaGraphExec_t> graphs;
   std::string err;
@@ -61,13 +61,15 @@ struct lbm_batch {
 namespace {
 
 // A batch at step j of its segment: block b takes grid b if it has an open
-// side and steps at j (the state it wrote is buffer (t0 + j + 1) mod 2).
+// side or a wall of NEE and steps at j (it read buffer (t0 + j) mod 2 and
+// wrote the other).
 template <class S>
 __global__ void __launch_bounds__(128)
-    batch_open_fixup_kernel(const BatchGrid* __restrict__ grids, int j) {
+    batch_side_fixup_kernel(const BatchGrid* __restrict__ grids, int j) {
   __shared__ Grid s_grid;
   const BatchGrid& bg = grids[blockIdx.x];
-  if (j >= bg.seg_steps || (bg.g.bc[0] != BC_INLET && bg.g.bc[1] != BC_OUTLET)) return;
+  if (j >= bg.seg_steps || (bg.g.bc[0] != BC_INLET && bg.g.bc[1] != BC_OUTLET && !bg.g.nee))
+    return;
   const int* gsrc = reinterpret_cast<const int*>(&bg.g);
   int* gdst = reinterpret_cast<int*>(&s_grid);
   for (int i = threadIdx.x; i < (int)(sizeof(Grid) / sizeof(int)); i += blockDim.x)
@@ -75,8 +77,9 @@ __global__ void __launch_bounds__(128)
   __syncthreads();
   if (threadIdx.x == 0) s_grid.t = (unsigned)(bg.t0 + j);
   __syncthreads();
-  S* dst = static_cast<S*>(bg.buf[(int)((bg.t0 + j + 1) & 1)]);
-  open_rows<S>(s_grid, dst, threadIdx.x, blockDim.x);
+  const int par = (int)((bg.t0 + j) & 1);
+  fixup_grid<S>(s_grid, static_cast<const S*>(bg.buf[par]), static_cast<S*>(bg.buf[par ^ 1]),
+                threadIdx.x, blockDim.x);
 }
 
 
@@ -158,9 +161,10 @@ int rebuild_items(lbm_batch* b) {
   int begin[BATCH_MODE_SLOTS], end[BATCH_MODE_SLOTS];
   for (int m = 0; m < BATCH_MODE_SLOTS; ++m) begin[m] = end[m] = 0;
   b->modes.clear();
-  b->has_open = false;
+  b->has_fix = false;
   for (int s : order) {
-    b->has_open |= b->slots[s].p.bc[0] == LBM_BC_INLET || b->slots[s].p.bc[1] == LBM_BC_OUTLET;
+    b->has_fix |= b->slots[s].p.bc[0] == LBM_BC_INLET || b->slots[s].p.bc[1] == LBM_BC_OUTLET ||
+                  b->slots[s].p.wall_nee != 0;
     const lbm_params& p = b->slots[s].p;
     const int mode = b->h_grids[s].mode, ms = mode_slot(mode);
     if (b->modes.empty() || b->modes.back() != mode) {
@@ -235,11 +239,12 @@ cudaError_t launch_all_modes(lbm_batch* b, int j) {
     });
     if (e != cudaSuccess) break;
   }
-  if (e == cudaSuccess && b->has_open) {
-    // open x sides: their ghost slots, once every grid has taken step j
+  if (e == cudaSuccess && b->has_fix) {
+    // open sides and walls of NEE: their ghost slots, once every grid has
+    // taken step j
     e = by_precision(b->precision, [&](auto* tag) {
       using S = std::remove_pointer_t<decltype(tag)>;
-      batch_open_fixup_kernel<S><<<b->max_grids, 128, 0, b->stream>>>(b->d_grids, j);
+      batch_side_fixup_kernel<S><<<b->max_grids, 128, 0, b->stream>>>(b->d_grids, j);
       return cudaGetLastError();
     });
   }
@@ -255,7 +260,7 @@ int* counters_of(lbm_batch* b) {
 // counters.  Cached per (k, modes present, open sides present).
 int graph_for(lbm_batch* b, int64_t k, cudaGraphExec_t* out) {
   auto key = std::make_pair(k, b->modes);
-  if (b->has_open) key.second.push_back(-1);
+  if (b->has_fix) key.second.push_back(-1);
   auto it = b->graphs.find(key);
   if (it != b->graphs.end()) {
     *out = it->second;

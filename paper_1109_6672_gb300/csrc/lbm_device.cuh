@@ -109,6 +109,7 @@ struct Grid {
   // inlet (x-, Eq. 53): rho = in_rho + in_drho s, u = uw[0] + (in_du s, 0),
   // theta = thw[0] + in_dth s, s = sin(in_omega t)
   double in_rho, in_drho, in_du, in_dth, in_omega;
+  int nee;                 // sides (bit s) with walls of non-equilibrium extrapolation
   int* status;             // device error word (bounded waits), may be NULL
   unsigned t;              // time step being taken (stochastic rounding counter)
 };

@@ -1,3 +1,6 @@
+// Ghost slots that the step kernels leave to a second pass: open x sides and
+// walls of non-equilibrium extrapolation.
+//
 // Open x sides of the attenuation-driven acoustic streaming set-up
 // (arXiv:1109.6672, Sec. IV.B): an inlet at x- reset every step to the
 // equilibria of the Eq. 53 state, and a zero-gradient outlet at x+ with
@@ -74,10 +77,150 @@ __device__ void open_rows(const Grid& g, S* __restrict__ dst, int first, int str
   }
 }
 
-// One grid: rows spread over the launch.
+// Walls of non-equilibrium extrapolation (the paper's wall method, ref.
+// [45]; side s flagged in Grid::nee).  The wall sits on the ghost node G one
+// spacing outside the boundary node F.  G's state: the wall velocity, theta_G
+// (the wall's on an isothermal side; on an adiabatic side zero slope at G to
+// second order, (4 theta_F - theta_F2)/3 with F2 the next node inward), and
+// F's pressure, rho_G = rho_F theta_F / theta_G.  Its pre-collision
+// populations are its equilibria plus F's non-equilibrium part
+// fbar(F) - f^eq(F) (likewise h); it collides like a fluid node (rates of
+// its own rho and theta, the Guo force of its own density, no correction
+// term), and the populations it sends into the domain are stored where the
+// receiving nodes pull them.  Ghost k of a grid: 0 .. ny + 1 the x- column
+// (G at y = k - 1, the corners included), then the x+ column, then nx per
+// y side; the step kernels treat these sides as halfway walls and this
+// rewrites every slot those wrote.
+__host__ __device__ inline int nee_ghosts(const Grid& g) { return 2 * (g.ny + 2) + 2 * g.nx; }
+
 template <class S>
-__global__ void __launch_bounds__(128) open_fixup_kernel(const Grid g, S* __restrict__ dst) {
-  open_rows<S>(g, dst, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+__device__ void nee_ghost(const Grid& g, const S* __restrict__ src, S* __restrict__ dst, int k) {
+  using C = typename Io<S>::C;
+  int side, gx, gy;
+  if (k < 2 * (g.ny + 2)) {
+    side = k < g.ny + 2 ? 0 : 1;
+    gx = side == 0 ? -1 : g.nx;
+    gy = k - (side == 0 ? 0 : g.ny + 2) - 1;
+  } else {
+    k -= 2 * (g.ny + 2);
+    side = k < g.nx ? 2 : 3;
+    gx = k - (side == 2 ? 0 : g.nx);
+    gy = side == 2 ? -1 : g.ny;
+  }
+  if (!(g.nee >> side & 1)) return;
+  const bool xs = side < 2;
+  const bool yper = g.bc[2] == BC_PERIODIC, xper = g.bc[0] == BC_PERIODIC;
+  const int nxo = side == 0 ? -1 : (side == 1 ? 1 : 0), nyo = side == 2 ? -1 : (side == 3 ? 1 : 0);
+  // F: the first node inward (an x side's corner ghost: the corner node)
+  int fx, fy;
+  bool corner = false;
+  if (xs) {
+    fx = gx - nxo;
+    if (gy < 0 || gy >= g.ny) {
+      if (yper) return;  // along a periodic y the column has no corner ghosts
+      corner = true;
+      fy = gy < 0 ? 0 : g.ny - 1;
+    } else {
+      fy = gy;
+    }
+  } else {
+    fx = gx;
+    fy = gy - nyo;
+  }
+  const bool total = g.energy_model == E_TOTAL;
+  const Phys<C>& kp = phys<C>(g);
+  C d[NPOP], rho, ux, uy, th, Es;
+  pull<S>(g, src, fx, fy, d);
+  moments<S>(g, d, rho, ux, uy, th, Es);
+  C feq[9], heq[9];
+  collision_equilibria<C>(rho, ux, uy, th, Es, kp.b6, total, feq, heq);
+  C thG;
+  if (g.bc[side] == BC_ISO) {
+    thG = kp.thw[side];
+  } else {
+    C d2[NPOP], r2, u2, v2, t2, e2;
+    pull<S>(g, src, fx - nxo, fy - nyo, d2);
+    moments<S>(g, d2, r2, u2, v2, t2, e2);
+    thG = (C(4) * th - t2) * C(1.0 / 3.0);
+  }
+  const C rG = rho * th / thG, uwx = kp.uw[side][0], uwy = kp.uw[side][1];
+  const C EsG = kp.b6 * thG + (total ? C(0.5) * (uwx * uwx + uwy * uwy) : C(0));
+  C fqG[9], hqG[9], fb[9], hb[9];
+  collision_equilibria<C>(rG, uwx, uwy, thG, EsG, kp.b6, total, fqG, hqG);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    fb[a] = fqG[a] + ((pref<S>(g, a) + d[a]) - feq[a]);
+    hb[a] = hqG[a] + ((pref<S>(g, 9 + a) + d[9 + a]) - heq[a]);
+  }
+  // collision of G
+  C wf, wh, kz;
+  node_rates<C>(g, kp, rG, thG, g.collision == COLL_MRT, wf, wh, kz);
+  C cc[9];
+  const C ay = -rG * kp.g;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const C ea = C(ey(a)) * ay;
+    const C eu = C(ex(a)) * uwx + C(ey(a)) * uwy;
+    cc[a] = g.has_force ? wgt<C>(a) * (C(3) * ea + C(9) * eu * ea - C(3) * uwy * ay) : C(0);
+  }
+  C fs[9], fn[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) fn[a] = fb[a] - fqG[a];
+  if (g.collision == COLL_MRT) {
+    C mc[9];
+    mrt_source<C>(false, C(0), C(0), g.has_force != 0, uwx, uwy, ay, mc);
+    mrt_collide<C>(kp, wf, fb, fn, mc, fs);
+  } else {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) fs[a] = fb[a] - wf * fn[a] + (C(1) - C(0.5) * wf) * cc[a];
+  }
+  const C usq = uwx * uwx + uwy * uwy;
+  const unsigned hs = Io<S>::sr ? sr_hash(g, gx, gy) : 0u;
+#pragma unroll
+  for (int a = 1; a < 9; ++a) {
+    if (ex(a) * nxo + ey(a) * nyo >= 0) continue;  // not into the domain
+    int dx = gx + ex(a), dy = gy + ey(a);
+    if (corner) {
+      if (dx != fx || dy != fy) continue;  // a corner ghost feeds the corner node only
+    } else {
+      if (dx < 0 || dx >= g.nx) {
+        if (!xper) continue;  // the x side's rule has it
+        dx = (dx + g.nx) % g.nx;
+      }
+      if (dy < 0 || dy >= g.ny) {
+        if (!yper) continue;
+        dy = (dy + g.ny) % g.ny;
+      }
+    }
+    C hsa = hb[a] - wh * (hb[a] - hqG[a]);
+    if (total) {
+      const C eu = C(ex(a)) * uwx + C(ey(a)) * uwy;
+      const C Z = g.z_full ? eu - C(0.5) * usq : eu;
+      hsa += kz * Z * (fn[a] + C(0.5) * cc[a]);
+    }
+    put<S>(g, dst, a, dx - ex(a), dy - ey(a), fs[a], hs, 18 + a);
+    put<S>(g, dst, 9 + a, dx - ex(a), dy - ey(a), hsa, hs, 27 + a);
+  }
+}
+
+// Every ghost slot of the open sides and of the walls of non-equilibrium
+// extrapolation of one grid (state at t in src, at t + 1 in dst, g.t = t),
+// work units first, first + stride, ...
+template <class S>
+__device__ void fixup_grid(const Grid& g, const S* __restrict__ src, S* __restrict__ dst,
+                           int first, int stride) {
+  if (g.bc[0] == BC_INLET || g.bc[1] == BC_OUTLET) open_rows<S>(g, dst, first, stride);
+  if (g.nee) {
+    const int n = nee_ghosts(g);
+    for (int k = first; k < n; k += stride) nee_ghost<S>(g, src, dst, k);
+  }
+}
+
+// One grid: work spread over the launch.
+template <class S>
+__global__ void __launch_bounds__(128)
+    side_fixup_kernel(const Grid g, const S* __restrict__ src, S* __restrict__ dst) {
+  fixup_grid<S>(g, src, dst, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 }  // namespace lbm

@@ -42,6 +42,7 @@ class lbm_params(ctypes.Structure):
         ("mu_law", ctypes.c_int32), ("mu_n", ctypes.c_double), ("mu_S", ctypes.c_double),
         ("in_rho", ctypes.c_double), ("in_drho", ctypes.c_double), ("in_du", ctypes.c_double),
         ("in_dT", ctypes.c_double), ("in_omega", ctypes.c_double),
+        ("wall_nee", ctypes.c_int32),
     ]
 
 
@@ -144,6 +145,7 @@ def make_params(p: dict) -> lbm_params:
     o.in_rho = float(p.get("in_rho", 1.0))
     o.in_drho, o.in_du, o.in_dT, o.in_omega = (
         float(p.get(k, 0.0)) for k in ("in_drho", "in_du", "in_dT", "in_omega"))
+    o.wall_nee = int(p.get("wall_nee", 0))
     return o
 
 

@@ -89,6 +89,21 @@ def test_open_side_validation_without_gpu(lib):
         assert e.value.status == lbm.LBM_ERR_PARAM
 
 
+def test_nee_validation_without_gpu(lib):
+    lbm.load()
+    p, _ = inputs.cavity(n=64, precision=lbm.LBM_P_FP32)
+    assert lbm.lbm_state_bytes(dict(p, wall_nee=15)) > 0
+    q, _ = inputs.couette(ny=33)
+    assert lbm.lbm_state_bytes(dict(q, wall_nee=12)) > 0
+    for bad in (dict(q, wall_nee=1), dict(p, wall_nee=16), dict(p, wall_nee=-1)):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_state_bytes(bad)
+        assert e.value.status == lbm.LBM_ERR_PARAM
+    a, _ = inputs.acoustic_channel()
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_state_bytes(dict(a, wall_nee=1))
+
+
 def test_status_strings(lib):
     assert lbm.status_string(lbm.LBM_ERR_NONFINITE) == "LBM_ERR_NONFINITE"
     assert lbm.status_string(0) == "LBM_OK"

@@ -1,0 +1,80 @@
+"""Walls of non-equilibrium extrapolation on the CUDA path: parity with the
+oracle for every wall layout, kernel family, storage precision and in
+batches; resume; and the large-temperature-difference cavity without gravity
+staying at rest (no creep along the adiabatic walls)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1109_6672_gb300 import inputs
+from paper_1109_6672_gb300 import lbm
+from test_gpu_parity import rel
+from test_oracle_nee import CASES, nee_case
+
+pytestmark = pytest.mark.gpu
+
+LAUNCHES = [None, (1, 3), (2, 5), (96, 4)]
+
+
+def big_case(name, precision, nx=150, ny=37, seed=5):
+    p, f = nee_case(name, nx=nx, ny=ny, seed=seed)
+    p["precision"] = precision
+    return p, f
+
+
+@pytest.mark.parametrize("launch", LAUNCHES)
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_nee_fp64_parity(name, launch):
+    p, f = big_case(name, lbm.LBM_P_FP64)
+    if launch and launch[0] == 2 and p.get("collision", 0) == 1:
+        pytest.skip("two nodes per thread: BGK with constant tau only")
+    o = orc.Oracle(p).init(*f).step(40)
+    g = lbm.Lbm(p)
+    if launch:
+        g.set_launch(*launch)
+    g.init(*f).step(40)
+    assert rel(g.pops(), o.pops()) <= 1e-12
+    g.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(lbm.LBM_P_FP32, 2e-5), (lbm.LBM_P_FP32_FP16, 2e-3),
+                                           (lbm.LBM_P_FP32_BF16, 1.5e-2)])
+@pytest.mark.parametrize("name", ["cavity_all", "couette_y", "mrt_all"])
+def test_nee_reduced_precision(name, precision, tol):
+    p, f = big_case(name, precision)
+    o = orc.Oracle(p).init(*f).step(40)
+    g = lbm.Lbm(p).init(*f).step(40)
+    assert rel(g.pops(), o.pops()) <= tol
+    g.close()
+
+
+def test_nee_in_a_batch():
+    grids = [big_case(n, lbm.LBM_P_FP64, nx=nx, ny=ny, seed=s)
+             for n, nx, ny, s in (("cavity_all", 130, 40, 1), ("couette_y", 9, 50, 2),
+                                  ("x_halfway_y_nee", 70, 33, 3), ("x_nee_y_periodic", 200, 12, 4))]
+    p, f = inputs.cavity(n=64, Ra=1e4, dT_over_T0=0.1, seed=6)
+    grids.append((p, f))
+    b = lbm.Batch(lbm.LBM_P_FP64, len(grids), 1 << 28)
+    slots = [b.add(p, f, 30) for p, f in grids]
+    b.run(30)
+    for (p, f), s in zip(grids, slots):
+        assert rel(b.pops(s), orc.Oracle(p).init(*f).step(30).pops()) <= 1e-12
+    b.close()
+
+
+@pytest.mark.parametrize("precision", [lbm.LBM_P_FP64, lbm.LBM_P_FP32_BF16])
+def test_nee_resume_bitwise(precision):
+    p, f = big_case("cavity_all", precision)
+    straight = lbm.Lbm(p).init(*f).step(33).pops()
+    a = lbm.Lbm(p).init(*f).step(14)
+    b = lbm.Lbm(p).set_pops(a.pops(), steps_done=a.steps_done).step(19)
+    np.testing.assert_array_equal(b.pops(), straight)
+
+
+def test_nee_large_dt_cavity_without_gravity_stays_at_rest():
+    p, f = inputs.cavity_large_dT(Ra=1e3, n=64, precision=lbm.LBM_P_FP32)
+    p.update(g=0.0, wall_nee=15)
+    g = lbm.Lbm(p).init(*f).step(40000)
+    rho, ux, uy, T = g.moments()
+    g.close()
+    assert max(np.abs(ux).max(), np.abs(uy).max()) < 1e-5
