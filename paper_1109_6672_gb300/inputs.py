@@ -171,24 +171,29 @@ LARGE_DT_CASES = {1e3: (100, 0.1), 1e4: (150, 0.1), 1e5: (200, 0.06)}
 
 def cavity_large_dT(Ra: float = 1e5, n: int | None = None, mu_r: float | None = None,
                     Pr: float = 0.71, seed: int = 1, noise: float = 1e-4,
-                    precision: int = P_FP64, **kw):
+                    precision: int = P_FP64, nee: bool = True, **kw):
     """Natural convection with a large temperature difference (Sec. IV.C):
     T_h = 960 K, T_l = 240 K, T0 = T_r = 600 K (theta 1.6 at x-, 0.4 at x+),
     adiabatic top and bottom.  Sutherland's law (Eq. 59, S = 110.5 K) referred
     to T_r (mu* taken from mu(T_r) = mu_r); Pr = 0.71 constant; mu_r and the
     grid per Ra as the paper takes them (100, 150, 200 nodes; mu_r = 0.1, 0.1,
     0.06 for Ra = 1e3, 1e4, 1e5).  MRT with tau_e = tau_eps = tau_f and
-    1/tau_q = 1.5, internal-energy model (Eq. 38), correction on.  Gravity
-    from Eq. 57 with beta = 1/T_r (Eq. 58): g = Ra nu_r^2 / (Pr beta dT H^3),
-    nu_r = mu_r / rho0, rho0 = 1."""
+    1/tau_q = 1.5, internal-energy model (Eq. 38), correction on.  ``nee``:
+    the paper's walls of non-equilibrium extrapolation on the wall nodes (the
+    paper's grid counts them: n = grid - 2 fluid nodes, H = n + 1); else
+    halfway walls (n = grid, H = n).  ``n`` overrides the fluid nodes per side.
+    Gravity from Eq. 57 with beta = 1/T_r (Eq. 58): g = Ra nu_r^2 /
+    (Pr beta dT H^3), nu_r = mu_r / rho0, rho0 = 1."""
     n0, mu0 = LARGE_DT_CASES.get(Ra, (200, 0.06))
-    n = n0 if n is None else n
+    if n is None:
+        n = n0 - 2 if nee else n0
     mu_r = mu0 if mu_r is None else mu_r
+    H = n + 1 if nee else n
     dT = (960.0 - 240.0) / 600.0
-    g = Ra * mu_r * mu_r / (Pr * dT * n ** 3)
+    g = Ra * mu_r * mu_r / (Pr * dT * H ** 3)
     tau_f = mu_r / RT0
     p = base_params(n, n, tau_f=tau_f, tau_h=tau_f / Pr, b=5.0, g=g, energy_model=E_INTERNAL,
                     bc=[WALL_ISOTHERMAL, WALL_ISOTHERMAL, WALL_ADIABATIC, WALL_ADIABATIC],
                     T_wall=[1.6, 0.4, 1.0, 1.0], precision=precision, mu_law=2,
-                    mu_S=110.5 / 600.0, collision=1, s_q=1.5, **kw)
+                    mu_S=110.5 / 600.0, collision=1, s_q=1.5, wall_nee=15 if nee else 0, **kw)
     return p, uniform_fields(n, n, seed=seed, u_amp=noise)
