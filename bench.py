@@ -429,15 +429,21 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = job_value(world, nodes, e2e_steps, e2e_t)
 
     variants = {}
+    cavity = inputs.cavity(n=n, Ra=1e5, dT_over_T0=0.3, seed=3)[0]
     if args.variants and world == 1:
         for name, pv, opts in (("f64", lbm.LBM_P_FP64, {}), ("f16dev", lbm.LBM_P_FP32_FP16, {}),
                                 ("bf16dev", lbm.LBM_P_FP32_BF16, {}),
                                 ("mrt_f32", lbm.LBM_P_FP32,
-                                 dict(collision=lbm.LBM_COLL_MRT, s_e=1.3, s_eps=1.1, s_q=1.6))):
+                                 dict(collision=lbm.LBM_COLL_MRT, s_e=1.3, s_eps=1.1, s_q=1.6)),
+                                # the same size as a walled cavity: halfway walls, and the
+                                # walls of non-equilibrium extrapolation (second pass)
+                                ("cavity_f32", lbm.LBM_P_FP32, dict(base=cavity)),
+                                ("cavity_nee_f32", lbm.LBM_P_FP32, dict(base=cavity, wall_nee=15))):
             if pv == prec and not opts:
                 continue
             g.close()
-            pp = dict(p, precision=pv, **opts)
+            opts = dict(opts)
+            pp = dict(opts.pop("base", p), precision=pv, **opts)
             gv = lbm.Lbm(pp, stream=stream.cuda_stream)
             with torch.cuda.stream(stream):
                 lbm.lbm_init_device(gv.h, *[t.data_ptr() for t in dev_fields])
@@ -465,9 +471,12 @@ def run_ours(args, rank, world, local_rank):
         cores = cpu_cores()
         side = args.ref_side
         gl, dt = oracle_glups(side, args.ref_steps, cores)
+        gl1, dt1 = oracle_glups(256, 60, 1)
         cpu = {"value": gl, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{side}x{side} periodic box of the same workload, {args.ref_steps} steps "
-                         f"({dt:.1f} s), FP64, OpenMP over rows"}
+                         f"({dt:.1f} s), FP64, OpenMP over rows",
+               "single_thread": {"value": gl1, "unit": UNIT, "cores": 1,
+                                 "sample": f"256x256 periodic box, 60 steps ({dt1:.1f} s), FP64"}}
 
     traffic = None
     if n == 4096 and args.threads in (0, 1) and args.rows == 0:
