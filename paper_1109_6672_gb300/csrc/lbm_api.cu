@@ -349,6 +349,9 @@ namespace lbm_host {
 
 // 3-D view of one state buffer for the TMA row loads: (x + 32, population,
 // y + 1) with a box of one lattice row, all 18 populations, box_cols columns.
+// The x extent ends at the ghost column x = nx: a box reaching past it (the
+// last strip of a grid, narrow grids) is filled by the TMA unit without
+// reading the row's padding up to the pitch; nothing reads those columns.
 int make_tensor_map(CUtensorMap* map, void* buffer, const lbm_params& p, const Grid& g,
                     int box_cols, int box_planes) {
   auto fn = encode_fn();
@@ -358,7 +361,7 @@ int make_tensor_map(CUtensorMap* map, void* buffer, const lbm_params& p, const G
                            : p.precision == LBM_P_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                            : p.precision == LBM_P_FP32_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                              : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)NPOP, (cuuint64_t)(g.ny + 2)};
+  cuuint64_t dims[3] = {(cuuint64_t)(XOFF + g.nx + 1), (cuuint64_t)NPOP, (cuuint64_t)(g.ny + 2)};
   cuuint64_t strides[2] = {(cuuint64_t)g.pitch * es, (cuuint64_t)g.rp * es};
   cuuint32_t box[3] = {(cuuint32_t)box_cols, (cuuint32_t)box_planes, 1};
   cuuint32_t estr[3] = {1, 1, 1};
