@@ -56,7 +56,8 @@
  *  - Walls of non-equilibrium extrapolation (wall_nee): the wall node G sits
  *    one spacing outside the boundary node F.  Its state is the wall
  *    velocity, theta_G (the wall's; adiabatic: zero slope at G to second
- *    order, (4 theta_F - theta_F2)/3, F2 the next node inward) and F's
+ *    order, (4 theta_F - theta_F2)/3, F2 the next node inward, floored at
+ *    theta_F / 2) and F's
  *    pressure (rho_G = rho_F theta_F / theta_G, since p = rho R T); its
  *    pre-collision populations are its equilibria plus F's non-equilibrium
  *    part; it collides like a fluid node (force of its own density, no

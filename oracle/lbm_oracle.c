@@ -619,7 +619,7 @@ static void phase2(orc_state* s, int nthreads) {
           thG = p->T_wall[side] / p->T0;
         } else {
           const long i2 = (long)(y - nyo) * nx + (x - nxo);
-          thG = (4.0 * th - s->theta[i2]) / 3.0;
+          thG = fmax((4.0 * th - s->theta[i2]) / 3.0, 0.5 * th); /* floored: rho_G = rho theta / theta_G */
         }
         const double uwx = p->u_wall[side][0], uwy = p->u_wall[side][1];
         /* the wall node: F's pressure, the wall's velocity, theta_G; its

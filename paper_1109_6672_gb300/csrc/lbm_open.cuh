@@ -81,7 +81,8 @@ __device__ void open_rows(const Grid& g, S* __restrict__ dst, int first, int str
 // [45]; side s flagged in Grid::nee).  The wall sits on the ghost node G one
 // spacing outside the boundary node F.  G's state: the wall velocity, theta_G
 // (the wall's on an isothermal side; on an adiabatic side zero slope at G to
-// second order, (4 theta_F - theta_F2)/3 with F2 the next node inward), and
+// second order, (4 theta_F - theta_F2)/3 with F2 the next node inward,
+// floored at theta_F / 2 so that the density below stays finite), and
 // F's pressure, rho_G = rho_F theta_F / theta_G.  Its pre-collision
 // populations are its equilibria plus F's non-equilibrium part
 // fbar(F) - f^eq(F) (likewise h); it collides like a fluid node (rates of
@@ -141,7 +142,7 @@ __device__ void nee_ghost(const Grid& g, const S* __restrict__ src, S* __restric
     C d2[NPOP], r2, u2, v2, t2, e2;
     pull<S>(g, src, fx - nxo, fy - nyo, d2);
     moments<S>(g, d2, r2, u2, v2, t2, e2);
-    thG = (C(4) * th - t2) * C(1.0 / 3.0);
+    thG = fmax((C(4) * th - t2) * C(1.0 / 3.0), C(0.5) * th);  // floored: rho_G = rho th / thG
   }
   const C rG = rho * th / thG, uwx = kp.uw[side][0], uwy = kp.uw[side][1];
   const C EsG = kp.b6 * thG + (total ? C(0.5) * (uwx * uwx + uwy * uwy) : C(0));

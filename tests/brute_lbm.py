@@ -246,7 +246,7 @@ class Brute:
                             tG = p["T_wall"][side] / p["T0"]
                         else:  # zero slope at the wall node: quadratic through F, F2
                             nxo, nyo = [(-1, 0), (1, 0), (0, -1), (0, 1)][side]
-                            tG = (4 * t - th[fy - nyo, fx - nxo]) / 3
+                            tG = max((4 * t - th[fy - nyo, fx - nxo]) / 3, 0.5 * t)
                         rG = r * t / tG
                         fG = feq_shells(rG, uw[0], uw[1], tG)
                         hG = (heq_total(rG, uw[0], uw[1], tG, p["b"], fG) if p["energy_model"] == 0
