@@ -382,7 +382,9 @@ def run_ours(args, rank, world, local_rank):
     prec = {"f64": lbm.LBM_P_FP64, "f32": lbm.LBM_P_FP32, "f16": lbm.LBM_P_FP32_FP16,
             "bf16": lbm.LBM_P_FP32_BF16}[args.precision]
     n = args.n
-    p, fields = inputs.periodic_box(n=n, precision=prec)
+    coll = dict(collision=lbm.LBM_COLL_MRT, s_e=1.3, s_eps=1.1, s_q=1.6) \
+        if args.collision == "mrt" else {}
+    p, fields = inputs.periodic_box(n=n, precision=prec, **coll)
     stream = torch.cuda.Stream()
     g = lbm.Lbm(p, stream=stream.cuda_stream)
     if args.threads:
@@ -479,7 +481,7 @@ def run_ours(args, rank, world, local_rank):
                                  "sample": f"256x256 periodic box, 60 steps ({dt1:.1f} s), FP64"}}
 
     traffic = None
-    if n == 4096 and args.threads in (0, 1) and args.rows == 0:
+    if n == 4096 and args.threads in (0, 1) and args.rows == 0 and args.collision == "bgk":
         traffic = MEASURED_TRAFFIC.get((kernel_hash(), args.precision))
     if rank == 0:
         line = {
@@ -489,7 +491,8 @@ def run_ours(args, rank, world, local_rank):
             "dtype": {"f64": "f64", "f32": "f32", "f16": "f32 (f16 storage)",
                       "bf16": "f32 (bf16 storage)"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": f"periodic box {n}x{n}, coupled f+h D2Q9 BGK, total energy, "
+            "config": {"workload": f"periodic box {n}x{n}, coupled f+h D2Q9 "
+                                   f"{args.collision.upper()}, total energy, "
                                    f"correction on, {lbm.PRECISION_NAMES[prec]} storage",
                        "nx": n, "ny": n, "precision": args.precision,
                        "bytes_per_node_update": bpn,
@@ -522,6 +525,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f32", choices=["f64", "f32", "f16", "bf16"])
+    ap.add_argument("--collision", default="bgk", choices=["bgk", "mrt"],
+                    help="collision of the timed box (MRT: Eqs. 40-47, rates 1.3 / 1.1 / 1.6)")
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--rows", type=int, default=0)
