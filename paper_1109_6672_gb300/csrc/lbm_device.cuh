@@ -658,10 +658,15 @@ __device__ __forceinline__ void node_rates(const Grid& g, const Phys<C>& k, C rh
 //   f* = f + M^-1 [ -S M n + (I - S/2) mc ],
 // S = diag(1, s_e, s_eps, 1, s_q, 1, s_q, w_f, w_f) (Eq. 40; the rates of
 // the conserved moments rho and j drop out of the result).
-template <class C>
+template <class C, bool NODE = true>
 __device__ __forceinline__ void mrt_collide(const Phys<C>& k, C wf, const C f[9], const C n[9],
                                             const C mc[9], C out[9]) {
-  // moments (rho, e, eps, jx, qx, jy, qy, pxx, pxy) of n: rows of M
+  // moments (e, eps, qx, qy, pxx, pxy) of n: rows of M.  For a node
+  // (NODE) the conserved ones need no sums: rho of n is 0 (f^eq carries the
+  // node's rho), jx of n is 0 and jy of n is -a_y/2 (u = (j + a/2)/rho,
+  // a = (0, a_y)); with their rate 1 and the source mc (jy: a_y) their
+  // relaxed changes are 0, 0, a_y.  A wall node of non-equilibrium
+  // extrapolation borrows n from its neighbour, so it takes them in full.
   C mn[9];
   {
     const C* q = n;
@@ -669,23 +674,29 @@ __device__ __forceinline__ void mrt_collide(const Phys<C>& k, C wf, const C f[9]
     const C sa = (q[1] + q[2]) + (q[3] + q[4]), sd = (q[5] + q[6]) + (q[7] + q[8]);
     const C dx1 = q[1] - q[3], dy1 = q[2] - q[4];
     const C dxd = (q[5] - q[6]) - (q[7] - q[8]), dyd = (q[5] + q[6]) - (q[7] + q[8]);
-    m[0] = q[0] + sa + sd;
+    m[0] = NODE ? C(0) : q[0] + sa + sd;
     m[1] = C(-4) * q[0] - sa + C(2) * sd;
     m[2] = C(4) * q[0] - C(2) * sa + sd;
-    m[3] = dx1 + dxd;
+    m[3] = NODE ? C(0) : dx1 + dxd;
     m[4] = C(-2) * dx1 + dxd;
-    m[5] = dy1 + dyd;
+    m[5] = NODE ? C(0) : dy1 + dyd;
     m[6] = C(-2) * dy1 + dyd;
     m[7] = (q[1] + q[3]) - (q[2] + q[4]);
     m[8] = (q[5] - q[6]) + (q[7] - q[8]);
   }
   const C se = k.se > C(0) ? k.se : wf, seps = k.seps > C(0) ? k.seps : wf;
   const C sq = k.sq > C(0) ? k.sq : wf;
-  const C s[9] = {C(1), se, seps, C(1), sq, C(1), sq, wf, wf};
   C dm[9];
-#pragma unroll
-  for (int q = 0; q < 9; ++q) dm[q] = -s[q] * mn[q] + (C(1) - C(0.5) * s[q]) * mc[q];
-  // M^-1 dm (Eq. B2), grouped by shell
+  dm[1] = -se * mn[1] + (C(1) - C(0.5) * se) * mc[1];
+  dm[2] = -seps * mn[2] + (C(1) - C(0.5) * seps) * mc[2];
+  dm[4] = -sq * mn[4] + (C(1) - C(0.5) * sq) * mc[4];
+  dm[0] = NODE ? C(0) : -mn[0] + C(0.5) * mc[0];
+  dm[3] = NODE ? C(0) : -mn[3] + C(0.5) * mc[3];
+  dm[5] = NODE ? mc[5] : -mn[5] + C(0.5) * mc[5];
+  dm[6] = -sq * mn[6] + (C(1) - C(0.5) * sq) * mc[6];
+  dm[7] = -wf * mn[7] + (C(1) - C(0.5) * wf) * mc[7];
+  dm[8] = -wf * mn[8] + (C(1) - C(0.5) * wf) * mc[8];
+  // M^-1 dm (Eq. B2), grouped by shell (for a node dm[0] = dm[3] = 0)
   const C r0 = dm[0] * C(1.0 / 9.0);
   const C ax = r0 - dm[1] * C(1.0 / 36.0) - dm[2] * C(1.0 / 18.0);
   const C dg = r0 + dm[1] * C(1.0 / 18.0) + dm[2] * C(1.0 / 36.0);
@@ -693,7 +704,7 @@ __device__ __forceinline__ void mrt_collide(const Phys<C>& k, C wf, const C f[9]
   const C x2 = dm[3] * C(1.0 / 6.0) + dm[4] * C(1.0 / 12.0);
   const C y2 = dm[5] * C(1.0 / 6.0) + dm[6] * C(1.0 / 12.0);
   const C pp = dm[7] * C(0.25), pq = dm[8] * C(0.25);
-  out[0] = f[0] + (r0 - dm[1] * C(1.0 / 9.0) + dm[2] * C(1.0 / 9.0));
+  out[0] = f[0] + (r0 + (dm[2] - dm[1]) * C(1.0 / 9.0));
   out[1] = f[1] + (ax + x1 + pp);
   out[2] = f[2] + (ax + y1 - pp);
   out[3] = f[3] + (ax - x1 + pp);

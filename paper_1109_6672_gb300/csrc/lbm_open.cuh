@@ -170,7 +170,7 @@ __device__ void nee_ghost(const Grid& g, const S* __restrict__ src, S* __restric
   if (g.collision == COLL_MRT) {
     C mc[9];
     mrt_source<C>(false, C(0), C(0), g.has_force != 0, uwx, uwy, ay, mc);
-    mrt_collide<C>(kp, wf, fb, fn, mc, fs);
+    mrt_collide<C, false>(kp, wf, fb, fn, mc, fs);
   } else {
 #pragma unroll
     for (int a = 0; a < 9; ++a) fs[a] = fb[a] - wf * fn[a] + (C(1) - C(0.5) * wf) * cc[a];
