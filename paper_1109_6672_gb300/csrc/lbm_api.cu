@@ -32,6 +32,7 @@ struct lbm_handle {
   bool ready = false;
   Grid grid{};
   int variant = TMA_PR_1, rows = 0;  // 1, 2: pulled-row TMA kernel; 64..256: register pull
+  int auto_rows = 0;                 // rows chosen for (variant, rows = 0); 0: not yet
   CUtensorMap maps[2][2];            // TMA descriptors [buffer][columns per thread - 1]
   double* partial = nullptr;  // reduction scratch: RED_BLOCKS x 4
   double* out4 = nullptr;     // reduction result
@@ -445,6 +446,36 @@ int create_impl(const lbm_params* p, void* stream, void* ext, int64_t ext_bytes,
 int block_cols(int variant) { return variant >= 64 ? variant - 2 : tma_cols(variant); }
 
 // Rows per block so that the step launches about one wave of blocks.
+// Rows per block of the pulled-row kernel.  Large grids keep the default
+// (6 rows, 12 for 16-bit storage; many waves of blocks); a grid that needs
+// fewer than 3 waves at the default takes the row count that minimises
+// waves x (rows + 2) (the 2: a block's fixed cost of staging its halo rows
+// and starting up, in rows), so that a mid-size grid runs in one full wave of
+// taller blocks instead of a wave and a fraction.
+int tma_rows(const lbm_handle* h, int variant) {
+  const int r0 = std::min(h->p.ny, tma_default_rows(elem_size(h->p.precision)));
+  const int bx = (h->p.nx + block_cols(variant) - 1) / block_cols(variant);
+  int occ = 0;
+  dispatch(h->p.precision, [&](auto* tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    occ = occupancy_step_tma<S>(h->grid, variant);
+    return 0;
+  });
+  const long long slots = (long long)std::max(occ, 1) * std::max(1, h->num_sms);
+  auto waves = [&](int r) { return ((long long)bx * ((h->p.ny + r - 1) / r) + slots - 1) / slots; };
+  if (waves(r0) >= 3) return r0;
+  int best = r0;
+  long long cost = waves(r0) * (r0 + 2);
+  for (int r = 2; r <= std::min(h->p.ny, 64); ++r) {
+    const long long c = waves(r) * (r + 2);
+    if (c < cost) {
+      cost = c;
+      best = r;
+    }
+  }
+  return best;
+}
+
 int auto_rows(const lbm_handle* h, int variant) {
   const int W = block_cols(variant);
   const int bx = (h->p.nx + W - 1) / W;
@@ -533,9 +564,9 @@ int lbm_step(lbm_handle* h, int64_t n) {
   if (n < 0) return fail(h, LBM_ERR_PARAM, "n must be >= 0");
   if (!h->ready) return fail(h, LBM_ERR_STATE, "lbm_step before lbm_init");
   const int variant = h->variant;
-  const int rows = h->rows > 0 ? h->rows
-                   : variant >= 64 ? auto_rows(h, variant)
-                                   : std::min(h->p.ny, tma_default_rows(elem_size(h->p.precision)));
+  if (h->rows <= 0 && h->auto_rows == 0)
+    h->auto_rows = variant >= 64 ? auto_rows(h, variant) : tma_rows(h, variant);
+  const int rows = h->rows > 0 ? h->rows : h->auto_rows;
   const int W = block_cols(variant);
   const int npt = variant >= 64 ? 1 : tma_npt(variant);
   dim3 grid((h->p.nx + W - 1) / W, (h->p.ny + rows - 1) / rows);
@@ -720,6 +751,7 @@ int lbm_set_launch(lbm_handle* h, int32_t variant, int32_t rows_per_block) {
                 "variant 2 (two nodes per thread) is built for BGK with constant tau only");
   h->variant = variant == 0 ? TMA_PR_1 : variant;
   h->rows = rows_per_block;
+  h->auto_rows = 0;
   return LBM_OK;
 }
 
