@@ -43,7 +43,7 @@ constexpr int NPOP = 18;
 constexpr int XOFF = 32;  // element offset of x = 0 within a population row
 
 // BC_INLET / BC_OUTLET: open x sides (x- / x+ only, y periodic).  The step
-// kernels treat them as walls; open_fixup_kernel (lbm_open.cuh) then rewrites
+// kernels treat them as walls; side_fixup_kernel (lbm_open.cuh) then rewrites
 // their ghost slots.
 enum { BC_PERIODIC = 0, BC_ISO = 1, BC_ADIA = 2, BC_INLET = 3, BC_OUTLET = 4 };
 enum { E_TOTAL = 0, E_INTERNAL = 1 };
