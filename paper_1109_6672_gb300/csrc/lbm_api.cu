@@ -33,6 +33,7 @@ struct lbm_handle {
   Grid grid{};
   int variant = TMA_PR_1, rows = 0;  // 1, 2: pulled-row TMA kernel; 64..256: register pull
   int auto_rows = 0;                 // rows chosen for (variant, rows = 0); 0: not yet
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // GRAPH_STEPS steps from buffer 0 / 1
   CUtensorMap maps[2][2];            // TMA descriptors [buffer][columns per thread - 1]
   double* partial = nullptr;  // reduction scratch: RED_BLOCKS x 4
   double* out4 = nullptr;     // reduction result
@@ -559,14 +560,23 @@ int lbm_init(lbm_handle* h, const double* rho, const double* ux, const double* u
   return lbm_sync(h);
 }
 
-int lbm_step(lbm_handle* h, int64_t n) {
-  if (!h) return LBM_ERR_PARAM;
-  if (n < 0) return fail(h, LBM_ERR_PARAM, "n must be >= 0");
-  if (!h->ready) return fail(h, LBM_ERR_STATE, "lbm_step before lbm_init");
-  const int variant = h->variant;
+namespace {
+
+// Steps that a cached CUDA graph replays at once (even: the buffer parity is
+// the same after it).
+constexpr int GRAPH_STEPS = 32;
+
+int step_rows(lbm_handle* h) {
   if (h->rows <= 0 && h->auto_rows == 0)
-    h->auto_rows = variant >= 64 ? auto_rows(h, variant) : tma_rows(h, variant);
-  const int rows = h->rows > 0 ? h->rows : h->auto_rows;
+    h->auto_rows = h->variant >= 64 ? auto_rows(h, h->variant) : tma_rows(h, h->variant);
+  return h->rows > 0 ? h->rows : h->auto_rows;
+}
+
+// Enqueue n steps on `stream` (the step kernel, then the second pass of the
+// open sides and of the walls of non-equilibrium extrapolation).
+cudaError_t enqueue_steps(lbm_handle* h, int64_t n, cudaStream_t stream) {
+  const int variant = h->variant;
+  const int rows = step_rows(h);
   const int W = block_cols(variant);
   const int npt = variant >= 64 ? 1 : tma_npt(variant);
   dim3 grid((h->p.nx + W - 1) / W, (h->p.ny + rows - 1) / rows);
@@ -581,26 +591,93 @@ int lbm_step(lbm_handle* h, int64_t n) {
       using S = std::remove_pointer_t<decltype(tag)>;
       if (variant >= 64) {
         const size_t smem = 3 * (size_t)variant * sizeof(typename Io<S>::C);
-        step_kernel<S><<<grid, variant, smem, h->stream>>>(g, rows);
+        step_kernel<S><<<grid, variant, smem, stream>>>(g, rows);
         e = cudaGetLastError();
       } else {
-        e = launch_step_tma<S>(g, map, variant, rows, grid, h->stream);
+        e = launch_step_tma<S>(g, map, variant, rows, grid, stream);
       }
       if (e == cudaSuccess && (g.bc[0] == BC_INLET || g.bc[1] == BC_OUTLET || g.nee)) {
         // open sides and walls of NEE: their ghost slots of the state just
         // written
         const int units = std::max(h->p.ny, g.nee ? nee_ghosts(g) : 0);
         const int blocks = std::min((units + 127) / 128, 1024);
-        side_fixup_kernel<S><<<blocks, 128, 0, h->stream>>>(g, static_cast<const S*>(g.src),
-                                                            static_cast<S*>(g.dst));
+        side_fixup_kernel<S><<<blocks, 128, 0, stream>>>(g, static_cast<const S*>(g.src),
+                                                         static_cast<S*>(g.dst));
         e = cudaGetLastError();
       }
       return 0;
     });
-    if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
+    if (e != cudaSuccess) return e;
     h->cur = 1 - h->cur;
     ++h->steps;
   }
+  return cudaSuccess;
+}
+
+// Replaying a graph is exact where the launches of a step do not depend on
+// the step count: FP32 and FP64 storage (no stochastic rounding) without an
+// inlet (whose phase follows the step count).
+bool graphable(const lbm_handle* h) {
+  return (h->p.precision == LBM_P_FP64 || h->p.precision == LBM_P_FP32) &&
+         h->p.bc[0] != LBM_BC_INLET && h->p.bc[1] != LBM_BC_OUTLET;
+}
+
+void drop_step_graphs(lbm_handle* h) {
+  for (auto& gx : h->graph) {
+    if (gx) cudaGraphExecDestroy(gx);
+    gx = nullptr;
+  }
+}
+
+// The graph of GRAPH_STEPS steps from the current buffer, captured on a
+// private stream (the handle's may be the legacy default stream).
+cudaError_t step_graph(lbm_handle* h, cudaGraphExec_t* out) {
+  cudaGraphExec_t& gx = h->graph[h->cur];
+  if (!gx) {
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    const int cur = h->cur;
+    const int64_t steps = h->steps;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t e1 = enqueue_steps(h, GRAPH_STEPS, cs);
+      const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+      e = e1 != cudaSuccess ? e1 : e2;
+    }
+    h->cur = cur;
+    h->steps = steps;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gx, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      gx = nullptr;
+      return e;
+    }
+  }
+  *out = gx;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+int lbm_step(lbm_handle* h, int64_t n) {
+  if (!h) return LBM_ERR_PARAM;
+  if (n < 0) return fail(h, LBM_ERR_PARAM, "n must be >= 0");
+  if (!h->ready) return fail(h, LBM_ERR_STATE, "lbm_step before lbm_init");
+  // long runs of identical launches: replay a captured graph of
+  // GRAPH_STEPS steps (it saves the host most of a launch per step)
+  while (n >= GRAPH_STEPS && graphable(h)) {
+    cudaGraphExec_t gx;
+    cudaError_t e = step_graph(h, &gx);
+    if (e == cudaSuccess) e = cudaGraphLaunch(gx, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step graph");
+    h->steps += GRAPH_STEPS;
+    n -= GRAPH_STEPS;
+  }
+  const cudaError_t e = enqueue_steps(h, n, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
   return LBM_OK;
 }
 
@@ -752,12 +829,14 @@ int lbm_set_launch(lbm_handle* h, int32_t variant, int32_t rows_per_block) {
   h->variant = variant == 0 ? TMA_PR_1 : variant;
   h->rows = rows_per_block;
   h->auto_rows = 0;
+  drop_step_graphs(h);
   return LBM_OK;
 }
 
 void lbm_destroy(lbm_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  drop_step_graphs(h);
   if (h->owns && h->base) cudaFree(h->base);
   if (h->partial) cudaFree(h->partial);
   if (h->staging) cudaFree(h->staging);

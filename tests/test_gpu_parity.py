@@ -190,3 +190,27 @@ def test_nonfinite_is_reported():
     with pytest.raises(lbm.LbmError) as e:
         g.moments()
     assert e.value.status == lbm.LBM_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("precision", [lbm.LBM_P_FP64, lbm.LBM_P_FP32])
+@pytest.mark.parametrize("name", ["cavity", "couette_walls"])
+def test_graph_replay_equals_single_launches(name, precision):
+    """Long lbm_step calls replay a captured graph of 32 steps; the result is
+    the same bit for bit as one launch per call (also across a change of
+    launch shape, which drops the graphs, and with walls of non-equilibrium
+    extrapolation, whose second pass is captured too)."""
+    for extra in ({}, {"wall_nee": 15} if name == "cavity" else {"wall_nee": 12}):
+        p, fields = make_case(name, precision)
+        p = dict(p, **extra)
+        a = lbm.Lbm(p).init(*fields)
+        for _ in range(70):
+            a.step(1)
+        b = lbm.Lbm(p).init(*fields).step(33).step(37)
+        np.testing.assert_array_equal(a.pops(), b.pops())
+        c = lbm.Lbm(p).init(*fields).step(40).set_launch(1, 3).step(30)
+        d = lbm.Lbm(p).init(*fields).step(40).set_launch(1, 3)
+        for _ in range(30):
+            d.step(1)
+        np.testing.assert_array_equal(c.pops(), d.pops())
+        for g in (a, b, c, d):
+            g.close()
