@@ -60,7 +60,8 @@
  *    theta_F / 2) and F's
  *    pressure (rho_G = rho_F theta_F / theta_G, since p = rho R T); its
  *    pre-collision populations are its equilibria plus F's non-equilibrium
- *    part; it collides like a fluid node (force of its own density, no
+ *    part (for h on an adiabatic wall, without that part's normal energy
+ *    flux); it collides like a fluid node (force of its own density, no
  *    correction term) and sends its populations into the domain.  A corner
  *    ghost at the end of an x side's column feeds the corner node (the x side
  *    wins); Eq. 50 across such a wall keeps the mirror ghost above.  Written

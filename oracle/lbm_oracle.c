@@ -66,7 +66,8 @@
  * node inward) and F's pressure (rho_G = rho_F theta_F / theta_G: p = rho R T,
  * so equal density would push mass through the wall).  Its pre-collision
  * populations are its equilibria plus F's non-equilibrium part
- * fbar(F) - f^eq(F) (likewise for h), and it collides like any node, with
+ * fbar(F) - f^eq(F) (likewise for h; on an adiabatic wall without the normal
+ * energy flux that part carries), and it collides like any node, with
  * the Guo force of its own density and no correction term; G emits the
  * post-collision populations pointing into the domain, and what leaves
  * through the side is dropped.
@@ -634,6 +635,18 @@ static void phase2(orc_state* s, int nthreads) {
         for (int a = 0; a < 9; ++a) {
           fbG[a] = eqfG[a] + (fb[a] - feq[a]);
           hbG[a] = eqhG[a] + (hb[a] - heq[a]);
+        }
+        if (p->bc[side] == ORC_WALL_ADIABATIC) {
+          /* an adiabatic wall node carries no normal energy flux: the
+           * normal moment of the borrowed h non-equilibrium part is taken
+           * out (its energy and tangential moments are untouched) */
+          double qn = 0.0, wn = 0.0;
+          for (int a = 0; a < 9; ++a) {
+            const double en = EX[a] * nxo + EY[a] * nyo;
+            qn += en * (hb[a] - heq[a]);
+            wn += W[a] * en * en;
+          }
+          for (int a = 0; a < 9; ++a) hbG[a] -= W[a] * (EX[a] * nxo + EY[a] * nyo) * qn / wn;
         }
         orc_force(RT0, uwx, uwy, 0.0, -rG * p->g, CG);
         collide(p, rG, uwx, uwy, thG, esG, fbG, hbG, CG, dummyf, dummyh, fG, hG);

@@ -85,7 +85,8 @@ __device__ void open_rows(const Grid& g, S* __restrict__ dst, int first, int str
 // floored at theta_F / 2 so that the density below stays finite), and
 // F's pressure, rho_G = rho_F theta_F / theta_G.  Its pre-collision
 // populations are its equilibria plus F's non-equilibrium part
-// fbar(F) - f^eq(F) (likewise h); it collides like a fluid node (rates of
+// fbar(F) - f^eq(F) (likewise h; on an adiabatic side without the normal
+// energy flux of that part); it collides like a fluid node (rates of
 // its own rho and theta, the Guo force of its own density, no correction
 // term), and the populations it sends into the domain are stored where the
 // receiving nodes pull them.  Ghost k of a grid: 0 .. ny + 1 the x- column
@@ -148,10 +149,20 @@ __device__ void nee_ghost(const Grid& g, const S* __restrict__ src, S* __restric
   const C EsG = kp.b6 * thG + (total ? C(0.5) * (uwx * uwx + uwy * uwy) : C(0));
   C fqG[9], hqG[9], fb[9], hb[9];
   collision_equilibria<C>(rG, uwx, uwy, thG, EsG, kp.b6, total, fqG, hqG);
+  C hn[9], qn = C(0);
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     fb[a] = fqG[a] + ((pref<S>(g, a) + d[a]) - feq[a]);
-    hb[a] = hqG[a] + ((pref<S>(g, 9 + a) + d[9 + a]) - heq[a]);
+    hn[a] = (pref<S>(g, 9 + a) + d[9 + a]) - heq[a];
+    qn += C(ex(a) * nxo + ey(a) * nyo) * hn[a];
+  }
+  // an adiabatic wall node carries no normal energy flux: the normal moment
+  // of the borrowed h non-equilibrium part is taken out (sum w e_n^2 = 1/3)
+  const bool adia = g.bc[side] != BC_ISO;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const C en = C(ex(a) * nxo + ey(a) * nyo);
+    hb[a] = hqG[a] + (adia ? hn[a] - wgt<C>(a) * en * qn * C(3) : hn[a]);
   }
   // collision of G
   C wf, wh, kz;

@@ -252,7 +252,12 @@ class Brute:
                         hG = (heq_total(rG, uw[0], uw[1], tG, p["b"], fG) if p["energy_model"] == 0
                               else heq_internal(tG, p["b"], fG))
                         fbG = np.array(fG) + self.F[:, fy, fx] - feq[:, fy, fx]
-                        hbG = np.array(hG) + self.H[:, fy, fx] - heq[:, fy, fx]
+                        hneq = self.H[:, fy, fx] - heq[:, fy, fx]
+                        if p["bc"][side] == ADIA:  # no normal energy flux at the wall node
+                            nxo, nyo = [(-1, 0), (1, 0), (0, -1), (0, 1)][side]
+                            en = EX * nxo + EY * nyo
+                            hneq = hneq - W * en * (en @ hneq) / (W @ (en * en))
+                        hbG = np.array(hG) + hneq
                         CG = np.array([W[k] * (3 * EY[k] * (-rG * p["g"]) + 9 * (
                             (EX[k] * uw[0] + EY[k] * uw[1]) * EY[k] * (-rG * p["g"]) -
                             (uw[1] * (-rG * p["g"])) / 3)) for k in range(9)])

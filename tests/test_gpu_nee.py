@@ -78,3 +78,38 @@ def test_nee_large_dt_cavity_without_gravity_stays_at_rest():
     rho, ux, uy, T = g.moments()
     g.close()
     assert max(np.abs(ux).max(), np.abs(uy).max()) < 1e-5
+
+
+@pytest.mark.parametrize("row", [(1, 0.35, 1.0408, 0.74), (3, 0.35, 1.1225, 0.65),
+                                 (5, 0.25, 1.1042, 0.58), (5, 0.15, 1.0375, 0.53)],
+                         ids=lambda r: f"Pr{r[0]}-Ma{r[1]}")
+def test_nee_table1_couette(row):
+    """The paper's mu ~ T Couette of Table I with its own wall method: 60 nodes
+    across including the two wall nodes, adiabatic lower wall, MRT rates 1.5,
+    correction omitted; the lower-wall temperature (the wall node's) within
+    the paper's own E_r (Eq. 52a; fixture tests/golden/table1_couette.txt).
+    (Pr = 5, Ma = 0.35 puts the wall at theta 1.2, where the b = 3
+    total-energy rest weight of h^eq vanishes; it stays bounded but off.)"""
+    import math
+    Pr, Ma, Ta, Er_paper = row
+    U = Ma * math.sqrt(5.0 / 9.0)
+    tau_f = 0.75
+    p = inputs.base_params(10, 58, tau_f=tau_f, tau_h=tau_f / Pr, b=3.0, correction=0,
+                           bc=[inputs.PERIODIC, inputs.PERIODIC, inputs.WALL_ADIABATIC,
+                               inputs.WALL_ISOTHERMAL],
+                           u_wall=[[0, 0], [0, 0], [0, 0], [U, 0]], mu_law=lbm.LBM_MU_POWER,
+                           mu_n=1.0, collision=lbm.LBM_COLL_MRT, s_e=1.5, s_eps=1.5, s_q=1.5,
+                           wall_nee=12, precision=lbm.LBM_P_FP32)
+    g = lbm.Lbm(p).init(*inputs.uniform_fields(10, 58, seed=0))
+    prev, steps, Tw = None, 0, None
+    while steps < 1_000_000:
+        g.step(25000)
+        steps += 25000
+        T = g.moments()[3][:, 0]
+        Tw = (4 * T[0] - T[1]) / 3
+        if prev is not None and abs(Tw - prev) < 1e-6:  # FP32 rounding of T ~ 1e-7
+            break
+        prev = Tw
+    g.close()
+    assert steps < 1_000_000, "not converged"
+    assert abs((Tw - 1) - (Ta - 1)) / (Ta - 1) <= Er_paper / 100
