@@ -58,7 +58,8 @@
  *    velocity, theta_G (the wall's; adiabatic: zero slope at G to second
  *    order, (4 theta_F - theta_F2)/3, F2 the next node inward, floored at
  *    theta_F / 2) and F's
- *    pressure (rho_G = rho_F theta_F / theta_G, since p = rho R T); its
+ *    pressure carried to G by hydrostatic balance (rho_G theta_G =
+ *    rho_F (theta_F - 3 g n_y), since p = rho R T); its
  *    pre-collision populations are its equilibria plus F's non-equilibrium
  *    part (for h on an adiabatic wall, without that part's normal energy
  *    flux); it collides like a fluid node (force of its own density, no

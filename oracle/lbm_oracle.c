@@ -63,8 +63,10 @@
  * spacing outside the boundary node F.  G's state is the wall velocity,
  * theta_G (theta_w on an isothermal wall; on an adiabatic one zero normal
  * gradient at G to second order, (4 theta_F - theta_F2)/3 with F2 the next
- * node inward) and F's pressure (rho_G = rho_F theta_F / theta_G: p = rho R T,
- * so equal density would push mass through the wall).  Its pre-collision
+ * node inward) and F's pressure carried to G by hydrostatic balance
+ * (rho_G theta_G = rho_F (theta_F - 3 g n_y): p = rho R T, so equal density
+ * would push mass through the wall, and so would gravity without the
+ * hydrostatic term).  Its pre-collision
  * populations are its equilibria plus F's non-equilibrium part
  * fbar(F) - f^eq(F) (likewise for h; on an adiabatic wall without the normal
  * energy flux that part carries), and it collides like any node, with
@@ -627,7 +629,9 @@ static void phase2(orc_state* s, int nthreads) {
          * pre-collision populations are its equilibria plus F's
          * non-equilibrium part, and it collides like any node, with the
          * force of its own density (no correction term) */
-        const double rG = rho * th / thG;
+        /* F's pressure carried one spacing outward by hydrostatic balance,
+         * p_G = p_F - rho_F g n_y (a = (0, -rho g), R T0 = 1/3) */
+        const double rG = rho * (th - 3.0 * p->g * nyo) / thG;
         const double esG = 0.5 * (p->b * RT0 * thG +
                                   (p->energy_model == ORC_E_TOTAL ? uwx * uwx + uwy * uwy : 0.0));
         double eqfG[9], eqhG[9], fbG[9], hbG[9], CG[9], fG[9], hG[9], dummyf[9], dummyh[9];

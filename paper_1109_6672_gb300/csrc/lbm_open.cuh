@@ -83,7 +83,8 @@ __device__ void open_rows(const Grid& g, S* __restrict__ dst, int first, int str
 // (the wall's on an isothermal side; on an adiabatic side zero slope at G to
 // second order, (4 theta_F - theta_F2)/3 with F2 the next node inward,
 // floored at theta_F / 2 so that the density below stays finite), and
-// F's pressure, rho_G = rho_F theta_F / theta_G.  Its pre-collision
+// F's pressure carried to G by hydrostatic balance,
+// rho_G = rho_F (theta_F - 3 g n_y) / theta_G.  Its pre-collision
 // populations are its equilibria plus F's non-equilibrium part
 // fbar(F) - f^eq(F) (likewise h; on an adiabatic side without the normal
 // energy flux of that part); it collides like a fluid node (rates of
@@ -145,7 +146,9 @@ __device__ void nee_ghost(const Grid& g, const S* __restrict__ src, S* __restric
     moments<S>(g, d2, r2, u2, v2, t2, e2);
     thG = fmax((C(4) * th - t2) * C(1.0 / 3.0), C(0.5) * th);  // floored: rho_G = rho th / thG
   }
-  const C rG = rho * th / thG, uwx = kp.uw[side][0], uwy = kp.uw[side][1];
+  // F's pressure carried to G by hydrostatic balance, p_G = p_F - rho_F g n_y
+  const C rG = rho * (th - C(3) * kp.g * C(nyo)) / thG;
+  const C uwx = kp.uw[side][0], uwy = kp.uw[side][1];
   const C EsG = kp.b6 * thG + (total ? C(0.5) * (uwx * uwx + uwy * uwy) : C(0));
   C fqG[9], hqG[9], fb[9], hb[9];
   collision_equilibria<C>(rG, uwx, uwy, thG, EsG, kp.b6, total, fqG, hqG);

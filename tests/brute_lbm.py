@@ -247,7 +247,8 @@ class Brute:
                         else:  # zero slope at the wall node: quadratic through F, F2
                             nxo, nyo = [(-1, 0), (1, 0), (0, -1), (0, 1)][side]
                             tG = max((4 * t - th[fy - nyo, fx - nxo]) / 3, 0.5 * t)
-                        rG = r * t / tG
+                        nyo = [0, 0, -1, 1][side]
+                        rG = r * (t - 3 * p["g"] * nyo) / tG  # hydrostatic pressure at G
                         fG = feq_shells(rG, uw[0], uw[1], tG)
                         hG = (heq_total(rG, uw[0], uw[1], tG, p["b"], fG) if p["energy_model"] == 0
                               else heq_internal(tG, p["b"], fG))
