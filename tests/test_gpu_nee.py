@@ -88,8 +88,9 @@ def test_nee_table1_couette(row):
     across including the two wall nodes, adiabatic lower wall, MRT rates 1.5,
     correction omitted; the lower-wall temperature (the wall node's) within
     the paper's own E_r (Eq. 52a; fixture tests/golden/table1_couette.txt).
-    (Pr = 5, Ma = 0.35 puts the wall at theta 1.2, where the b = 3
-    total-energy rest weight of h^eq vanishes; it stays bounded but off.)"""
+    (Pr = 5, Ma = 0.35 puts the wall at theta 1.2, where a uniform box at
+    these parameters is already unstable to grid-scale noise; that run
+    reaches no steady state.)"""
     import math
     Pr, Ma, Ta, Er_paper = row
     U = Ma * math.sqrt(5.0 / 9.0)
