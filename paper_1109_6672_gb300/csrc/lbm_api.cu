@@ -291,6 +291,8 @@ void fill_grid(const lbm_params* p, Grid& g) {
   }
   g.href_sum = hs;
   g.dref = hs - p->b / 6.0;
+  g.pd.dref = g.dref;
+  g.pf.dref = (float)g.dref;
   g.in_rho = p->in_rho;
   g.in_drho = p->in_drho;
   g.in_du = p->in_du;

@@ -84,6 +84,7 @@ struct Phys {
   C omega_f, omega_h;  // 2 / (2 tau + 1)
   C g;                 // gravity, a = (0, -rho g)
   C b6, six_b;         // b / 6 and 6 / b
+  C dref;              // sum of the h references - b/6 (deviation storage)
   C uw[4][2];          // wall velocities
   C thw[4];            // wall theta = T_w / T0
   C kz;                // coefficient of the Z coupling of h (Eq. 36 / Eq. 47)
@@ -160,13 +161,17 @@ struct Io<__half> {
   __device__ static __half ld(const __half* p) { return __ldg(p); }
   __device__ static float to(__half v) { return __half2float(v) * (1.0f / 256.0f); }
   __device__ static __half from(float v) { return __float2half_rn(v * 256.0f); }
-  __device__ static __half from_sr(float v, unsigned r) {
-    const float x = v * 256.0f;
-    if (!(fabsf(x) < 65504.0f)) return __float2half_rn(x);
-    // FP32 -> FP16 keeps 10 of 23 mantissa bits: add 13 random bits, cut
-    // them, and convert the now exactly representable value
-    const unsigned u = (__float_as_uint(x) + (r >> 19)) & 0xFFFFE000u;
+  // |256 v| below the FP16 maximum 65504 (false for NaN)
+  __device__ static bool in_range(float v) { return fabsf(v) < 255.875f; }
+  // stochastic rounding of an in-range value: FP32 -> FP16 keeps 10 of 23
+  // mantissa bits, so add 13 random bits, cut them, and convert the now
+  // exactly representable value
+  __device__ static __half from_sr_in_range(float v, unsigned r) {
+    const unsigned u = (__float_as_uint(v * 256.0f) + (r >> 19)) & 0xFFFFE000u;
     return __float2half_rz(__uint_as_float(u));
+  }
+  __device__ static __half from_sr(float v, unsigned r) {
+    return in_range(v) ? from_sr_in_range(v, r) : __float2half_rn(v * 256.0f);
   }
 };
 template <>
@@ -177,11 +182,15 @@ struct Io<__nv_bfloat16> {
   __device__ static __nv_bfloat16 ld(const __nv_bfloat16* p) { return __ldg(p); }
   __device__ static float to(__nv_bfloat16 v) { return __bfloat162float(v); }
   __device__ static __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
+  // finite (false for infinities and NaN)
+  __device__ static bool in_range(float v) { return fabsf(v) <= 3.40282347e38f; }
+  // stochastic rounding of a finite value: BF16 is the upper half of FP32,
+  // so add 16 random bits below it and cut
+  __device__ static __nv_bfloat16 from_sr_in_range(float v, unsigned r) {
+    return __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (r >> 16)) >> 16));
+  }
   __device__ static __nv_bfloat16 from_sr(float v, unsigned r) {
-    const unsigned u = __float_as_uint(v);
-    if ((u & 0x7F800000u) == 0x7F800000u) return __float2bfloat16_rn(v);
-    // BF16 is the upper half of FP32: add 16 random bits below it and cut
-    return __ushort_as_bfloat16((unsigned short)((u + (r >> 16)) >> 16));
+    return in_range(v) ? from_sr_in_range(v, r) : __float2bfloat16_rn(v);
   }
 };
 

@@ -57,15 +57,18 @@ inline int mode_of(const Grid& g) {
   return m;
 }
 
-// Moments (Eq. 35 with the force shift, Eq. 37 or the Eq. 38 form); deviation
-// storage forms rho E - rho u^2 / 2 in FP64.
 // Moments of the pulled populations d (Eq. 35 with the force shift under
 // Eq. 51; Eq. 37 or the Eq. 38 form for theta).  Absolute storage returns
 // r0 = rho, rth = theta, res = Es (= sum h / rho); deviation storage returns
 // the deviations from the rest state, r0 = rho - 1, rth = theta - 1,
 // res = Es - b/6, formed from the sums of the stored deviations so that
-// nothing is rounded at the scale of the populations.  16-bit storage forms
-// the balance of internal energy, rho (Es - b/6) - rho u^2 / 2, in FP64.
+// nothing is rounded at the scale of the populations (the references' own
+// sums are taken in FP64 on the host: dref).  The balance of internal
+// energy, rho (Es - b/6) - rho u^2 / 2, is then one subtraction of two FP32
+// numbers, and FP32's correctly rounded subtraction gives the value an FP64
+// subtraction rounded back to FP32 would: the exact difference is an FP64
+// number when the exponents differ by at most 28, and otherwise lies within
+// 2^-28 of the larger operand, far from any FP32 rounding tie.
 template <class S, int M>
 __device__ __forceinline__ void moments_m(const Grid& g, const typename Io<S>::C d[NPOP],
                                           typename Io<S>::C& r0, typename Io<S>::C& ux,
@@ -90,16 +93,16 @@ __device__ __forceinline__ void moments_m(const Grid& g, const typename Io<S>::C
   if constexpr (Io<S>::dev) {
     r0 = sf;
     if constexpr (sizeof(S) == 2) {
-      const C e = (C)g.dref + sh - k.b6 * sf;  // rho (Es - b/6): small terms only
+      const C e = k.dref + sh - k.b6 * sf;  // rho (Es - b/6): small terms only
       res = e * inv;
       if constexpr (MD::total) {
-        const double ei = (double)e - 0.5 * (double)(rho * (ux * ux + uy * uy));
-        rth = k.six_b * (C)ei * inv;
+        const C kin = C(0.5) * (rho * (ux * ux + uy * uy));
+        rth = k.six_b * __fsub_rn(e, kin) * inv;
       } else {
         rth = k.six_b * res;
       }
     } else {
-      res = ((C)g.dref + sh - k.b6 * sf) * inv;
+      res = (k.dref + sh - k.b6 * sf) * inv;
       rth = k.six_b * (MD::total ? res - C(0.5) * (ux * ux + uy * uy) : res);
     }
   } else if constexpr (MD::total) {
@@ -197,6 +200,22 @@ __device__ __forceinline__ void collide_m(const Grid& g, S* __restrict__ p, int 
     v[18 + a] = heq[a];
   }
   unsigned r = Io<S>::sr ? sr_hash(g, x, y) : 0u;
+  if constexpr (Io<S>::sr) {
+    // one range test for the node's 18 values, then the rounding without
+    // the per-value test (same results; a node with a value out of range
+    // takes the per-value stores below)
+    bool in_range = true;
+#pragma unroll
+    for (int a = 0; a < NPOP; ++a) in_range = in_range && Io<S>::in_range(v[a]);
+    if (in_range) {
+#pragma unroll
+      for (int a = 0; a < NPOP; ++a) {
+        r = lcg_next(r);
+        p[plane(a) * pitch] = Io<S>::from_sr_in_range(v[a], r);
+      }
+      return;
+    }
+  }
 #pragma unroll
   for (int a = 0; a < NPOP; ++a) {
     if constexpr (Io<S>::sr) r = lcg_next(r);
