@@ -100,8 +100,9 @@ enum {
 enum { LBM_E_TOTAL = 0, LBM_E_INTERNAL = 1 };
 /* Storage / arithmetic: FP64 everywhere; FP32 everywhere; FP32 arithmetic with
  * populations stored as FP16 or BF16 deviations from the rest equilibrium
- * (rho = 1, u = 0, T = T0; the step computed on deviations), T recovered and
- * reductions accumulated in FP64.
+ * (rho = 1, u = 0, T = T0; the step computed on deviations), T recovered from
+ * deviation sums and FP64 reference sums (its last subtraction, of two FP32
+ * numbers, rounds as in FP64), reductions accumulated in FP64.
  * The 16-bit stores of a time step round stochastically (zero-mean error;
  * the random bits are a function of step, node and population only, see
  * lbm_set_steps_done); FP16 holds 256 x the deviation. */
