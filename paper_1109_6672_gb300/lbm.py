@@ -150,8 +150,22 @@ def make_params(p: dict) -> lbm_params:
 
 
 def _dp(a: np.ndarray):
-    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("host buffers must be C-contiguous float64 arrays")
     return a.ctypes.data_as(_DP)
+
+
+# (ny, nx) of every live handle that lbm_create / lbm_create_in returned: the
+# C entry points read or write nx*ny (or 18*nx*ny) doubles through the host
+# pointers they get, so buffers of another size are refused before the call.
+_shapes: dict[int, tuple[int, int]] = {}
+
+
+def _check_size(h, a: np.ndarray, per_node: int, what: str):
+    shape = _shapes.get(getattr(h, "value", h))
+    if shape is not None and a.size != per_node * shape[0] * shape[1]:
+        raise ValueError(f"{what}: {a.size} values for a {shape[0]} x {shape[1]} grid "
+                         f"(expected {per_node * shape[0] * shape[1]})")
 
 
 def _check(status: int, h=None):
@@ -172,6 +186,7 @@ def lbm_create(params: dict, stream: int = 0):
     h = _H()
     _check(load().lbm_create(ctypes.byref(make_params(params)), ctypes.c_void_p(stream or None),
                              ctypes.byref(h)))
+    _shapes[h.value] = (int(params["ny"]), int(params["nx"]))
     return h
 
 
@@ -179,11 +194,14 @@ def lbm_create_in(params: dict, device_buffer: int, nbytes: int, stream: int = 0
     h = _H()
     _check(load().lbm_create_in(ctypes.byref(make_params(params)), ctypes.c_void_p(stream or None),
                                 ctypes.c_void_p(device_buffer), int(nbytes), ctypes.byref(h)))
+    _shapes[h.value] = (int(params["ny"]), int(params["nx"]))
     return h
 
 
 def lbm_init(h, rho, ux, uy, T):
     arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (rho, ux, uy, T)]
+    for a in arrs:
+        _check_size(h, a, 1, "lbm_init")
     _check(load().lbm_init(h, *[_dp(a) for a in arrs]), h)
 
 
@@ -197,6 +215,7 @@ def lbm_step(h, n: int = 1):
 
 def lbm_moments(h, shape):
     out = [np.empty(shape, dtype=np.float64) for _ in range(4)]
+    _check_size(h, out[0], 1, "lbm_moments")
     _check(load().lbm_moments(h, *[_dp(a) for a in out]), h)
     return tuple(out)
 
@@ -222,12 +241,14 @@ def lbm_conserved_noalloc(params: dict, d_state: int, d_out: int, stream: int = 
 
 def lbm_get_state(h, shape) -> np.ndarray:
     out = np.empty((18,) + tuple(shape), dtype=np.float64)
+    _check_size(h, out, 18, "lbm_get_state")
     _check(load().lbm_get_state(h, _dp(out)), h)
     return out
 
 
 def lbm_set_state(h, pops: np.ndarray):
     a = np.ascontiguousarray(pops, dtype=np.float64)
+    _check_size(h, a, 18, "lbm_set_state")
     _check(load().lbm_set_state(h, _dp(a)), h)
 
 
@@ -254,6 +275,7 @@ def lbm_set_launch(h, threads: int, rows_per_block: int = 0):
 
 def lbm_destroy(h):
     if h:
+        _shapes.pop(getattr(h, "value", h), None)
         load().lbm_destroy(h)
 
 
