@@ -9,7 +9,8 @@ all admitted grids together in segments of k steps (one graph launch per
 segment, one kernel launch per step covering every grid); between segments
 finished requests are read back (moments) and released and queued requests are
 admitted, so work that arrives while others run overlaps with them on the
-device.  Latency = completion - arrival (queueing included).
+device.  Latency = completion - arrival (queueing included).  A request that
+does not fit even the empty pool fails alone (it could never be admitted).
 
 The batch backend is injected, so the scheduling logic also runs against a
 host-only stand-in in the CPU tests.
@@ -23,6 +24,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import inputs
+from .lbm import LBM_ERR_NONFINITE, LBM_ERR_OOM
 
 
 @dataclass
@@ -146,9 +148,14 @@ class Server:
                 try:
                     slot = self.batch.add(p, f, r.steps)
                 except Exception as e:  # no slot / no room: keep waiting
-                    if getattr(e, "status", None) not in (-2,):
+                    if getattr(e, "status", None) != LBM_ERR_OOM:
                         raise
-                    still.append(r)
+                    if not active:  # refused by the empty pool: never fits
+                        t = self.clock() - t0
+                        results.append(Result(r.rid, r.kind, r.nodes, r.steps, r.arrival, t, t,
+                                              None, "does not fit the device pool"))
+                    else:
+                        still.append(r)
                     continue
                 active[slot] = (r, self.clock() - t0)
             queue = still
@@ -171,7 +178,7 @@ class Server:
                 try:
                     mom = self.batch.moments(s)
                 except Exception as e:  # a diverged simulation fails alone
-                    if getattr(e, "status", None) != -4:
+                    if getattr(e, "status", None) != LBM_ERR_NONFINITE:
                         raise
                     mom, err = None, "non-finite result"
                 self.batch.remove(s)

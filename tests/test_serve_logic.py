@@ -122,3 +122,19 @@ def test_trace_is_seeded_and_has_the_mix():
     assert 0.55 < frac < 0.85
     assert all(1000 <= r.steps <= 100000 for r in a)
     assert abs(a[-1].arrival / 200 - 1 / 50) < 0.01
+
+
+def test_request_larger_than_the_pool_fails_alone():
+    clock = Clock()
+    fb = FakeBatch(slots=4, node_budget=60 * 60, clock=clock)
+    srv = serve.Server(fb, precision=3, seg_max=16, seg_min=4, clock=clock, sleep=clock.sleep)
+    trace = [serve.Request(0, "cavity", 0.0, 40, dict(n=50, Ra=1e4, dT_over_T0=0.1)),
+             serve.Request(1, "cavity", 0.0, 40, dict(n=100, Ra=1e4, dT_over_T0=0.1)),
+             serve.Request(2, "cavity", 1e-3, 40, dict(n=100, Ra=1e4, dT_over_T0=0.1))]
+    res = {r.rid: r for r in srv.run(trace)}  # must end: nothing can ever admit 1 or 2
+    assert set(res) == {0, 1, 2}
+    assert res[0].error == ""
+    assert res[1].error and res[2].error
+    assert res[1].finished >= res[0].admitted  # tried again after 0 left, then failed
+    s = serve.summarize(list(res.values()), srv.wall, srv.node_updates)
+    assert s["failed"] == 2
