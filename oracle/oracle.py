@@ -83,7 +83,9 @@ _lib = None
 def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(str(build()))
+        # LBM_ORACLE_LIB: a variant build of lbm_oracle.c, for the tests that
+        # plant a mistake in a copy of the source and check that a pin fails
+        _lib = ctypes.CDLL(os.environ.get("LBM_ORACLE_LIB") or str(build()))
         dp = ctypes.POINTER(ctypes.c_double)
         _lib.orc_new.restype = ctypes.c_void_p
         _lib.orc_new.argtypes = [ctypes.POINTER(OrcParams)]

@@ -1,0 +1,99 @@
+"""Planted mistakes: each test copies oracle/lbm_oracle.c, plants one plausible
+mistake (a flipped sign, a dropped term, a wrong rate or exponent), builds the
+copy, and runs the fast oracle pins against it in a child process
+(LBM_ORACLE_LIB).  At least one pin must fail.  The pins run here are those
+fixed by the paper or by the mathematics (closed forms, moment constraints,
+conservation, decay rates, the paper's tables); the comparisons with the
+NumPy restatement are left out, so that the mistake is caught by something
+other than a second reading of the same equations.  The unmodified source,
+built the same way, passes the same pins.
+
+Not in the list, because no such pin can see it: the -u^2/2 part of Z_a in
+the coupling term of Eq. 36.  The paper notes that Z_a reduces to e_a.u at
+the Navier-Stokes level, so the closed forms, decay rates and tables do not
+depend on it (its sign flipped passes every pin here); it is checked against
+the NumPy restatement only."""
+import os
+import subprocess
+import sys
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parent.parent
+SRC = ROOT / "oracle" / "lbm_oracle.c"
+
+PIN_FILES = [str(ROOT / "tests" / f) for f in (
+    "test_oracle_equilibria.py", "test_oracle_correction.py", "test_oracle_step.py",
+    "test_oracle_physics.py", "test_oracle_mrt.py", "test_oracle_viscosity.py",
+    "test_oracle_nee.py", "test_oracle_acoustic.py")]
+# the restatement comparisons, and the pins slower than about two seconds
+DESELECT = ("not brute and not couette_b_five and not small_tau_stability and not table1 "
+            "and not large_dt_cavity and not mu_proportional")
+
+# (name, text in lbm_oracle.c, replacement, what the mistake is)
+MUTANTS = [
+    ("feq_third_order_sign", "(esq / RT0 - DIM - 2.0)", "(esq / RT0 - DIM + 2.0)",
+     "Eq. 18a: sign in the theta-dependent third-order term"),
+    ("heq_drops_linear_term", "double br = eu / RT0 + ", "double br = ",
+     "Eq. 18b: the e.u / RT0 term of the bracket dropped"),
+    ("correction_sign", "out[1] = -phx / 36.0 + phy / 4.0;", "out[1] = -phx / 36.0 - phy / 4.0;",
+     "Eq. 49: sign of the Q-difference piece in C_1"),
+    ("no_half_force_shift", "double vy = (jy + 0.5 * ay) / r;", "double vy = jy / r;",
+     "text under Eq. 51: the a/2 shift of the velocity dropped"),
+    ("omega_is_one_over_tau", "const double wf = 2.0 / (2.0 * tau_f + 1.0);",
+     "const double wf = 1.0 / tau_f;", "below Eq. 34: omega_f = 1 / tau_f"),
+    ("coupling_sign", ": wh - wf;", ": wf - wh;", "Eq. 36: (omega_h - omega_f) reversed"),
+    ("T_without_kinetic_energy",
+     "T = 2.0 / (p->b * p->R) * (sh / r - 0.5 * (vx * vx + vy * vy));",
+     "T = 2.0 / (p->b * p->R) * (sh / r);", "Eq. 37: kinetic energy not subtracted"),
+    ("guo_force_drops_velocity_term",
+     "out[a] = W[a] * (ea / RT0 + (ua_ee - RT0 * ua) / (RT0 * RT0));",
+     "out[a] = W[a] * (ea / RT0);", "Guo force: the u-dependent term dropped"),
+    ("mrt_source_factor", "(1.0 - 0.5 * S[k]) * Ch[k]", "(1.0 + 0.5 * S[k]) * Ch[k]",
+     "Eq. 44: (I - S/2) C-hat with the wrong sign"),
+    ("sutherland_exponent", "pow(th, 1.5) * (1.0 + p->mu_S)", "pow(th, 0.5) * (1.0 + p->mu_S)",
+     "Eq. 59: exponent 1/2 instead of 3/2"),
+    ("iso_ghost_theta", "fmax(2.0 * thw - th, 0.5 * thw)", "fmax(2.0 * th - thw, 0.5 * thw)",
+     "isothermal ghost: theta_w and theta swapped"),
+    ("nee_pressure_not_carried", "const double rG = rho * (th - 3.0 * p->g * nyo) / thG;",
+     "const double rG = rho;", "non-equilibrium wall node at the neighbour's density"),
+]
+
+
+def _build(src_text: str, out: Path) -> Path:
+    c = out.with_suffix(".c")
+    c.write_text(src_text)
+    base = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", str(c), "-o", str(out), "-lm"]
+    r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.run(base, check=True, capture_output=True)
+    return out
+
+
+def _pins(lib: Path, first_failure: bool) -> subprocess.CompletedProcess:
+    env = dict(os.environ, LBM_ORACLE_LIB=str(lib))
+    cmd = [sys.executable, "-m", "pytest", *PIN_FILES, "-q", "-p", "no:cacheprovider",
+           "-m", "not gpu", "-k", DESELECT]
+    try:
+        import xdist  # noqa: F401
+        cmd += ["-n", "4"]
+    except ImportError:
+        pass
+    if first_failure:
+        cmd.append("-x")
+    return subprocess.run(cmd, env=env, cwd=str(ROOT), capture_output=True, text=True,
+                          timeout=600)
+
+
+def test_unmodified_source_passes_the_pins(tmp_path):
+    r = _pins(_build(SRC.read_text(), tmp_path / "orig.so"), first_failure=False)
+    assert r.returncode == 0, r.stdout[-3000:]
+
+
+@pytest.mark.parametrize("name,old,new,what", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(tmp_path, name, old, new, what):
+    text = SRC.read_text()
+    assert text.count(old) == 1, f"{name}: target text not found once"
+    r = _pins(_build(text.replace(old, new), tmp_path / f"{name}.so"), first_failure=True)
+    assert r.returncode != 0, f"{name} ({what}) passed every pin"
