@@ -8,13 +8,15 @@
  * baseline do.  It shares no code, header, table or constant with the CUDA
  * library: every constant below is written out here from the paper.
  *
- * Parity unpinned, in part: the -u^2/2 part of Z_a in the coupling term of
- * Eq. 36 (the full Z form).  The paper notes that Z_a reduces to e_a.u at
- * the Navier-Stokes level, so no closed form, decay rate or table it fixes
- * depends on that part; its sign is checked only against the independent
- * NumPy restatement.  Every other piece of the step is caught by a pin the
- * paper or the mathematics fixes when a plausible mistake is planted in it
- * (tests/test_oracle_mutants.py).
+ * Parity unpinned, in part: (1) the -u^2/2 part of Z_a in the coupling
+ * term of Eq. 36 (the full Z form).  The paper notes that Z_a reduces to
+ * e_a.u at the Navier-Stokes level, so no closed form, decay rate or table
+ * it fixes depends on that part.  (2) Q of the ghost node across a wall in
+ * the Eq. 50 differences (the mirror 2 Q_w - Q, a reading: the paper does
+ * not say), whose effect is of the order of Ma^3.  Both are checked only
+ * against the independent NumPy restatement.  The other pieces of the step
+ * tried so far are caught by a pin the paper or the mathematics fixes when
+ * a plausible mistake is planted in them (tests/test_oracle_mutants.py).
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared [-fopenmp] (no FMA
  * contraction, so every product and sum is rounded as written).
