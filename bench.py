@@ -69,7 +69,9 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+    """nvidia-smi clocks and throttle reasons: one sample just before the
+    timed region, samples every 200 ms during it, and one just after (so a
+    region shorter than the polling period still has a record)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -80,7 +82,17 @@ class ClockSampler:
         self.proc = None
         self.path = os.path.join("/tmp", f"lbm_clocks_{os.getpid()}.csv")
 
+    def one_shot(self):
+        try:
+            r = subprocess.run(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                               timeout=20)
+            return r.stdout
+        except Exception:
+            return ""
+
     def __enter__(self):
+        self.edges = [self.one_shot()]
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
@@ -98,16 +110,21 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
             self.f.close()
+        self.edges.append(self.one_shot())
 
     def summary(self):
-        if self.proc is None:
+        lines = []
+        if self.proc is not None:
+            with open(self.path) as f:
+                lines = f.read().splitlines()
+        lines += [ln for chunk in self.edges for ln in chunk.splitlines()]
+        if self.proc is None and not lines:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         rows = []
-        with open(self.path) as f:
-            for line in f:
-                parts = [s.strip() for s in line.split(",")]
-                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
-                    rows.append(parts)
+        for line in lines:
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                rows.append(parts)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         mine = [r for r in rows if r[0] == str(self.gpu)]
@@ -422,19 +439,26 @@ def run_ours(args, rank, world, local_rank):
     achieved = nodes * bpn / per_launch / 1e9
 
     # e2e through the C ABI with host buffers: H2D of the fields from pinned
-    # memory, `steps` steps, D2H of the moments, all inside the timed region
+    # memory, `steps` steps, D2H of the moments, all inside the timed region;
+    # median of args.e2e_reps repetitions (the handle's staging is allocated
+    # at create, so no repetition allocates)
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in fields]
     out = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in range(4)]
     e2e_steps = args.steps
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    lbm.lbm_init(g.h, *[t.numpy() for t in pinned])
-    g.step(e2e_steps)
-    rc = lbm.load().lbm_moments(g.h, *[lbm._dp(t.numpy()) for t in out])
-    if rc != 0:
-        raise lbm.LbmError(rc, lbm.lbm_last_error(g.h))
-    e2e_t = reduce_max(time.perf_counter() - t0, dist, "cuda")
+    e2e_times = []
+    for _ in range(max(1, args.e2e_reps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lbm.lbm_init(g.h, *[t.numpy() for t in pinned])
+        g.step(e2e_steps)
+        rc = lbm.load().lbm_moments(g.h, *[lbm._dp(t.numpy()) for t in out])
+        if rc != 0:
+            raise lbm.LbmError(rc, lbm.lbm_last_error(g.h))
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_t = reduce_max(statistics.median(e2e_times), dist, "cuda")
     e2e_value = job_value(world, nodes, e2e_steps, e2e_t)
+    io_bytes = 2 * 4 * nodes * 8  # four FP64 fields in, four out
+    e2e_io_s = max(e2e_t - e2e_steps * per_launch, 1e-12)
 
     variants = {}
     cavity = inputs.cavity(n=n, Ra=1e5, dT_over_T0=0.3, seed=3)[0]
@@ -512,7 +536,13 @@ def run_ours(args, rank, world, local_rank):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(4 * nodes * 8 / e2e_steps),
-                    "d2h_bytes_per_step": int(4 * nodes * 8 / e2e_steps)},
+                    "d2h_bytes_per_step": int(4 * nodes * 8 / e2e_steps),
+                    "reps": len(e2e_times), "seconds_median": e2e_t,
+                    "seconds_all": e2e_times,
+                    "transfer_gbs": io_bytes / e2e_io_s / 1e9,
+                    "transfer_note": "host<->device bytes (fields in, moments out) / (e2e time "
+                                     "- steps x device step time); includes the init and "
+                                     "export kernels"},
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
             "variants": variants,
@@ -545,6 +575,7 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--batch-err-grids", type=int, default=4)
     ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--e2e-reps", type=int, default=3)
     ap.add_argument("--config3-steps", type=int, default=0,
                     help="run the large-dT cavity precision study for this many steps")
     args = ap.parse_args()

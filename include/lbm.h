@@ -173,11 +173,15 @@ int64_t lbm_state_bytes(const lbm_params* p);
 
 /* Validates *p, allocates the device state and creates a handle bound to the
  * current CUDA device and to cuda_stream (a cudaStream_t; NULL = default).
+ * Also allocates the staging of host transfers (4 nx ny doubles), so that
+ * lbm_init() and lbm_moments() allocate nothing (lbm_get_state() and
+ * lbm_set_state() grow it to 18 nx ny doubles on first use).
  * On error *out is NULL.  Errors: LBM_ERR_PARAM (see lbm_params), LBM_ERR_OOM,
  * LBM_ERR_CUDA. */
 int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out);
 
 /* Same as lbm_create() but places the state in caller-owned device memory
+ * (the staging of host transfers is still the library's own)
  * (for example a buffer from a caching allocator): device_buffer must be
  * 256-byte aligned and at least lbm_state_bytes(p) long.  Layout (opaque to
  * callers): two buffers, each 18 planes per row, row-interleaved
@@ -205,7 +209,8 @@ int lbm_step(lbm_handle* h, int64_t n);
  * (Eq. 35 and text under Eq. 51) and T (Eq. 37, or 2 sum hbar/(rho b R)),
  * computed in FP64 from the stored populations.  Host outputs, nx*ny each;
  * synchronous.  LBM_ERR_NONFINITE if any value is NaN/Inf (arrays still
- * filled). */
+ * filled; the export kernel raises a device flag, the host scans nothing).
+ * LBM_ERR_STATE before lbm_init() or after a lost state (lbm_sync()). */
 int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy, double* T);
 
 /* Same as lbm_moments() into device arrays, asynchronous, no finite check. */
@@ -245,7 +250,11 @@ int lbm_set_state(lbm_handle* h, const double* pops);
  * grids needing more partial slots are rejected with LBM_ERR_PARAM (with the
  * library's node limit of 2^31 none does).  The first call on a device looks
  * the array up on that device (make it, with that device current, before any
- * stream capture).  All calls share the array: calls that overlap on the GPU
+ * stream capture); every later call outside stream capture looks it up again
+ * (a host-side lookup that allocates nothing), so that a context recreated
+ * after cudaDeviceReset() is followed, and calls inside a capture use the
+ * address of the last call outside one (after a device reset, make one call
+ * outside capture first again).  All calls share the array: calls that overlap on the GPU
  * (different streams, or devices sharing nothing but the host thread's
  * current device) race and must be ordered by the caller.  Returns
  * LBM_ERR_PARAM for invalid arguments, LBM_ERR_CUDA if the lookup or a launch
@@ -314,7 +323,14 @@ void lbm_batch_destroy(lbm_batch* b); /* NULL-safe */
 const char* lbm_batch_last_error(const lbm_batch* b);
 
 /* Waits for all work enqueued on the handle's stream; reports a pending
- * kernel error as LBM_ERR_CUDA. */
+ * kernel error as LBM_ERR_CUDA.  LBM_ERR_TIMEOUT if a step kernel gave up a
+ * bounded wait for a staged row (2 s; the handle stays usable).  If such a
+ * kernel also ran out of time draining its own copies, a copy may have landed
+ * in shared memory after it left: the state is then treated as lost, and
+ * lbm_step(), lbm_moments(), lbm_conserved() and lbm_get_state() return
+ * LBM_ERR_STATE until lbm_init(), lbm_init_device() or lbm_set_state()
+ * reloads it.  (A batch in that case refuses further runs and reads until it
+ * is destroyed.) */
 int lbm_sync(lbm_handle* h);
 
 /* Time steps taken since the last lbm_init() / lbm_set_state(). */

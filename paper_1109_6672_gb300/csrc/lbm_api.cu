@@ -30,6 +30,7 @@ struct lbm_handle {
   int cur = 0;  // buffer holding the state at the current time
   int64_t steps = 0;
   bool ready = false;
+  bool lost = false;  // a step kernel left with copies in flight: reload the state
   Grid grid{};
   int variant = TMA_PR_1, rows = 0;  // 1, 2: pulled-row TMA kernel; 64..256: register pull
   int auto_rows = 0;                 // rows chosen for (variant, rows = 0); 0: not yet
@@ -38,6 +39,7 @@ struct lbm_handle {
   double* partial = nullptr;  // reduction scratch: RED_BLOCKS x 4
   double* out4 = nullptr;     // reduction result
   int* status = nullptr;      // device error word of the step kernels
+  int* nonfinite = nullptr;   // device flag of export_kernel (lbm_moments)
   double* staging = nullptr;  // device staging for host transfers
   size_t staging_bytes = 0;
   std::string err;
@@ -422,7 +424,18 @@ int create_impl(const lbm_params* p, void* stream, void* ext, int64_t ext_bytes,
   }
   h->out4 = h->partial + RED_BLOCKS * 4;
   h->status = reinterpret_cast<int*>(h->out4 + 4);
-  cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+  h->nonfinite = h->status + 1;
+  cudaMemsetAsync(h->status, 0, 2 * sizeof(int), h->stream);
+  // staging of the host fields (lbm_init, lbm_moments), allocated here so
+  // that no transfer call allocates
+  rc = ensure_staging(h, 4 * (size_t)p->nx * p->ny * sizeof(double));
+  if (rc != LBM_OK) {
+    cudaGetLastError();
+    if (h->owns) cudaFree(h->base);
+    cudaFree(h->partial);
+    delete h;
+    return fail(nullptr, LBM_ERR_OOM, "cudaMalloc of the host-transfer staging failed");
+  }
   // ghost slots that no rule writes are never read; zero everything once so
   // the buffers hold defined values
   e = cudaMemsetAsync(h->base, 0, need, h->stream);
@@ -541,6 +554,7 @@ int lbm_init_device(lbm_handle* h, const double* rho, const double* ux, const do
   if (e != cudaSuccess) return cuda_fail(h, e, "init kernel launch");
   h->steps = 0;
   h->ready = true;
+  h->lost = false;
   return LBM_OK;
 }
 
@@ -668,6 +682,7 @@ int lbm_step(lbm_handle* h, int64_t n) {
   if (!h) return LBM_ERR_PARAM;
   if (n < 0) return fail(h, LBM_ERR_PARAM, "n must be >= 0");
   if (!h->ready) return fail(h, LBM_ERR_STATE, "lbm_step before lbm_init");
+  if (h->lost) return fail(h, LBM_ERR_STATE, "state lost after a timeout: reload it");
   // long runs of identical launches: replay a captured graph of
   // GRAPH_STEPS steps (it saves the host most of a launch per step)
   while (n >= GRAPH_STEPS && graphable(h)) {
@@ -684,7 +699,7 @@ int lbm_step(lbm_handle* h, int64_t n) {
 }
 
 static int export_impl(lbm_handle* h, double* rho, double* ux, double* uy, double* T,
-                       double* pops) {
+                       double* pops, int* nonfinite = nullptr) {
   const long long n = (long long)h->p.nx * h->p.ny;
   Grid g = h->grid;
   const void* src = buf_ptr(h, h->cur);
@@ -692,7 +707,7 @@ static int export_impl(lbm_handle* h, double* rho, double* ux, double* uy, doubl
   dispatch(h->p.precision, [&](auto* tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
     export_kernel<S><<<grid_blocks(n), 256, 0, h->stream>>>(g, static_cast<const S*>(src), rho,
-                                                             ux, uy, T, T0, pops);
+                                                             ux, uy, T, T0, pops, nonfinite);
     return 0;
   });
   cudaError_t e = cudaGetLastError();
@@ -703,6 +718,7 @@ static int export_impl(lbm_handle* h, double* rho, double* ux, double* uy, doubl
 int lbm_moments_device(lbm_handle* h, double* rho, double* ux, double* uy, double* T) {
   if (!h) return LBM_ERR_PARAM;
   if (!h->ready) return fail(h, LBM_ERR_STATE, "lbm_moments before lbm_init");
+  if (h->lost) return fail(h, LBM_ERR_STATE, "state lost after a timeout: reload it");
   if (!rho || !ux || !uy || !T) return fail(h, LBM_ERR_PARAM, "NULL output pointer");
   return export_impl(h, rho, ux, uy, T, nullptr);
 }
@@ -710,29 +726,35 @@ int lbm_moments_device(lbm_handle* h, double* rho, double* ux, double* uy, doubl
 int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy, double* T) {
   if (!h) return LBM_ERR_PARAM;
   if (!h->ready) return fail(h, LBM_ERR_STATE, "lbm_moments before lbm_init");
+  if (h->lost) return fail(h, LBM_ERR_STATE, "state lost after a timeout: reload it");
   if (!rho || !ux || !uy || !T) return fail(h, LBM_ERR_PARAM, "NULL output pointer");
   const size_t n = (size_t)h->p.nx * h->p.ny;
   int rc = ensure_staging(h, 4 * n * sizeof(double));
   if (rc) return rc;
-  rc = export_impl(h, h->staging, h->staging + n, h->staging + 2 * n, h->staging + 3 * n, nullptr);
+  cudaError_t e = cudaMemsetAsync(h->nonfinite, 0, sizeof(int), h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+  rc = export_impl(h, h->staging, h->staging + n, h->staging + 2 * n, h->staging + 3 * n, nullptr,
+                   h->nonfinite);
   if (rc) return rc;
   double* dst[4] = {rho, ux, uy, T};
   for (int k = 0; k < 4; ++k) {
-    cudaError_t e = cudaMemcpyAsync(dst[k], h->staging + k * n, n * sizeof(double),
-                                    cudaMemcpyDeviceToHost, h->stream);
+    e = cudaMemcpyAsync(dst[k], h->staging + k * n, n * sizeof(double), cudaMemcpyDeviceToHost,
+                        h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "device-to-host copy");
   }
+  int bad = 0;
+  e = cudaMemcpyAsync(&bad, h->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "device-to-host copy");
   rc = lbm_sync(h);
   if (rc) return rc;
-  for (int k = 0; k < 4; ++k)
-    for (size_t i = 0; i < n; ++i)
-      if (!std::isfinite(dst[k][i])) return fail(h, LBM_ERR_NONFINITE, "non-finite moment");
+  if (bad) return fail(h, LBM_ERR_NONFINITE, "non-finite moment");
   return LBM_OK;
 }
 
 int lbm_conserved(lbm_handle* h, double out[4]) {
   if (!h) return LBM_ERR_PARAM;
   if (!h->ready) return fail(h, LBM_ERR_STATE, "lbm_conserved before lbm_init");
+  if (h->lost) return fail(h, LBM_ERR_STATE, "state lost after a timeout: reload it");
   if (!out) return fail(h, LBM_ERR_PARAM, "out is NULL");
   const long long n = (long long)h->p.nx * h->p.ny;
   const int nb = (int)std::min<long long>(RED_BLOCKS, (n + RED_THREADS - 1) / RED_THREADS);
@@ -759,6 +781,7 @@ int lbm_conserved(lbm_handle* h, double out[4]) {
 int lbm_get_state(lbm_handle* h, double* pops) {
   if (!h) return LBM_ERR_PARAM;
   if (!h->ready) return fail(h, LBM_ERR_STATE, "lbm_get_state before lbm_init");
+  if (h->lost) return fail(h, LBM_ERR_STATE, "state lost after a timeout: reload it");
   if (!pops) return fail(h, LBM_ERR_PARAM, "pops is NULL");
   const size_t n = (size_t)h->p.nx * h->p.ny;
   int rc = ensure_staging(h, NPOP * n * sizeof(double));
@@ -793,6 +816,7 @@ int lbm_set_state(lbm_handle* h, const double* pops) {
   if (e != cudaSuccess) return cuda_fail(h, e, "set-state launch");
   h->steps = 0;
   h->ready = true;
+  h->lost = false;
   return lbm_sync(h);
 }
 
@@ -805,6 +829,12 @@ int lbm_sync(lbm_handle* h) {
   if (st != 0) {
     cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
     cudaStreamSynchronize(h->stream);
+    if (st & 2) {
+      h->lost = true;
+      return fail(h, LBM_ERR_TIMEOUT,
+                  "a step kernel gave up waiting for a staged row and left with copies in "
+                  "flight; the state is lost until lbm_init/lbm_set_state reloads it");
+    }
     return fail(h, LBM_ERR_TIMEOUT, "a step kernel gave up waiting for a staged row");
   }
   return LBM_OK;

@@ -45,6 +45,7 @@ struct lbm_batch {
   size_t item_cap = 0;
   BatchCtl* d_ctl = nullptr;
   int* d_status = nullptr;
+  bool lost = false;  // a step left with copies in flight: every state is suspect
   double* staging = nullptr;
   size_t staging_bytes = 0;
   bool items_dirty = true;
@@ -297,6 +298,12 @@ int check_status(lbm_batch* b) {
     return bfail(b, LBM_ERR_CUDA, "status read failed");
   if (st) {
     cudaMemset(b->d_status, 0, sizeof(int));
+    if (st & 2) {
+      b->lost = true;
+      return bfail(b, LBM_ERR_TIMEOUT,
+                   "a batched step gave up waiting for a staged row and left with copies in "
+                   "flight; the batch's states are lost (destroy the batch)");
+    }
     return bfail(b, LBM_ERR_TIMEOUT, "a batched step gave up waiting for a staged row");
   }
   return LBM_OK;
@@ -460,6 +467,7 @@ int lbm_batch_add(lbm_batch* b, const lbm_params* p, const double* rho, const do
 int lbm_batch_run(lbm_batch* b, int64_t k) {
   if (!b) return LBM_ERR_PARAM;
   if (k < 0 || k > BATCH_MAX_SEG) return bfail(b, LBM_ERR_PARAM, "k must be in [0, 4096]");
+  if (b->lost) return bfail(b, LBM_ERR_STATE, "states lost after a timeout: destroy the batch");
   if (k == 0) return LBM_OK;
   int rc;
   if (b->items_dirty && (rc = rebuild_items(b))) return rc;
@@ -501,37 +509,44 @@ int lbm_batch_moments(lbm_batch* b, int32_t slot, double* rho, double* ux, doubl
   if (!b || slot < 0 || slot >= b->max_grids || !b->slots[slot].used)
     return bfail(b, LBM_ERR_PARAM, "no such slot");
   if (!rho || !ux || !uy || !T) return bfail(b, LBM_ERR_PARAM, "NULL output pointer");
+  if (b->lost) return bfail(b, LBM_ERR_STATE, "states lost after a timeout: destroy the batch");
   const lbm_batch::Slot& sl = b->slots[slot];
   const size_t n = (size_t)sl.p.nx * sl.p.ny;
-  int rc = ensure_staging(b, 4 * n * sizeof(double));
+  // the four fields, then the non-finite flag of export_kernel
+  int rc = ensure_staging(b, 4 * n * sizeof(double) + 16);
   if (rc) return rc;
+  int* flag = reinterpret_cast<int*>(b->staging + 4 * n);
   const BatchGrid& bg = b->h_grids[slot];
   Grid g = bg.g;
   const void* cur = bg.buf[sl.steps & 1];
   const double T0 = sl.p.T0;
   const int blocks = (int)std::max<size_t>(1, std::min<size_t>(4096, (n + 255) / 256));
-  cudaError_t e = by_precision(b->precision, [&](auto* tag) {
-    using S = std::remove_pointer_t<decltype(tag)>;
-    export_kernel<S><<<blocks, 256, 0, b->stream>>>(g, static_cast<const S*>(cur), b->staging,
-                                                    b->staging + n, b->staging + 2 * n,
-                                                    b->staging + 3 * n, T0, nullptr);
-    return cudaGetLastError();
-  });
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), b->stream);
+  if (e == cudaSuccess)
+    e = by_precision(b->precision, [&](auto* tag) {
+      using S = std::remove_pointer_t<decltype(tag)>;
+      export_kernel<S><<<blocks, 256, 0, b->stream>>>(g, static_cast<const S*>(cur), b->staging,
+                                                      b->staging + n, b->staging + 2 * n,
+                                                      b->staging + 3 * n, T0, nullptr, flag);
+      return cudaGetLastError();
+    });
   double* dst[4] = {rho, ux, uy, T};
   for (int k = 0; k < 4 && e == cudaSuccess; ++k)
     e = cudaMemcpyAsync(dst[k], b->staging + k * n, n * sizeof(double), cudaMemcpyDeviceToHost,
                         b->stream);
+  int bad = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, "moments failed");
-  for (int k = 0; k < 4; ++k)
-    for (size_t i = 0; i < n; ++i)
-      if (!std::isfinite(dst[k][i])) return bfail(b, LBM_ERR_NONFINITE, "non-finite moment");
+  if (bad) return bfail(b, LBM_ERR_NONFINITE, "non-finite moment");
   return LBM_OK;
 }
 
 int lbm_batch_get_state(lbm_batch* b, int32_t slot, double* pops) {
   if (!b || slot < 0 || slot >= b->max_grids || !b->slots[slot].used || !pops)
     return bfail(b, LBM_ERR_PARAM, "no such slot or NULL output");
+  if (b->lost) return bfail(b, LBM_ERR_STATE, "states lost after a timeout: destroy the batch");
   const lbm_batch::Slot& sl = b->slots[slot];
   const size_t n = (size_t)sl.p.nx * sl.p.ny;
   int rc = ensure_staging(b, NPOP * n * sizeof(double));

@@ -1001,9 +1001,12 @@ __device__ __forceinline__ void moments_fp64(const Grid& g, const double p[NPOP]
 }
 
 // rho, u, T (FP64) and optionally the canonical populations [18][ny][nx].
+// nonfinite (may be NULL): set to 1 when any exported moment is NaN or
+// infinite, so the host need not scan the fields.
 template <class S>
 __global__ void export_kernel(const Grid g, const S* __restrict__ buf, double* rho, double* ux,
-                              double* uy, double* T, double T0, double* pops) {
+                              double* uy, double* T, double T0, double* pops,
+                              int* nonfinite = nullptr) {
   const long long n = (long long)g.nx * g.ny;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -1020,6 +1023,8 @@ __global__ void export_kernel(const Grid g, const S* __restrict__ buf, double* r
       ux[i] = vx;
       uy[i] = vy;
       T[i] = th * T0;
+      if (nonfinite && !(isfinite(r) && isfinite(vx) && isfinite(vy) && isfinite(th * T0)))
+        *nonfinite = 1;
     }
   }
 }

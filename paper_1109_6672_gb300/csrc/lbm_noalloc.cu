@@ -32,11 +32,17 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_partials_ptr[kMaxDevices] = {};
 
-// Device address of the partial-sum array on `dev` (the current device),
-// looked up once per device with that device current.
-cudaError_t partials_on(int dev, double** out) {
+// Device address of the partial-sum array on `dev` (the current device).
+// Looked up with that device current on the first call, and again on every
+// call made outside stream capture (a host-side lookup that allocates
+// nothing), so that a context recreated after cudaDeviceReset() is followed;
+// a call inside a capture uses the address of the last call outside one.
+cudaError_t partials_on(int dev, cudaStream_t st, double** out) {
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_partials_ptr[dev]) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const bool capturing =
+      cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone;
+  if (!capturing || !g_partials_ptr[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
     if (e != cudaSuccess) return e;
@@ -64,12 +70,12 @@ extern "C" int lbm_conserved_noalloc(const lbm_params* p, const void* d_state, d
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   double* partials = nullptr;
-  e = partials_on(dev, &partials);
+  e = partials_on(dev, st, &partials);
   if (e != cudaSuccess) return LBM_ERR_CUDA;
   Grid g;
   lbm_host::fill_grid(p, g);
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   // every slot the final pass reads is written by this call's first pass, so
   // nothing left over from an earlier call is used and nothing needs clearing
   switch (p->precision) {

@@ -309,11 +309,16 @@ __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, c
       }
     }
     if (__syncthreads_or(!ok)) {
-      // a staged row never arrived: record, drain what is in flight, leave
+      // a staged row never arrived: record, drain what is in flight, leave.
+      // Bit 2: the drain itself ran out, so a copy may still land in shared
+      // memory after the block has left; the host then treats the state as
+      // lost until it is reloaded.
       if (helper && hl == 0) {
-        if (g.status) atomicOr(g.status, 1);
+        bool drained = true;
         for (int j = max(k, 0); j < issued; ++j)
-          mbar_wait(bar_s + 8 * ((kbase + j) % D), ((kbase + j) / D) & 1, WAIT_NS / 4);
+          drained = mbar_wait(bar_s + 8 * ((kbase + j) % D), ((kbase + j) / D) & 1,
+                              WAIT_NS / 4) && drained;
+        if (g.status) atomicOr(g.status, drained ? 1 : 3);
       }
       return 1;
     }

@@ -4,7 +4,11 @@ Requests arrive over time (a seeded Poisson stream).  Each request is one
 simulation: a grid, its parameters and initial fields, and a number of time
 steps.  The server keeps the populations of every admitted request resident in
 one device pool (``lbm.Batch``); a request is admitted as soon as a slot and its
-footprint (``lbm_state_bytes``) are free, in arrival order.  The GPU advances
+footprint (``lbm_state_bytes``) are free, in arrival order: a later request
+may pass a waiting one only while that one has waited fewer than
+``max_bypass`` segments, after which nothing is admitted until it fits (so a
+large request waits a bounded number of segments behind smaller ones; 0 gives
+strict first-in-first-out).  The GPU advances
 all admitted grids together in segments of k steps (one graph launch per
 segment, one kernel launch per step covering every grid); between segments
 finished requests are read back (moments) and released and queued requests are
@@ -36,6 +40,7 @@ class Request:
     spec: dict  # arguments of the inputs recipe
     params: dict = field(default=None, repr=False)
     fields: tuple = field(default=None, repr=False)
+    passed: int = field(default=0, repr=False)  # segments waited after a refusal
 
     def materialize(self, precision: int):
         if self.params is None:
@@ -118,8 +123,10 @@ class Server:
     interface (add / run / remaining / moments / remove / info)."""
 
     def __init__(self, batch, precision: int, seg_max: int = 256, seg_min: int = 16,
-                 keep_moments: bool = False, clock=time.perf_counter, sleep=time.sleep):
+                 keep_moments: bool = False, clock=time.perf_counter, sleep=time.sleep,
+                 max_bypass: int = 8):
         self.batch = batch
+        self.max_bypass = max_bypass
         self.precision = precision
         self.seg_max = seg_max
         self.seg_min = seg_min
@@ -131,6 +138,8 @@ class Server:
 
     def run(self, trace):
         pending = sorted(trace, key=lambda r: r.arrival)
+        for r in pending:
+            r.passed = 0
         queue = []
         active = {}  # slot -> (request, admitted time)
         results = []
@@ -141,9 +150,16 @@ class Server:
             while i < len(pending) and pending[i].arrival <= now:
                 queue.append(pending[i])
                 i += 1
-            # admit in arrival order while slots and pool space last
+            # admit in arrival order while slots and pool space last; a
+            # refused request may be passed by later ones only while it has
+            # waited fewer than max_bypass segments (then admission stops at
+            # it until it fits)
             still = []
+            blocked = False
             for r in queue:
+                if blocked:
+                    still.append(r)
+                    continue
                 p, f = r.materialize(self.precision)
                 try:
                     slot = self.batch.add(p, f, r.steps)
@@ -155,6 +171,7 @@ class Server:
                         results.append(Result(r.rid, r.kind, r.nodes, r.steps, r.arrival, t, t,
                                               None, "does not fit the device pool"))
                     else:
+                        blocked = r.passed >= self.max_bypass
                         still.append(r)
                     continue
                 active[slot] = (r, self.clock() - t0)
@@ -169,6 +186,8 @@ class Server:
             k = max(self.seg_min, min(self.seg_max, min(rem.values())))
             self.batch.run(k)
             self.segments += 1
+            for r in queue:  # segments the refused requests have waited through
+                r.passed += 1
             for s, r0 in rem.items():
                 r, _ = active[s]
                 self.node_updates += r.nodes * min(k, r0)

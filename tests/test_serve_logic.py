@@ -138,3 +138,35 @@ def test_request_larger_than_the_pool_fails_alone():
     assert res[1].finished >= res[0].admitted  # tried again after 0 left, then failed
     s = serve.summarize(list(res.values()), srv.wall, srv.node_updates)
     assert s["failed"] == 2
+
+
+
+@pytest.mark.parametrize("max_bypass", [0, 3, 10 ** 9])
+def test_large_request_is_not_passed_without_limit(max_bypass):
+    """A request refused for room waits a bounded number of segments: later,
+    smaller requests pass it at most max_bypass segments running, then
+    admission stops at it until it fits.  Without the bound (10**9) a steady
+    stream of small requests keeps it out until the stream ends."""
+    clock = Clock()
+    small = 33 * 4
+    # room for the 60^2 request beside at most two small channels
+    fb = FakeBatch(slots=8, node_budget=60 * 60 + 2 * small, clock=clock, t_per_update=1e-9)
+    srv = serve.Server(fb, precision=3, seg_max=16, seg_min=16, clock=clock, sleep=clock.sleep,
+                       max_bypass=max_bypass)
+    trace, t = [], 0.0
+    for i in range(300):  # a steady stream of small channels, 3 segments each,
+        # about one arrival per segment, so some are always running
+        trace.append(serve.Request(1 + i, "couette", t, 48, dict(ny=33, nx=4, U=0.05)))
+        t += 5e-6
+    trace.append(serve.Request(0, "cavity", 1e-4 + 1e-9, 32, dict(n=60, Ra=1e4, dT_over_T0=0.1)))
+    res = {r.rid: r for r in srv.run(trace)}
+    assert len(res) == len(trace) and not any(r.error for r in res.values())
+    big = res[0]
+    passed = sum(1 for r in res.values() if r.rid >= 1 and big.arrival < r.arrival
+                 and r.admitted < big.admitted)
+    if max_bypass == 0:
+        assert passed == 0
+    elif max_bypass == 3:
+        assert 0 < passed <= (max_bypass + 1) * 8
+    else:  # unbounded bypass: the big request waits for (nearly) the whole stream
+        assert passed > 250

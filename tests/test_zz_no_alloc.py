@@ -17,7 +17,8 @@ from paper_1109_6672_gb300 import lbm
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision", [lbm.LBM_P_FP64, lbm.LBM_P_FP32, lbm.LBM_P_FP32_BF16])
+@pytest.mark.parametrize("precision", [lbm.LBM_P_FP64, lbm.LBM_P_FP32, lbm.LBM_P_FP32_FP16,
+                                       lbm.LBM_P_FP32_BF16])
 def test_noalloc_matches_lbm_conserved(precision):
     torch = pytest.importorskip("torch")
     p = inputs.base_params(300, 77, tau_f=0.35, tau_h=0.5, precision=precision,
