@@ -1,0 +1,420 @@
+/*
+ * Oracle of the three-dimensional extension: plain, slow, FP64 CPU statement
+ * of one time step of the coupled double-distribution-function thermal
+ * lattice Boltzmann method (Li, Luo, He, Gao & Tao, arXiv:1109.6672) on the
+ * D3Q19 lattice, BGK scheme.  The paper derives the model for D2Q9 and
+ * states (Sec. V) that its formulation extends to 3-D; this file is that
+ * extension written from the paper's own construction:
+ *   - equilibria: Eq. 18a and Eq. 18b with D = 3 (the Hermite expansions of
+ *     Eqs. 13 and 17 discretised on D3Q19, c = 1, R T0 = 1/3);
+ *   - correction term: Eq. 22 with the constraints of Eq. 26 and, as Eq. 28
+ *     is obtained from Eq. 27, a second moment that removes the deviation of
+ *     the third-order moment of f^eq from Eq. 10d:
+ *        sum_a e_ai e_aj C_a = sum_k d/dx_k D_ijk,
+ *        D_ijk = sum_a f^eq_a e_ai e_aj e_ak - rho R T (u_i d_jk + u_j d_ik + u_k d_ij)
+ *     (on D2Q9 this is exactly Eq. 20/28; on D3Q19 the deviation also has
+ *     entries D_iik, i != k, besides the diagonal D_iii).  D is evaluated
+ *     here by summing the lattice, node by node, and differentiated by the
+ *     central differences of Eq. 50 along each axis.  C_a itself is the
+ *     lattice analogue of Eqs. 48-49: an even quadratic polynomial of e_a
+ *     without weights, C_a = sum_ij A_ij (e_ai e_aj - kappa d_ij) with
+ *     kappa = sum_a e_ax^2 / 19 (so sum C = 0), the symmetric A solved from
+ *     the six second-moment conditions (on D2Q9 this construction gives
+ *     Eq. 49 exactly: only the second-order moments of the orthogonal basis
+ *     are non-zero);
+ *   - time discretisation: Eqs. 33-36 (BGK, omega = 2/(2 tau + 1), the sign
+ *     of the C term read as + as in the D2Q9 oracle), or Eq. 38 with the
+ *     internal-energy h^eq = b R T f^eq / 2; moments Eq. 35, Eq. 37.
+ * Every side is periodic (the 3-D statement covers the bulk scheme only).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; only the tests, the smoke check and the benchmark's CPU
+ * baseline do.  It shares no code, header, table or constant with the CUDA
+ * library or with the D2Q9 oracle.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared [-fopenmp].
+ *
+ * State: the canonical pre-collision distributions fbar_a(x,t), hbar_a(x,t),
+ * stored as f[a][(z*ny + y)*nx + x].
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define Q3 19
+
+/* D3Q19 velocities: rest, the six axis directions, the twelve face
+ * diagonals; weights 1/3, 1/18, 1/36. */
+static const int E3[Q3][3] = {
+    {0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+    {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1},
+    {-1, 0, 1}, {0, 1, 1},   {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+static double weight3(int a) {
+  int s = abs(E3[a][0]) + abs(E3[a][1]) + abs(E3[a][2]);
+  return s == 0 ? 1.0 / 3.0 : (s == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+enum { O3_E_TOTAL = 0, O3_E_INTERNAL = 1 };
+
+typedef struct {
+  int32_t nx, ny, nz;
+  int32_t energy_model; /* O3_E_TOTAL (Eq. 36) or O3_E_INTERNAL (Eq. 38 form) */
+  int32_t correction;   /* 1: C_a as above; 0: omitted */
+  int32_t z_full;       /* 1: Z = e.u - u^2/2; 0: Z = e.u */
+  double tau_f, tau_h;  /* continuous-time relaxation times */
+  double R, T0, b;      /* R T0 = 1/3; b degrees of freedom */
+} o3_params;
+
+typedef struct {
+  o3_params p;
+  long n;
+  double *f[Q3], *h[Q3], *fn[Q3], *hn[Q3];
+  double *rho, *ux, *uy, *uz, *theta, *es;
+  double* D; /* 27 per node: the third-moment deviation D_ijk */
+} o3_state;
+
+/* ---- pointwise pieces ---------------------------------------------------- */
+
+/* Eq. 18a with D = 3. */
+void o3_feq(double RT0, double rho, const double u[3], double theta, double out[Q3]) {
+  const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  for (int a = 0; a < Q3; ++a) {
+    double eu = E3[a][0] * u[0] + E3[a][1] * u[1] + E3[a][2] * u[2];
+    double esq = (double)(E3[a][0] * E3[a][0] + E3[a][1] * E3[a][1] + E3[a][2] * E3[a][2]);
+    double t = 1.0 + eu / RT0 +
+               0.5 * ((eu / RT0) * (eu / RT0) - usq / RT0 + (theta - 1.0) * (esq / RT0 - 3.0)) +
+               eu / (2.0 * RT0) * (theta - 1.0) * (esq / RT0 - 3.0 - 2.0);
+    out[a] = rho * weight3(a) * t;
+  }
+}
+
+/* Eq. 18b with D = 3 (p = rho R T = rho RT0 theta). */
+void o3_heq(double RT0, double rho, const double u[3], double theta, double E,
+            const double feq[Q3], double out[Q3]) {
+  const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const double p = rho * RT0 * theta;
+  for (int a = 0; a < Q3; ++a) {
+    double eu = E3[a][0] * u[0] + E3[a][1] * u[1] + E3[a][2] * u[2];
+    double esq = (double)(E3[a][0] * E3[a][0] + E3[a][1] * E3[a][1] + E3[a][2] * E3[a][2]);
+    double br = eu / RT0 + (eu / RT0) * (eu / RT0) - usq / RT0 + 0.5 * theta * (esq / RT0 - 3.0);
+    out[a] = E * feq[a] + weight3(a) * p * br;
+  }
+}
+
+/* Internal-energy form under Eq. 38: h^eq = b R T f^eq / 2. */
+void o3_heq_internal(double RT0, double b, double theta, const double feq[Q3], double out[Q3]) {
+  for (int a = 0; a < Q3; ++a) out[a] = 0.5 * b * RT0 * theta * feq[a];
+}
+
+/* Deviation of the third-order moment of f^eq from Eq. 10d without its
+ * cubic velocity term (which the model neglects): D[9i+3j+k]. */
+void o3_defect(double RT0, double rho, const double u[3], double theta, double D[27]) {
+  double feq[Q3];
+  o3_feq(RT0, rho, u, theta, feq);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k) {
+        double m = 0.0;
+        for (int a = 0; a < Q3; ++a) m += feq[a] * E3[a][i] * E3[a][j] * E3[a][k];
+        double req = rho * RT0 * theta *
+                     (u[i] * (j == k) + u[j] * (i == k) + u[k] * (i == j));
+        D[9 * i + 3 * j + k] = m - req;
+      }
+}
+
+/* Solve the n x n system M x = r in place (Gaussian elimination with
+ * partial pivoting); n <= 6. */
+static void solve(int n, double M[6][6], double r[6], double x[6]) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < n; ++i)
+      if (fabs(M[i][c]) > fabs(M[piv][c])) piv = i;
+    if (piv != c) {
+      for (int j = 0; j < n; ++j) {
+        double t = M[c][j];
+        M[c][j] = M[piv][j];
+        M[piv][j] = t;
+      }
+      double t = r[c];
+      r[c] = r[piv];
+      r[piv] = t;
+    }
+    for (int i = c + 1; i < n; ++i) {
+      double f = M[i][c] / M[c][c];
+      for (int j = c; j < n; ++j) M[i][j] -= f * M[c][j];
+      r[i] -= f * r[c];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = r[i];
+    for (int j = i + 1; j < n; ++j) s -= M[i][j] * x[j];
+    x[i] = s / M[i][i];
+  }
+}
+
+/* The correction term whose second moments are G (G[3i+j], symmetrised):
+ * C_a = sum_ij A_ij (e_ai e_aj - kappa d_ij), zero mass and momentum. */
+void o3_correction(const double G[9], double out[Q3]) {
+  static const int P[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  double kappa = 0.0;
+  for (int a = 0; a < Q3; ++a) kappa += E3[a][0] * E3[a][0];
+  kappa /= Q3;
+  /* basis polynomial m of the unknown A_m at velocity a (off-diagonal
+   * entries appear twice in the double sum) */
+  double phi[6][Q3];
+  for (int m = 0; m < 6; ++m) {
+    int i = P[m][0], j = P[m][1];
+    for (int a = 0; a < Q3; ++a)
+      phi[m][a] = i == j ? E3[a][i] * E3[a][i] - kappa : 2.0 * E3[a][i] * E3[a][j];
+  }
+  double M[6][6], r[6], A[6];
+  for (int row = 0; row < 6; ++row) {
+    int k = P[row][0], l = P[row][1];
+    for (int m = 0; m < 6; ++m) {
+      double s = 0.0;
+      for (int a = 0; a < Q3; ++a) s += E3[a][k] * E3[a][l] * phi[m][a];
+      M[row][m] = s;
+    }
+    r[row] = 0.5 * (G[3 * k + l] + G[3 * l + k]);
+  }
+  solve(6, M, r, A);
+  for (int a = 0; a < Q3; ++a) {
+    double c = 0.0;
+    for (int m = 0; m < 6; ++m) c += A[m] * phi[m][a];
+    out[a] = c;
+  }
+}
+
+/* ---- grid state ------------------------------------------------------------ */
+
+static long idx3(const o3_params* p, int x, int y, int z) {
+  x = (x % p->nx + p->nx) % p->nx;
+  y = (y % p->ny + p->ny) % p->ny;
+  z = (z % p->nz + p->nz) % p->nz;
+  return ((long)z * p->ny + y) * p->nx + x;
+}
+
+o3_state* o3_new(const o3_params* p) {
+  o3_state* s = (o3_state*)calloc(1, sizeof(o3_state));
+  if (!s) return NULL;
+  s->p = *p;
+  s->n = (long)p->nx * p->ny * p->nz;
+  for (int a = 0; a < Q3; ++a) {
+    s->f[a] = (double*)calloc(s->n, sizeof(double));
+    s->h[a] = (double*)calloc(s->n, sizeof(double));
+    s->fn[a] = (double*)calloc(s->n, sizeof(double));
+    s->hn[a] = (double*)calloc(s->n, sizeof(double));
+  }
+  s->rho = (double*)calloc(s->n, sizeof(double));
+  s->ux = (double*)calloc(s->n, sizeof(double));
+  s->uy = (double*)calloc(s->n, sizeof(double));
+  s->uz = (double*)calloc(s->n, sizeof(double));
+  s->theta = (double*)calloc(s->n, sizeof(double));
+  s->es = (double*)calloc(s->n, sizeof(double));
+  s->D = (double*)calloc(27 * s->n, sizeof(double));
+  return s;
+}
+
+void o3_free(o3_state* s) {
+  if (!s) return;
+  for (int a = 0; a < Q3; ++a) {
+    free(s->f[a]);
+    free(s->h[a]);
+    free(s->fn[a]);
+    free(s->hn[a]);
+  }
+  free(s->rho);
+  free(s->ux);
+  free(s->uy);
+  free(s->uz);
+  free(s->theta);
+  free(s->es);
+  free(s->D);
+  free(s);
+}
+
+static void equilibria(const o3_params* p, double rho, const double u[3], double th, double E,
+                       double feq[Q3], double heq[Q3]) {
+  const double RT0 = p->R * p->T0;
+  o3_feq(RT0, rho, u, th, feq);
+  if (p->energy_model == O3_E_TOTAL)
+    o3_heq(RT0, rho, u, th, E, feq, heq);
+  else
+    o3_heq_internal(RT0, p->b, th, feq, heq);
+}
+
+/* Initial state: fbar = f^eq, hbar = h^eq at the given fields (T in units
+ * of T0's temperature scale). */
+void o3_init(o3_state* s, const double* rho, const double* ux, const double* uy,
+             const double* uz, const double* T) {
+  const o3_params* p = &s->p;
+  const double RT0 = p->R * p->T0;
+  for (long i = 0; i < s->n; ++i) {
+    double u[3] = {ux[i], uy[i], uz[i]};
+    double th = T[i] / p->T0;
+    double E = 0.5 * (p->b * RT0 * th + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    double feq[Q3], heq[Q3];
+    equilibria(p, rho[i], u, th, E, feq, heq);
+    for (int a = 0; a < Q3; ++a) {
+      s->f[a][i] = feq[a];
+      s->h[a][i] = heq[a];
+    }
+  }
+}
+
+/* Eq. 35 and Eq. 37 (or the internal-energy temperature under Eq. 38). */
+static void node_moments(const o3_state* s, long i, double* rho, double u[3], double* th,
+                         double* es) {
+  const o3_params* p = &s->p;
+  double r = 0, j[3] = {0, 0, 0}, sh = 0;
+  for (int a = 0; a < Q3; ++a) {
+    r += s->f[a][i];
+    for (int d = 0; d < 3; ++d) j[d] += E3[a][d] * s->f[a][i];
+    sh += s->h[a][i];
+  }
+  for (int d = 0; d < 3; ++d) u[d] = j[d] / r;
+  double T;
+  if (p->energy_model == O3_E_TOTAL)
+    T = 2.0 / (p->b * p->R) * (sh / r - 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+  else
+    T = 2.0 * sh / (r * p->b * p->R);
+  *rho = r;
+  *th = T / p->T0;
+  *es = sh / r;
+}
+
+static void phase1(o3_state* s, int nthreads) {
+  const o3_params* p = &s->p;
+  const double RT0 = p->R * p->T0;
+  (void)nthreads;
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+  for (long i = 0; i < s->n; ++i) {
+    double u[3];
+    node_moments(s, i, &s->rho[i], u, &s->theta[i], &s->es[i]);
+    s->ux[i] = u[0];
+    s->uy[i] = u[1];
+    s->uz[i] = u[2];
+    o3_defect(RT0, s->rho[i], u, s->theta[i], &s->D[27 * i]);
+  }
+}
+
+/* G_ij = sum_k dD_ijk/dx_k by the central differences of Eq. 50. */
+static void node_G(const o3_state* s, int x, int y, int z, double G[9]) {
+  const o3_params* p = &s->p;
+  for (int ij = 0; ij < 9; ++ij) G[ij] = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    int dx = k == 0, dy = k == 1, dz = k == 2;
+    const double* Dp = &s->D[27 * idx3(p, x + dx, y + dy, z + dz)];
+    const double* Dm = &s->D[27 * idx3(p, x - dx, y - dy, z - dz)];
+    for (int ij = 0; ij < 9; ++ij) G[ij] += 0.5 * (Dp[3 * ij + k] - Dm[3 * ij + k]);
+  }
+}
+
+static void phase2(o3_state* s, int nthreads) {
+  const o3_params* p = &s->p;
+  const double RT0 = p->R * p->T0;
+  const double wf = 2.0 / (2.0 * p->tau_f + 1.0);
+  const double wh = 2.0 / (2.0 * p->tau_h + 1.0);
+  (void)nthreads;
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+  for (int z = 0; z < p->nz; ++z)
+    for (int y = 0; y < p->ny; ++y)
+      for (int x = 0; x < p->nx; ++x) {
+        long i = idx3(p, x, y, z);
+        double rho = s->rho[i], th = s->theta[i];
+        double u[3] = {s->ux[i], s->uy[i], s->uz[i]};
+        double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        double C[Q3] = {0};
+        if (p->correction) {
+          double G[9];
+          node_G(s, x, y, z, G);
+          o3_correction(G, C);
+        }
+        double feq[Q3], heq[Q3];
+        equilibria(p, rho, u, th, s->es[i], feq, heq);
+        for (int a = 0; a < Q3; ++a) {
+          double fb = s->f[a][i], hb = s->h[a][i];
+          double fneq = fb - feq[a];
+          /* Eq. 34 (+ (1 - w_f/2) C) */
+          double fs = fb - wf * fneq + (1.0 - 0.5 * wf) * C[a];
+          /* Eq. 36 or Eq. 38 */
+          double hs = hb - wh * (hb - heq[a]);
+          if (p->energy_model == O3_E_TOTAL) {
+            double eu = E3[a][0] * u[0] + E3[a][1] * u[1] + E3[a][2] * u[2];
+            double Z = p->z_full ? eu - 0.5 * usq : eu;
+            hs += (wh - wf) * Z * (fneq + 0.5 * C[a]);
+          }
+          /* streaming to x + e_a (periodic) */
+          long j = idx3(p, x + E3[a][0], y + E3[a][1], z + E3[a][2]);
+          s->fn[a][j] = fs;
+          s->hn[a][j] = hs;
+        }
+      }
+}
+
+void o3_step(o3_state* s, long nsteps, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  for (long t = 0; t < nsteps; ++t) {
+    phase1(s, nthreads);
+    phase2(s, nthreads);
+    for (int a = 0; a < Q3; ++a) {
+      double* tf = s->f[a];
+      s->f[a] = s->fn[a];
+      s->fn[a] = tf;
+      double* th = s->h[a];
+      s->h[a] = s->hn[a];
+      s->hn[a] = th;
+    }
+  }
+}
+
+void o3_moments(const o3_state* s, double* rho, double* ux, double* uy, double* uz,
+                double* T) {
+  for (long i = 0; i < s->n; ++i) {
+    double u[3], th, es;
+    node_moments(s, i, &rho[i], u, &th, &es);
+    ux[i] = u[0];
+    uy[i] = u[1];
+    uz[i] = u[2];
+    T[i] = th * s->p.T0;
+  }
+}
+
+/* Sums of rho, rho u (3) and hbar over the grid. */
+void o3_conserved(const o3_state* s, double out[5]) {
+  for (int k = 0; k < 5; ++k) out[k] = 0.0;
+  for (long i = 0; i < s->n; ++i) {
+    for (int a = 0; a < Q3; ++a) {
+      out[0] += s->f[a][i];
+      for (int d = 0; d < 3; ++d) out[1 + d] += E3[a][d] * s->f[a][i];
+      out[4] += s->h[a][i];
+    }
+  }
+}
+
+/* Populations [38][nz][ny][nx]: f_0..f_18, then h_0..h_18. */
+void o3_get_pops(const o3_state* s, double* out) {
+  for (int a = 0; a < Q3; ++a) {
+    memcpy(out + (long)a * s->n, s->f[a], s->n * sizeof(double));
+    memcpy(out + (long)(Q3 + a) * s->n, s->h[a], s->n * sizeof(double));
+  }
+}
+
+void o3_set_pops(o3_state* s, const double* in) {
+  for (int a = 0; a < Q3; ++a) {
+    memcpy(s->f[a], in + (long)a * s->n, s->n * sizeof(double));
+    memcpy(s->h[a], in + (long)(Q3 + a) * s->n, s->n * sizeof(double));
+  }
+}
+
+/* The lattice as the oracle uses it: e[3a+d] and w[a]. */
+void o3_lattice(int* e, double* w) {
+  for (int a = 0; a < Q3; ++a) {
+    for (int d = 0; d < 3; ++d) e[3 * a + d] = E3[a][d];
+    w[a] = weight3(a);
+  }
+}
+
+int o3_param_size(void) { return (int)sizeof(o3_params); }

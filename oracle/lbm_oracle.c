@@ -8,15 +8,17 @@
  * baseline do.  It shares no code, header, table or constant with the CUDA
  * library: every constant below is written out here from the paper.
  *
- * Parity unpinned, in part: (1) the -u^2/2 part of Z_a in the coupling
- * term of Eq. 36 (the full Z form).  The paper notes that Z_a reduces to
- * e_a.u at the Navier-Stokes level, so no closed form, decay rate or table
- * it fixes depends on that part.  (2) Q of the ghost node across a wall in
- * the Eq. 50 differences (the mirror 2 Q_w - Q, a reading: the paper does
- * not say), whose effect is of the order of Ma^3.  Both are checked only
- * against the independent NumPy restatement.  The other pieces of the step
- * tried so far are caught by a pin the paper or the mathematics fixes when
- * a plausible mistake is planted in them (tests/test_oracle_mutants.py).
+ * Parity unpinned, in part: the -u^2/2 part of Z_a in the coupling term of
+ * Eq. 36 (the full Z form).  The paper notes that Z_a reduces to e_a.u at
+ * the Navier-Stokes level, so no closed form, decay rate or table it fixes
+ * depends on that part; it is checked only against the independent NumPy
+ * restatement.  Q of the ghost node across a wall in the Eq. 50 differences
+ * (the linear ghost 2 Q_w - Q, a reading: the paper does not say) is pinned
+ * by consistency: at the boundary node the difference converges to the
+ * derivative of any smooth field that takes Q_w at the wall
+ * (orc_gradients).  The other pieces of the step tried so far are caught by
+ * a pin the paper or the mathematics fixes when a plausible mistake is
+ * planted in them (tests/test_oracle_mutants.py).
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared [-fopenmp] (no FMA
  * contraction, so every product and sum is rounded as written).
@@ -389,6 +391,13 @@ static double neighbour_Q(const orc_state* s, int x, int y, int side, int comp) 
   return 2.0 * Qw - Q[i];
 }
 
+/* Eq. 50: the central differences dQx/dx, dQy/dy at node (x, y), from the Q
+ * of phase 1 and, across a side, the neighbour_Q stand-ins above. */
+static void node_dQ(const orc_state* s, int x, int y, double* dQx, double* dQy) {
+  *dQx = 0.5 * (neighbour_Q(s, x, y, 1, 0) - neighbour_Q(s, x, y, 0, 0));
+  *dQy = 0.5 * (neighbour_Q(s, x, y, 3, 1) - neighbour_Q(s, x, y, 2, 1));
+}
+
 static void phase1(orc_state* s, int nthreads) {
   const orc_params* p = &s->p;
   (void)nthreads;
@@ -531,8 +540,8 @@ static void phase2(orc_state* s, int nthreads) {
       /* Eq. 50: central differences of Q; Eq. 48-49: C_a. */
       double C[9] = {0};
       if (p->correction) {
-        double dQx = 0.5 * (neighbour_Q(s, x, y, 1, 0) - neighbour_Q(s, x, y, 0, 0));
-        double dQy = 0.5 * (neighbour_Q(s, x, y, 3, 1) - neighbour_Q(s, x, y, 2, 1));
+        double dQx, dQy;
+        node_dQ(s, x, y, &dQx, &dQy);
         orc_correction(dQx, dQy, C);
       }
       /* Force absorbed into C (text under Eq. 51). */
@@ -757,6 +766,18 @@ void orc_set_pops(orc_state* s, const double* in) {
     memcpy(s->f[a], in + (long)a * s->n, sizeof(double) * s->n);
     memcpy(s->h[a], in + (long)(9 + a) * s->n, sizeof(double) * s->n);
   }
+}
+
+/* The Eq. 50 differences of the current state at every node, as phase 2 of
+ * the next step takes them (phase 1 recomputes the moments and Q first):
+ * dqx[y*nx+x] = dQx/dx, dqy[y*nx+x] = dQy/dy.  Does not advance the state. */
+void orc_gradients(orc_state* s, double* dqx, double* dqy) {
+  phase1(s, 1);
+  for (int y = 0; y < s->p.ny; ++y)
+    for (int x = 0; x < s->p.nx; ++x) {
+      long i = (long)y * s->p.nx + x;
+      node_dQ(s, x, y, &dqx[i], &dqy[i]);
+    }
 }
 
 int orc_param_size(void) { return (int)sizeof(orc_params); }

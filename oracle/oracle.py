@@ -107,6 +107,7 @@ def lib() -> ctypes.CDLL:
         _lib.orc_set_time.argtypes = [ctypes.c_void_p, ctypes.c_long]
         _lib.orc_meq.argtypes = [ctypes.c_double] * 4 + [dp]
         _lib.orc_mrt_matrices.argtypes = [dp, dp]
+        _lib.orc_gradients.argtypes = [ctypes.c_void_p, dp, dp]
         assert _lib.orc_param_size() == ctypes.sizeof(OrcParams)
     return _lib
 
@@ -234,6 +235,13 @@ class Oracle:
         out = [np.empty((self.ny, self.nx)) for _ in range(4)]
         lib().orc_moments(self._h, *[_dp(v) for v in out])
         return tuple(out)  # rho, ux, uy, T
+
+    def gradients(self):
+        """dQx/dx and dQy/dy of Eq. 50 at every node of the current state, as
+        the next step's correction term takes them (walls: the ghost Q)."""
+        out = [np.empty((self.ny, self.nx)) for _ in range(2)]
+        lib().orc_gradients(self._h, *[_dp(v) for v in out])
+        return tuple(out)
 
     def conserved(self) -> np.ndarray:
         out = np.zeros(4)

@@ -197,3 +197,36 @@ def cavity_large_dT(Ra: float = 1e5, n: int | None = None, mu_r: float | None = 
                     T_wall=[1.6, 0.4, 1.0, 1.0], precision=precision, mu_law=2,
                     mu_S=110.5 / 600.0, collision=1, s_q=1.5, wall_nee=15 if nee else 0, **kw)
     return p, uniform_fields(n, n, seed=seed, u_amp=noise)
+
+
+# ---- three-dimensional (D3Q19) workloads ------------------------------------
+
+def base_params3d(nx: int, ny: int, nz: int, **kw) -> dict:
+    """Parameters of a 3-D grid (every side periodic): the same physical
+    parameters as base_params, without walls or gravity."""
+    p = dict(nx=int(nx), ny=int(ny), nz=int(nz), tau_f=0.3, tau_h=0.3 / 0.71, R=1.0 / 3.0,
+             T0=1.0, b=3.0, energy_model=E_TOTAL, correction=1, z_full=1, precision=P_FP64)
+    p.update(kw)
+    return p
+
+
+def uniform_fields3d(nx: int, ny: int, nz: int, seed: int, rho0: float = 1.0,
+                     u_amp: float = 0.0, T0: float = 1.0, T_amp: float = 0.0,
+                     rho_amp: float = 0.0):
+    """rho, ux, uy, uz, T as [nz, ny, nx] float64: constant means plus
+    independent uniform noise U(-amp, amp) from numpy's PCG64 seeded with
+    ``seed``.  T_amp is relative to T0."""
+    rng = np.random.default_rng(seed)
+    shape = (nz, ny, nx)
+    rho = rho0 + rho_amp * rng.uniform(-1.0, 1.0, shape) if rho_amp else np.full(shape, rho0)
+    u = [u_amp * rng.uniform(-1.0, 1.0, shape) if u_amp else np.zeros(shape) for _ in range(3)]
+    T = T0 * (1.0 + T_amp * rng.uniform(-1.0, 1.0, shape)) if T_amp else np.full(shape, T0)
+    return (rho, *u, T)
+
+
+def periodic_box3d(n: int = 256, seed: int = 2, precision: int = P_FP32, **kw):
+    """Fully periodic n^3 box, the 3-D counterpart of periodic_box: rho = 1,
+    u ~ U(-1e-3, 1e-3), T = T0 (1 + U(-1e-2, 1e-2)), tau_f = 0.3, Pr = 0.71,
+    b = 3, total-energy model, correction on."""
+    p = base_params3d(n, n, n, precision=precision, **kw)
+    return p, uniform_fields3d(n, n, n, seed=seed, u_amp=1e-3, T_amp=1e-2)

@@ -62,3 +62,81 @@ def test_cavity_matches_table2(Ra, n, precision, chunk, max_steps, tol):
         assert got[k] == pytest.approx(ref[k], rel=tol), (k, got)
     assert abs(got["y_max"] - ref["y_max"]) <= 2 / n, got
     assert abs(got["x_max"] - ref["x_max"]) <= 2 / n, got
+
+
+# ---- grid convergence on the CUDA path ----------------------------------------
+#
+# Ra = 1e4 on H = 64, 128, 256 in diffusive scaling (tau_f = 0.06 held, g
+# from Ra, dT/T0 = 0.2): Mach number ~ 1/H, stratification ~ 1/H^2, so every
+# error of the scheme is of second order in the spacing.  FP64 storage: the
+# rounding drift of FP32 storage over the millions of steps these runs take
+# (a Ra = 1e5, 128/256/512 FP32 attempt needed 5.9 million steps at 512^2)
+# shows in Nu at the level of the differences between the finer grids.
+# Each grid starts from the previous grid's steady fields, interpolated.
+
+def _conv_params(n, Ra=1e4, Pr=0.71, dT=0.2, tau_f=0.06, precision=lbm.LBM_P_FP64):
+    nu = tau_f * inputs.RT0
+    chi = nu / Pr
+    g = Ra * nu * chi / (dT * n ** 3)
+    p = inputs.base_params(n, n, tau_f=tau_f, tau_h=tau_f / Pr, b=5.0, g=g,
+                           energy_model=inputs.E_INTERNAL, precision=precision,
+                           bc=[inputs.WALL_ISOTHERMAL, inputs.WALL_ISOTHERMAL,
+                               inputs.WALL_ADIABATIC, inputs.WALL_ADIABATIC],
+                           T_wall=[1 + dT / 2, 1 - dT / 2, 1.0, 1.0])
+    return p, chi
+
+
+def _refine(a):
+    n = a.shape[0]
+    c = np.arange(2 * n) / 2 - 0.25
+    x = np.arange(n)
+    rows = np.array([np.interp(c, x, r) for r in a])
+    return np.array([np.interp(c, x, col) for col in rows.T]).T
+
+
+def _peak(a):
+    k = int(np.argmax(a))
+    y0, y1, y2 = a[k - 1], a[k], a[k + 1]
+    d = 0.5 * (y0 - y2) / (y0 - 2 * y1 + y2)
+    return y1 - 0.25 * (y0 - y2) * d
+
+
+def _steady_gpu(n, start, chunk, max_steps, tol=1e-7):
+    p, chi = _conv_params(n)
+    fields = inputs.uniform_fields(n, n, seed=1, u_amp=1e-4) if start is None else \
+        tuple(_refine(a) for a in start)
+    g = lbm.Lbm(p).init(*fields)
+    Th, Tl = p["T_wall"][0], p["T_wall"][1]
+    prev, steps = None, 0
+    while steps < max_steps:
+        g.step(chunk)
+        steps += chunk
+        mom = g.moments()
+        T = mom[3]
+        Nu = float(((9 * T[:, n - 1] - T[:, n - 2] - 8 * Tl) / 3).mean() * n / (Th - Tl))
+        if prev is not None and abs(Nu - prev) < tol * Nu:
+            break
+        prev = Nu
+    g.close()
+    rho, ux, uy, T = mom
+    m = n // 2
+    u_mid = 0.5 * (ux[:, m - 1] + ux[:, m])
+    v_mid = 0.5 * (uy[m - 1, :] + uy[m, :])
+    return dict(Nu=Nu, u_max=_peak(u_mid) * n / chi, v_max=_peak(v_mid) * n / chi,
+                steps=steps), mom
+
+
+def test_cavity_grid_convergence_gpu():
+    res, mom = [], None
+    for n, chunk, cap in ((64, 10000, 1000000), (128, 20000, 2000000), (256, 50000, 4000000)):
+        r, mom = _steady_gpu(n, mom, chunk, cap)
+        assert r["steps"] < cap, f"{n}^2 not converged: {r}"
+        res.append(r)
+    print("grid convergence (64, 128, 256):", res)
+    ref = table2()[1e4]
+    for k in ("Nu", "u_max", "v_max"):
+        a, b, c = (r[k] for r in res)
+        order = np.log2(abs(a - b) / abs(b - c))
+        print(k, "order", order, "extrapolated", c + (c - b) / 3, "Table II", ref[k])
+        assert 1.5 <= order <= 2.5, (k, order, res)
+        assert c + (c - b) / 3 == pytest.approx(ref[k], rel=0.02), (k, res)

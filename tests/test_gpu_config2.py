@@ -1,7 +1,8 @@
 """The small-dT cavity at its configured size and step count: 256 x 256,
 dT/T0 = 0.01, Ra = 1e5, Pr = 0.71, noise 1e-4 (seed 1), 50 000 steps, FP64
 and FP32.  The FP64 CUDA path matches the oracle to 1e-12 after all 50 000
-steps (populations, rho and T relative, u relative to the lattice speed);
+steps (populations, rho and T relative, u relative to the lattice speed;
+u relative to its own maximum to 1e-11);
 FP32 stays within the 1e-3 relative T target."""
 import os
 
@@ -28,9 +29,16 @@ def test_small_dT_cavity_full_run():
     assert rel(g64.pops(), o.pops()) <= 1e-12
     rho_o, ux_o, uy_o, T_o = o.moments()
     rho, ux, uy, T = g64.moments()
-    # velocities relative to the lattice speed c = 1 (u is 1e-2 of c here, so
-    # the populations' rounding shows 100x larger relative to max |u|)
-    assert max(np.abs(ux - ux_o).max(), np.abs(uy - uy_o).max()) <= 1e-12
+    # velocities relative to the lattice speed c = 1, and relative to the
+    # flow's own max |u|: u is 8.6e-3 of c here and comes from differences
+    # of populations of order 1, so their rounding shows about 100x larger
+    # in that norm (measured 5.0e-14 of c = 5.8e-12 of max |u| after the
+    # full run); the gate in that norm is therefore 1e-11, not 1e-12
+    du = max(np.abs(ux - ux_o).max(), np.abs(uy - uy_o).max())
+    umax = max(np.abs(ux_o).max(), np.abs(uy_o).max())
+    print(f"u error after {STEPS} steps: {du:.3e} of c, {du / umax:.3e} of max|u| ({umax:.3e})")
+    assert du <= 1e-12
+    assert du / umax <= 1e-11
     assert rel(rho, rho_o) <= 1e-12
     assert rel(T, T_o) <= 1e-12
     g64.close()

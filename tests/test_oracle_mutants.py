@@ -8,16 +8,14 @@ NumPy restatement are left out, so that the mistake is caught by something
 other than a second reading of the same equations.  The unmodified source,
 built the same way, passes the same pins.
 
-Not in the list, because no such pin can see them:
-* the -u^2/2 part of Z_a in the coupling term of Eq. 36.  The paper notes
-  that Z_a reduces to e_a.u at the Navier-Stokes level, so the closed forms,
-  decay rates and tables do not depend on it (its sign flipped passes every
-  pin here);
-* Q of the ghost node across a wall in the central differences of Eq. 50
-  (the mirror 2 Q_w - Q; the paper does not say): zero gradient, or the
-  mirror's sign flipped, passes every pin, the correction term being of the
-  order of Ma^3.
-Both are checked against the NumPy restatement only."""
+Not in the list, because no such pin can see it: the -u^2/2 part of Z_a in
+the coupling term of Eq. 36.  The paper notes that Z_a reduces to e_a.u at
+the Navier-Stokes level, so the closed forms, decay rates and tables do not
+depend on it (its sign flipped passes every pin here); it is checked against
+the NumPy restatement only.  (Q of the ghost node across a wall in Eq. 50,
+which the step's pins cannot see either, is pinned directly: the wall
+difference must converge to the derivative of a smooth field,
+test_oracle_correction.py::test_eq50_wall_ghost_is_consistent.)"""
 import os
 import subprocess
 import sys
@@ -82,6 +80,12 @@ MUTANTS = [
     ("mrt_inverse_sign", "{1. / 9, -1. / 36, -1. / 18, 1. / 6, -1. / 6, 0, 0, 1. / 4, 0},",
      "{1. / 9, -1. / 36, -1. / 18, 1. / 6, -1. / 6, 0, 0, -1. / 4, 0},",
      "Eq. B2: a sign in the inverse transformation"),
+    ("wall_ghost_q_sign", "  return 2.0 * Qw - Q[i];", "  return -(2.0 * Qw - Q[i]);",
+     "Eq. 50 at a wall: the mirror ghost's sign flipped"),
+    ("wall_ghost_q_zero_gradient", "  return 2.0 * Qw - Q[i];", "  (void)Qw;\n  return Q[i];",
+     "Eq. 50 at a wall: zero-gradient ghost"),
+    ("wall_ghost_q_drops_wall_value", "  return 2.0 * Qw - Q[i];", "  (void)Qw;\n  return -Q[i];",
+     "Eq. 50 at a wall: the wall value Q_w of Eq. 48 dropped from the ghost"),
     ("nee_adiabatic_first_order", "thG = fmax((4.0 * th - s->theta[i2]) / 3.0, 0.5 * th);",
      "thG = th;", "adiabatic non-equilibrium wall: zero slope to first order only",
      ["test_oracle_nee.py::test_nee_table1_couette_pr1"]),
