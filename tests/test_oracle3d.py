@@ -229,3 +229,44 @@ def test_sound_wave_needs_the_correction_3d():
         for direction in ("x", "xy"):
             G, _, G_th, _ = sound_run(theta0, direction, correction=0)
             assert abs(G / G_th - 1) > 0.05, (theta0, direction)
+
+
+def test_moments_of_an_equilibrium_state_return_its_fields():
+    """Eq. 35 and Eq. 37 with E = (b R T + u^2)/2: the moments of the initial
+    equilibrium state are the fields it was built from (a uniform flow at
+    |u| = 0.2 shows a kinetic-energy slip as a temperature error of
+    u^2/(b R))."""
+    for model in (inputs.E_TOTAL, inputs.E_INTERNAL):
+        p = inputs.base_params3d(4, 3, 5, b=5.0, energy_model=model)
+        f = inputs.uniform_fields3d(4, 3, 5, seed=6, u_amp=0.2, T_amp=0.2, rho_amp=0.2)
+        m = o3.Oracle3d(p).init(*f).moments()
+        for got, want in zip(m, f):
+            assert np.abs(got - want).max() < 1e-14
+
+
+def test_viscous_heating_of_a_decaying_shear_wave():
+    """Total-energy model: a shear wave u_x = A sin(k z) decays at nu k^2 and
+    its dissipation mu (du_x/dz)^2 heats the gas at twice the wavenumber.  In
+    the isobaric limit (the heating is slow against the acoustic time) the
+    cos(2 k z) mode of T obeys rho c_p dT2/dt = mu A^2 k^2 / 2 - lambda 4 k^2 T2
+    (Eqs. 29c-30 with the viscous work u.Pi), so
+    T2(t) = nu k^2 A0^2 / (2 c_p) (exp(-2 nu k^2 t) - exp(-4 chi k^2 t)) / (4 chi k^2 - 2 nu k^2).
+    This needs the (omega_h - omega_f) Z_a coupling of Eq. 36 when tau_h !=
+    tau_f (Pr = 3 here)."""
+    L, A0, b, tau_f, tau_h = 32, 0.08, 5.0, 0.3, 0.1
+    p = inputs.base_params3d(2, 2, L, tau_f=tau_f, tau_h=tau_h, b=b)
+    k = 2 * math.pi / L
+    z = np.arange(L)[:, None, None] * np.ones((1, 2, 2))
+    o = o3.Oracle3d(p).init(1.0, A0 * np.sin(k * z), 0.0, 0.0, 1.0)
+    nu, chi, cp = tau_f * RT0, tau_h * RT0, (b + 2) / 2 * RT0
+    c2 = np.cos(2 * k * z)
+    t = 0
+    for t_next in (200, 300, 400):
+        o.step(t_next - t)
+        t = t_next
+        T = o.moments()[4]
+        T2 = float((T * c2).sum() / (c2 * c2).sum())
+        a = 4 * k * k * chi
+        want = nu * k * k * A0 ** 2 / (2 * cp) * (math.exp(-2 * nu * k * k * t) -
+                                                    math.exp(-a * t)) / (a - 2 * nu * k * k)
+        assert T2 == pytest.approx(want, rel=0.03), t
