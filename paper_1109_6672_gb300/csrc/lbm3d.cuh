@@ -1,0 +1,480 @@
+// Device side of the three-dimensional extension of the coupled DDF thermal
+// lattice Boltzmann step (arXiv:1109.6672, BGK scheme of Sec. III.C.1
+// carried to D3Q19; the paper states that its formulation extends to 3-D).
+//
+// Equilibria: Eq. 18a / 18b with D = 3 (R T0 = 1/3, c = 1).  Correction
+// term: on D3Q19 the third-order moment of f^eq deviates from Eq. 10d by
+//   D_iii = Q_i   and   D_iik = D_iki = D_kii = Q_k / 6   (i != k),
+// Q = rho u (1 - theta) (the diagonal is Eq. 20; the cross entries come from
+// the missing (1,1,1) velocities), so the argument that gives Eq. 28 from
+// Eq. 27 asks for second moments
+//   G_ii = dQ_i/dx_i + (1/6) sum_{k != i} dQ_k/dx_k,
+//   G_ij = (dQ_j/dx_i + dQ_i/dx_j) / 6   (i != j),
+// with the central differences of Eq. 50 along every axis.  C_a is the
+// even quadratic polynomial of e_a orthogonal to the constants (the D3Q19
+// counterpart of Eq. 49: only second-order moments):
+//   C_a = sum_ij A_ij (e_ai e_aj - kappa d_ij), kappa = 10/19,
+//   A_kk = (G_kk + (4/7) tr G) / 6,  A_ij = G_ij / 8,
+// i.e. C_0 = -(5/21) tr G, C_(+-x) = A_xx - (5/21) tr G,
+// C_(+-1,+-1,0) = A_xx + A_yy - (5/21) tr G +- G_xy / 4 (sign of e_x e_y).
+//
+// State layout (one buffer; two buffers ping-pong): element (a, x, y, z),
+// a = 0..37 (f_0..f_18, h_0..h_18), x in [-1, nx], y in [-1, ny], z in
+// [-1, nz] (a one-node ghost ring) at
+//     ((z + 1) * (ny + 2) + (y + 1)) * 38 * pitch + a * pitch + x + 32,
+// pitch a multiple of 32 and >= nx + 33.  As in 2-D, a buffer holds the
+// post-collision value f*_a(s) at the slot s from which node s + e_a pulls
+// it: the canonical pre-collision state of node x is buf_a(x - e_a), the
+// nodes on the faces write the periodic copies into the ghost slots.
+//
+// Kernel: a block owns a 32 x TY tile of (x, y) and marches along z over
+// its z range.  For each plane it first computes the moments (and Q) of the
+// tile plus a one-node halo ring (wrapped periodically) into a 3-plane ring
+// of Q in shared memory, then collides the plane below, whose own moments
+// the thread kept in registers; its populations are pulled again (L1/L2
+// hits).  Every side is periodic.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm3 {
+
+using lbm::Io;
+
+constexpr int Q19 = 19;
+constexpr int NP3 = 38;
+constexpr int XOFF3 = 32;
+
+// D3Q19: rest, +-x, +-y, +-z, then the face diagonals (+-1,+-1,0),
+// (+-1,0,+-1), (0,+-1,+-1), each velocity followed by its opposite.
+__host__ __device__ constexpr int e3x(int a) {
+  return (a == 1 || a == 7 || a == 9 || a == 11 || a == 13) ? 1
+         : (a == 2 || a == 8 || a == 10 || a == 12 || a == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int e3y(int a) {
+  return (a == 3 || a == 7 || a == 10 || a == 15 || a == 17) ? 1
+         : (a == 4 || a == 8 || a == 9 || a == 16 || a == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int e3z(int a) {
+  return (a == 5 || a == 11 || a == 14 || a == 15 || a == 18) ? 1
+         : (a == 6 || a == 12 || a == 13 || a == 16 || a == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int e3sq(int a) {
+  return e3x(a) * e3x(a) + e3y(a) * e3y(a) + e3z(a) * e3z(a);
+}
+template <class C>
+__host__ __device__ constexpr C w3(int a) {
+  return a == 0 ? C(1) / C(3) : (a <= 6 ? C(1) / C(18) : C(1) / C(36));
+}
+
+enum { M3_TOTAL = 1, M3_ZFULL = 2, M3_CORR = 4 };
+
+template <class C>
+struct Phys3 {
+  C omega_f, omega_h;  // 2 / (2 tau + 1)
+  C kz;                // omega_h - omega_f (Eq. 36)
+  C b6, six_b;         // b / 6, 6 / b
+};
+
+struct Grid3 {
+  void* src;
+  void* dst;
+  int nx, ny, nz, pitch;
+  long long lp, zs;  // line stride (38 pitch) and plane stride ((ny + 2) lp)
+  int energy_model, correction, z_full;
+  Phys3<double> pd;
+  Phys3<float> pf;
+};
+
+template <class C>
+__host__ __device__ __forceinline__ const Phys3<C>& phys3(const Grid3& g) {
+  if constexpr (sizeof(C) == 8)
+    return g.pd;
+  else
+    return g.pf;
+}
+
+__host__ __device__ __forceinline__ long long slot3(const Grid3& g, int a, int x, int y, int z) {
+  return (long long)(z + 1) * g.zs + (long long)(y + 1) * g.lp + (long long)a * g.pitch +
+         (x + XOFF3);
+}
+
+__device__ __forceinline__ int wrap3(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Pull the 38 values of node (x, y, z): d[a] = buf_a(x - e_a).
+template <class S>
+__device__ __forceinline__ void pull3(const Grid3& g, const S* __restrict__ src, int x, int y,
+                                      int z, typename Io<S>::C d[NP3]) {
+  const S* p = src + slot3(g, 0, x, y, z);
+#pragma unroll
+  for (int a = 0; a < NP3; ++a) {
+    const int q = a % Q19;
+    d[a] = Io<S>::to(Io<S>::ld(p + (long long)a * g.pitch - (long long)e3z(q) * g.zs -
+                               (long long)e3y(q) * g.lp - e3x(q)));
+  }
+}
+
+// Eq. 35 and Eq. 37 (or the internal-energy form under Eq. 38): rho, u,
+// theta and the specific energy Es = sum h / rho.
+template <class C, int M>
+__device__ __forceinline__ void moments3(const Grid3& g, const C d[NP3], C& rho, C& ux, C& uy,
+                                         C& uz, C& th, C& es) {
+  const Phys3<C>& k = phys3<C>(g);
+  C sf = d[0], sh = d[Q19];
+  C jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int a = 1; a < Q19; a += 2) {
+    sf += d[a] + d[a + 1];
+    sh += d[Q19 + a] + d[Q19 + a + 1];
+    if (e3x(a)) jx += C(e3x(a)) * (d[a] - d[a + 1]);
+    if (e3y(a)) jy += C(e3y(a)) * (d[a] - d[a + 1]);
+    if (e3z(a)) jz += C(e3z(a)) * (d[a] - d[a + 1]);
+  }
+  rho = sf;
+  const C inv = C(1) / rho;
+  ux = jx * inv;
+  uy = jy * inv;
+  uz = jz * inv;
+  es = sh * inv;
+  if constexpr ((M & M3_TOTAL) != 0)
+    th = k.six_b * (es - C(0.5) * (ux * ux + uy * uy + uz * uz));
+  else
+    th = k.six_b * es;
+}
+
+// f^eq (Eq. 18a, D = 3) and h^eq (Eq. 18b, D = 3, or Es f^eq) per pair of
+// opposite velocities:
+//   axis (e^2 = 1):     f = rho w [1 - 3/2 u^2 + 9/2 eu^2 +- (6 - 3 theta) eu]
+//   diagonal (e^2 = 2): f = rho w [1 - 3/2 u^2 + 9/2 eu^2 + 3/2 (theta - 1)
+//                                  +- (3/2 + 3/2 theta) eu]
+//   h = Es f + w p [+-3 eu + 9 eu^2 - 3 u^2 + (0 axis | 3/2 theta diagonal)]
+// The rest populations are the remainders of sum f^eq = rho and
+// sum h^eq = rho Es (Eqs. 19a/19b make this an identity), Es being the
+// node's own specific energy.
+template <class C, bool TOTAL>
+__device__ __forceinline__ void equilibria3(C rho, C ux, C uy, C uz, C th, C es, C feq[Q19],
+                                            C heq[Q19]) {
+  const C usq = ux * ux + uy * uy + uz * uz;
+  const C A0 = C(1) - C(1.5) * usq;
+  const C lin1 = C(6) - C(3) * th, lin2 = C(1.5) + C(1.5) * th;
+  const C base2 = A0 + C(1.5) * (th - C(1));
+  const C p = rho * th * (C(1) / C(3));
+  const C hu = C(-3) * usq;
+  C sf = 0, sh = 0;
+#pragma unroll
+  for (int a = 1; a < Q19; a += 2) {
+    const C eu = C(e3x(a)) * ux + C(e3y(a)) * uy + C(e3z(a)) * uz;
+    const bool axis = a <= 6;
+    const C w = w3<C>(a);
+    const C even = (axis ? A0 : base2) + C(4.5) * eu * eu;
+    const C odd = (axis ? lin1 : lin2) * eu;
+    feq[a] = rho * w * (even + odd);
+    feq[a + 1] = rho * w * (even - odd);
+    if constexpr (TOTAL) {
+      const C he = hu + C(9) * eu * eu + (axis ? C(0) : C(1.5) * th);
+      const C ho = C(3) * eu;
+      heq[a] = es * feq[a] + w * p * (he + ho);
+      heq[a + 1] = es * feq[a + 1] + w * p * (he - ho);
+    } else {
+      heq[a] = es * feq[a];
+      heq[a + 1] = es * feq[a + 1];
+    }
+    sf += feq[a] + feq[a + 1];
+    sh += heq[a] + heq[a + 1];
+  }
+  feq[0] = rho - sf;
+  heq[0] = rho * es - sh;
+}
+
+// C_a from the gradients dq[k][j] = dQ_j/dx_k (closed form above).
+template <class C>
+__device__ __forceinline__ void correction3(const C dq[3][3], C cc[Q19]) {
+  const C gxx = dq[0][0] + (dq[1][1] + dq[2][2]) * C(1.0 / 6.0);
+  const C gyy = dq[1][1] + (dq[0][0] + dq[2][2]) * C(1.0 / 6.0);
+  const C gzz = dq[2][2] + (dq[0][0] + dq[1][1]) * C(1.0 / 6.0);
+  const C gxy = (dq[0][1] + dq[1][0]) * C(1.0 / 6.0);
+  const C gxz = (dq[0][2] + dq[2][0]) * C(1.0 / 6.0);
+  const C gyz = (dq[1][2] + dq[2][1]) * C(1.0 / 6.0);
+  const C tr = gxx + gyy + gzz;
+  const C c0 = tr * C(-5.0 / 21.0);
+  const C t47 = tr * C(4.0 / 7.0);
+  const C axx = (gxx + t47) * C(1.0 / 6.0), ayy = (gyy + t47) * C(1.0 / 6.0),
+          azz = (gzz + t47) * C(1.0 / 6.0);
+  cc[0] = c0;
+  cc[1] = cc[2] = axx + c0;
+  cc[3] = cc[4] = ayy + c0;
+  cc[5] = cc[6] = azz + c0;
+  const C dxy = axx + ayy + c0, dxz = axx + azz + c0, dyz = ayy + azz + c0;
+  const C oxy = gxy * C(0.25), oxz = gxz * C(0.25), oyz = gyz * C(0.25);
+  cc[7] = cc[8] = dxy + oxy;    // e_x e_y = +1
+  cc[9] = cc[10] = dxy - oxy;   // e_x e_y = -1
+  cc[11] = cc[12] = dxz + oxz;  // e_x e_z = +1
+  cc[13] = cc[14] = dxz - oxz;  // e_x e_z = -1
+  cc[15] = cc[16] = dyz + oyz;  // e_y e_z = +1
+  cc[17] = cc[18] = dyz - oyz;  // e_y e_z = -1
+}
+
+// Store of the 38 post-collision values of node (x, y, z) at its own slots,
+// and for a node on a face the periodic copies into the ghost slots: the
+// node at w = wrap(x + e_a) pulls population a from w - e_a.
+template <class S>
+__device__ __forceinline__ void store3(const Grid3& g, S* __restrict__ dst, int x, int y, int z,
+                                       const typename Io<S>::C v[NP3]) {
+  S* p = dst + slot3(g, 0, x, y, z);
+#pragma unroll
+  for (int a = 0; a < NP3; ++a) p[(long long)a * g.pitch] = Io<S>::from(v[a]);
+  const bool face = x == 0 || y == 0 || z == 0 || x == g.nx - 1 || y == g.ny - 1 || z == g.nz - 1;
+  if (!face) return;
+#pragma unroll
+  for (int q = 1; q < Q19; ++q) {
+    const int dx = x + e3x(q), dy = y + e3y(q), dz = z + e3z(q);
+    if (dx >= 0 && dx < g.nx && dy >= 0 && dy < g.ny && dz >= 0 && dz < g.nz) continue;
+    const int sx = wrap3(dx, g.nx) - e3x(q), sy = wrap3(dy, g.ny) - e3y(q),
+              sz = wrap3(dz, g.nz) - e3z(q);
+    dst[slot3(g, q, sx, sy, sz)] = Io<S>::from(v[q]);
+    dst[slot3(g, Q19 + q, sx, sy, sz)] = Io<S>::from(v[Q19 + q]);
+  }
+}
+
+constexpr int TX3 = 32;
+
+template <class S>
+__host__ __device__ constexpr int ty3() {
+  return 8;
+}
+
+// One time step of every node of the block's tile over z in [z0, z0 + zrows).
+template <class S, int M>
+__global__ void __launch_bounds__(TX3 * 8, (sizeof(S) == 8 ? 1 : 2))
+    step3d_kernel(const Grid3 g, int zrows) {
+  using C = typename Io<S>::C;
+  constexpr int TY = ty3<S>();
+  constexpr int HX = TX3 + 2, HY = TY + 2, HN = HX * HY, NT = TX3 * TY;
+  constexpr int NHALO = HN - NT;
+  static_assert(NHALO <= NT, "one halo cell per thread at most");
+  __shared__ C qs[3][3][HN];  // ring of 3 planes x 3 components of Q
+
+  const int t = threadIdx.x, tx = t % TX3, ty = t / TX3;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int x0 = blockIdx.x * TX3, y0 = blockIdx.y * TY, z0 = blockIdx.z * zrows;
+  if (z0 >= nz) return;
+  const int z1 = min(z0 + zrows, nz);
+  const S* __restrict__ src = static_cast<const S*>(g.src);
+  S* __restrict__ dst = static_cast<S*>(g.dst);
+
+  // this thread's interior cell and node
+  const int cell = (ty + 1) * HX + tx + 1;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool mine = x < nx && y < ny;
+  const int wx = wrap3(x % nx, nx), wy = wrap3(y % ny, ny);  // wrapped (ragged tiles)
+  // halo cell of this thread (t < NHALO): the ring around the tile
+  int hcell = -1, hx = 0, hy = 0;
+  if (t < NHALO) {
+    int cx, cy;
+    if (t < HX) {
+      cx = t;
+      cy = 0;
+    } else if (t < 2 * HX) {
+      cx = t - HX;
+      cy = HY - 1;
+    } else {
+      const int k = t - 2 * HX;  // the side columns, rows 1 .. HY - 2
+      cx = (k & 1) ? HX - 1 : 0;
+      cy = 1 + (k >> 1);
+    }
+    hcell = cy * HX + cx;
+    hx = wrap3(((x0 + cx - 1) % nx + nx) % nx, nx);
+    hy = wrap3(((y0 + cy - 1) % ny + ny) % ny, ny);
+  }
+
+  C prho = 1, pux = 0, puy = 0, puz = 0, pth = 1, pes = 0;
+  for (int r = z0 - 1; r <= z1; ++r) {
+    const int s = (r - z0 + 1) % 3;
+    const int zr = wrap3(r, nz);
+    __syncthreads();  // the previous plane's collision is done with slot s
+    // moments of plane r: this thread's cell (wrapped), and its halo cell
+    C crho, cux, cuy, cuz, cth, ces;
+    {
+      C d[NP3];
+      pull3<S>(g, src, wx, wy, zr, d);
+      moments3<C, M>(g, d, crho, cux, cuy, cuz, cth, ces);
+      const C f = crho * (C(1) - cth);
+      qs[s][0][cell] = f * cux;
+      qs[s][1][cell] = f * cuy;
+      qs[s][2][cell] = f * cuz;
+    }
+    if (hcell >= 0) {
+      C d[NP3], hr, hu, hv, hw, ht, he;
+      pull3<S>(g, src, hx, hy, zr, d);
+      moments3<C, M>(g, d, hr, hu, hv, hw, ht, he);
+      const C f = hr * (C(1) - ht);
+      qs[s][0][hcell] = f * hu;
+      qs[s][1][hcell] = f * hv;
+      qs[s][2][hcell] = f * hw;
+    }
+    __syncthreads();
+    const int zc = r - 1;  // plane to collide
+    if (zc >= z0 && mine) {
+      const int sm = (s + 1) % 3, s0 = (s + 2) % 3;  // planes r - 2 and r - 1
+      C dq[3][3];  // dq[k][j] = dQ_j / dx_k
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        dq[0][j] = C(0.5) * (qs[s0][j][cell + 1] - qs[s0][j][cell - 1]);
+        dq[1][j] = C(0.5) * (qs[s0][j][cell + HX] - qs[s0][j][cell - HX]);
+        dq[2][j] = C(0.5) * (qs[s][j][cell] - qs[sm][j][cell]);
+      }
+      C cc[Q19];
+      if constexpr ((M & M3_CORR) != 0) {
+        correction3<C>(dq, cc);
+      } else {
+#pragma unroll
+        for (int a = 0; a < Q19; ++a) cc[a] = C(0);
+      }
+      C d[NP3];
+      pull3<S>(g, src, x, y, zc, d);
+      C feq[Q19], heq[Q19];
+      equilibria3<C, (M & M3_TOTAL) != 0>(prho, pux, puy, puz, pth, pes, feq, heq);
+      const Phys3<C>& k = phys3<C>(g);
+      const C wf = k.omega_f, wh = k.omega_h, kc = C(1) - C(0.5) * wf;
+      const C zc2 = (M & M3_ZFULL) ? C(0.5) * (pux * pux + puy * puy + puz * puz) : C(0);
+      C v[NP3];
+#pragma unroll
+      for (int a = 0; a < Q19; ++a) {
+        const C fneq = d[a] - feq[a];
+        v[a] = d[a] - wf * fneq + kc * cc[a];  // Eq. 34 with +(1 - w_f/2) C
+        C hs = d[Q19 + a] - wh * (d[Q19 + a] - heq[a]);
+        if constexpr ((M & M3_TOTAL) != 0) {  // Eq. 36
+          const C eu = C(e3x(a)) * pux + C(e3y(a)) * puy + C(e3z(a)) * puz;
+          hs += k.kz * (eu - zc2) * (fneq + C(0.5) * cc[a]);
+        }
+        v[Q19 + a] = hs;
+      }
+      store3<S>(g, dst, x, y, zc, v);
+    }
+    prho = crho;
+    pux = cux;
+    puy = cuy;
+    puz = cuz;
+    pth = cth;
+    pes = ces;
+  }
+}
+
+// ---- initialisation, export, reductions -----------------------------------
+
+// Equilibrium state (FP64) of node i at the given fields, scattered into the
+// slots the next pull reads: buf_a(x - e_a).
+template <class S, bool TOTAL>
+__global__ void init3d_kernel(const Grid3 g, S* buf, const double* __restrict__ rho,
+                              const double* __restrict__ ux, const double* __restrict__ uy,
+                              const double* __restrict__ uz, const double* __restrict__ T,
+                              double invT0) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / g.nx / g.ny);
+    const double th = T[i] * invT0;
+    const double es = TOTAL ? g.pd.b6 * th + 0.5 * (ux[i] * ux[i] + uy[i] * uy[i] + uz[i] * uz[i])
+                            : g.pd.b6 * th;
+    double feq[Q19], heq[Q19];
+    equilibria3<double, TOTAL>(rho[i], ux[i], uy[i], uz[i], th, es, feq, heq);
+    for (int a = 0; a < Q19; ++a) {
+      const long long o = slot3(g, a, x - e3x(a), y - e3y(a), z - e3z(a));
+      buf[o] = Io<S>::from((typename Io<S>::C)feq[a]);
+      buf[o + (long long)Q19 * g.pitch] = Io<S>::from((typename Io<S>::C)heq[a]);
+    }
+  }
+}
+
+// Canonical populations (FP64) of node (x, y, z).
+template <class S>
+__device__ __forceinline__ void pull3_fp64(const Grid3& g, const S* __restrict__ buf, int x,
+                                           int y, int z, double p[NP3]) {
+  for (int a = 0; a < NP3; ++a) {
+    const int q = a % Q19;
+    p[a] = (double)Io<S>::to(buf[slot3(g, a, x - e3x(q), y - e3y(q), z - e3z(q))]);
+  }
+}
+
+// rho, u, T (FP64) and optionally the canonical populations [38][nz][ny][nx];
+// *nonfinite set to 1 if a moment is NaN or infinite.
+template <class S>
+__global__ void export3d_kernel(const Grid3 g, const S* __restrict__ buf, double* rho, double* ux,
+                                double* uy, double* uz, double* T, double T0, double* pops,
+                                int* nonfinite) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / g.nx / g.ny);
+    double p[NP3];
+    pull3_fp64<S>(g, buf, x, y, z, p);
+    if (pops)
+      for (int a = 0; a < NP3; ++a) pops[(long long)a * n + i] = p[a];
+    if (rho) {
+      double r = 0, jx = 0, jy = 0, jz = 0, sh = 0;
+      for (int a = 0; a < Q19; ++a) {
+        r += p[a];
+        jx += e3x(a) * p[a];
+        jy += e3y(a) * p[a];
+        jz += e3z(a) * p[a];
+        sh += p[Q19 + a];
+      }
+      const double vx = jx / r, vy = jy / r, vz = jz / r;
+      const double th = g.energy_model == 0
+                            ? g.pd.six_b * (sh / r - 0.5 * (vx * vx + vy * vy + vz * vz))
+                            : g.pd.six_b * sh / r;
+      rho[i] = r;
+      ux[i] = vx;
+      uy[i] = vy;
+      uz[i] = vz;
+      T[i] = th * T0;
+      if (nonfinite && !(isfinite(r) && isfinite(vx) && isfinite(vy) && isfinite(vz) &&
+                         isfinite(th)))
+        *nonfinite = 1;
+    }
+  }
+}
+
+// Per-block FP64 partial sums of rho, rho u (3) and hbar, fixed order.
+constexpr int RED3 = 256;
+template <class S>
+__global__ void __launch_bounds__(RED3) conserved3d_kernel(const Grid3 g, const S* __restrict__ buf,
+                                                           double* partial) {
+  __shared__ double sm[5][RED3];
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / g.nx / g.ny);
+    double p[NP3];
+    pull3_fp64<S>(g, buf, x, y, z, p);
+    for (int a = 0; a < Q19; ++a) {
+      acc[0] += p[a];
+      acc[1] += e3x(a) * p[a];
+      acc[2] += e3y(a) * p[a];
+      acc[3] += e3z(a) * p[a];
+      acc[4] += p[Q19 + a];
+    }
+  }
+  for (int k = 0; k < 5; ++k) sm[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int s = RED3 / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int k = 0; k < 5; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 5; ++k) partial[5 * blockIdx.x + k] = sm[k][0];
+}
+
+template <int UNUSED = 0>
+__global__ void conserved3d_final_kernel(const double* __restrict__ partial, int nb, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int k = 0; k < 5; ++k) {
+    double s = 0;
+    for (int i = 0; i < nb; ++i) s += partial[5 * i + k];
+    out[k] = s;
+  }
+}
+
+}  // namespace lbm3

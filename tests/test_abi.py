@@ -18,7 +18,8 @@ def declared_functions():
     names = []
     for hdr in sorted((ROOT / "include").glob("*.h")):
         text = re.sub(r"/\*.*?\*/", "", hdr.read_text(), flags=re.S)
-        for m in re.finditer(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(lbm_\w+)\s*\(", text, flags=re.M):
+        for m in re.finditer(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(lbm(?:3d)?_\w+)\s*\(", text,
+                             flags=re.M):
             names.append(m.group(1))
     return sorted(set(names))
 
@@ -33,6 +34,13 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("lbm_create", "lbm_init", "lbm_step", "lbm_moments", "lbm_destroy",
                      "lbm_conserved", "lbm_last_error"):
+        assert required in names
+
+
+def test_header_declares_the_3d_boundary():
+    names = declared_functions()
+    for required in ("lbm3d_create", "lbm3d_init", "lbm3d_step", "lbm3d_moments",
+                     "lbm3d_get_state", "lbm3d_conserved", "lbm3d_destroy", "lbm3d_last_error"):
         assert required in names
 
 
@@ -113,3 +121,36 @@ def test_selftest_wait_validates_without_gpu(lib):
     # out-of-range limits are rejected before any device call
     assert lbm.lbm_selftest_wait(10) == lbm.LBM_ERR_PARAM
     assert lbm.lbm_selftest_wait(3_000_000_000) == lbm.LBM_ERR_PARAM
+
+
+def test_params3d_struct_layout_matches_header(lib, tmp_path):
+    from paper_1109_6672_gb300 import lbm3d
+
+    fields = [f for f, _ in lbm3d.lbm3d_params._fields_]
+    src = tmp_path / "layout3.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "lbm3d.h"\nint main(void) {\n'
+        '  printf("%zu\\n", sizeof(lbm3d_params));\n'
+        + "".join(f'  printf("%zu\\n", offsetof(lbm3d_params, {f}));\n' for f in fields)
+        + "  return 0;\n}\n")
+    exe = tmp_path / "layout3"
+    subprocess.run(["gcc", "-I", str(ROOT / "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(lbm3d.lbm3d_params)
+    assert out[1:] == [getattr(lbm3d.lbm3d_params, f).offset for f in fields]
+
+
+def test_3d_state_bytes_and_validation_without_gpu(lib):
+    from paper_1109_6672_gb300 import lbm3d
+
+    p, _ = inputs.periodic_box3d(n=256, precision=lbm.LBM_P_FP32)
+    n = lbm3d.lbm3d_state_bytes(p)
+    assert n == 2 * 258 * 258 * 38 * 320 * 4
+    assert lbm3d.lbm3d_state_bytes(dict(p, precision=lbm.LBM_P_FP64)) == 2 * n
+    for bad in (dict(p, tau_f=0.0), dict(p, R=1.0), dict(p, b=2.0), dict(p, nz=0),
+                dict(p, precision=lbm.LBM_P_FP32_BF16), dict(p, energy_model=3),
+                dict(p, correction=2), dict(p, nx=2048, ny=2048, nz=1024)):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm3d.lbm3d_state_bytes(bad)
+        assert e.value.status == lbm.LBM_ERR_PARAM
