@@ -491,6 +491,29 @@ def run_ours(args, rank, world, local_rank):
             gv.close()
     else:
         g.close()
+    if args.variants and world == 1 and args.n3d > 0:
+        # the 3-D (D3Q19) extension: periodic n3d^3 box of the same recipe,
+        # 38 populations per node (304 B per node update in FP32, 608 in FP64)
+        from paper_1109_6672_gb300 import lbm3d
+
+        p3, f3 = inputs.periodic_box3d(n=args.n3d)
+        d3 = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in f3]
+        for name, pv in (("d3q19_f32", lbm.LBM_P_FP32), ("d3q19_f64", lbm.LBM_P_FP64)):
+            g3 = lbm3d.Lbm3d(dict(p3, precision=pv), stream=stream.cuda_stream)
+            with torch.cuda.stream(stream):
+                g3.init_device(*[t.data_ptr() for t in d3])
+            g3.step(args.warmup)
+            g3.sync()
+            k3 = max(3, args.steps // (16 if pv == lbm.LBM_P_FP64 else 4))
+            t3 = time_steps(torch, lbm, g3, stream, k3)
+            g3.close()
+            gl = args.n3d ** 3 * k3 / t3 / 1e9
+            bpn3 = lbm3d.BYTES_PER_NODE_UPDATE_3D[pv]
+            variants[name] = {"glups": gl, "bytes_per_node_update": bpn3,
+                              "achieved_gbs": gl * bpn3, "hbm_frac": gl * bpn3 / hbm, "steps": k3,
+                              "workload": f"periodic box {args.n3d}^3, D3Q19, total energy, "
+                                          "correction on"}
+        del d3
 
     extra = {}
     if rank == 0 and world == 1 and args.batch:
@@ -576,6 +599,8 @@ def main():
     ap.add_argument("--batch-err-grids", type=int, default=4)
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--e2e-reps", type=int, default=3)
+    ap.add_argument("--n3d", type=int, default=256,
+                    help="side of the D3Q19 box variant (0: skip it)")
     ap.add_argument("--config3-steps", type=int, default=0,
                     help="run the large-dT cavity precision study for this many steps")
     args = ap.parse_args()
