@@ -31,8 +31,9 @@
 // its z range.  For each plane it first computes the moments (and Q) of the
 // tile plus a one-node halo ring (wrapped periodically) into a 3-plane ring
 // of Q in shared memory, then collides the plane below, whose own moments
-// the thread kept in registers; its populations are pulled again (L1/L2
-// hits).  Every side is periodic.
+// the thread kept in registers and whose pulled populations it parked in
+// shared memory (a per-thread column, two planes deep, so no barrier guards
+// it).  Every side is periodic.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -243,6 +244,14 @@ __host__ __device__ constexpr int ty3() {
   return 8;
 }
 
+// Dynamic shared memory of the step kernel: the parked populations of two
+// planes, [2][38][threads], then the Q ring [3][3][halo tile].
+template <class S>
+__host__ __device__ constexpr size_t step3d_smem() {
+  using C = typename Io<S>::C;
+  return sizeof(C) * ((size_t)2 * NP3 * TX3 * ty3<S>() + 9 * (TX3 + 2) * (ty3<S>() + 2));
+}
+
 // One time step of every node of the block's tile over z in [z0, z0 + zrows).
 template <class S, int M>
 __global__ void __launch_bounds__(TX3 * 8, (sizeof(S) == 8 ? 1 : 2))
@@ -252,7 +261,9 @@ __global__ void __launch_bounds__(TX3 * 8, (sizeof(S) == 8 ? 1 : 2))
   constexpr int HX = TX3 + 2, HY = TY + 2, HN = HX * HY, NT = TX3 * TY;
   constexpr int NHALO = HN - NT;
   static_assert(NHALO <= NT, "one halo cell per thread at most");
-  __shared__ C qs[3][3][HN];  // ring of 3 planes x 3 components of Q
+  extern __shared__ __align__(16) unsigned char smem3[];
+  C* park = reinterpret_cast<C*>(smem3);  // [2][NP3][NT]
+  C(*qs)[3][HN] = reinterpret_cast<C(*)[3][HN]>(park + 2 * NP3 * NT);  // [3][3][HN]
 
   const int t = threadIdx.x, tx = t % TX3, ty = t / TX3;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -297,6 +308,9 @@ __global__ void __launch_bounds__(TX3 * 8, (sizeof(S) == 8 ? 1 : 2))
     {
       C d[NP3];
       pull3<S>(g, src, wx, wy, zr, d);
+      C* pk = park + (r & 1) * NP3 * NT + t;
+#pragma unroll
+      for (int a = 0; a < NP3; ++a) pk[a * NT] = d[a];
       moments3<C, M>(g, d, crho, cux, cuy, cuz, cth, ces);
       const C f = crho * (C(1) - cth);
       qs[s][0][cell] = f * cux;
@@ -331,7 +345,9 @@ __global__ void __launch_bounds__(TX3 * 8, (sizeof(S) == 8 ? 1 : 2))
         for (int a = 0; a < Q19; ++a) cc[a] = C(0);
       }
       C d[NP3];
-      pull3<S>(g, src, x, y, zc, d);
+      const C* pk = park + (zc & 1) * NP3 * NT + t;  // parked by this thread at plane zc
+#pragma unroll
+      for (int a = 0; a < NP3; ++a) d[a] = pk[a * NT];
       C feq[Q19], heq[Q19];
       equilibria3<C, (M & M3_TOTAL) != 0>(prho, pux, puy, puz, pth, pes, feq, heq);
       const Phys3<C>& k = phys3<C>(g);

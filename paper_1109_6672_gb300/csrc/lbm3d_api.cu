@@ -152,6 +152,10 @@ void choose_launch(lbm3d_handle* h) {
                                                       : step3d_attributes_f32(mode, &a);
   int per_sm = h->p.precision == LBM_P_FP64 ? 1 : 2;
   if (e == cudaSuccess && a.numRegs > 0) per_sm = std::max(1, 65536 / (a.numRegs * TX3 * 8));
+  // and by shared memory (the parked populations and the Q ring, plus the
+  // 1 KB the hardware reserves per block, of 228 KB per SM)
+  const size_t smem = h->p.precision == LBM_P_FP64 ? step3d_smem<double>() : step3d_smem<float>();
+  per_sm = std::max(1, std::min(per_sm, (int)(233472 / (smem + 1024))));
   const long long resident = (long long)per_sm * std::max(1, h->num_sms);
   const long long chunks =
       std::max<long long>(1, std::min<long long>(h->p.nz, (4 * resident + tx * ty - 1) / (tx * ty)));

@@ -6,30 +6,38 @@
 
 namespace lbm3 {
 
+template <class S, int M>
+cudaError_t launch_mode3(const Grid3& g, dim3 grid, int zrows, cudaStream_t st) {
+  constexpr int NT = TX3 * ty3<S>();
+  constexpr size_t SM = step3d_smem<S>();
+  static bool attr_set = false;  // per process and instantiation (one device attribute)
+  if (!attr_set) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(step3d_kernel<S, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  step3d_kernel<S, M><<<grid, NT, SM, st>>>(g, zrows);
+  return cudaGetLastError();
+}
+
 template <class S>
 cudaError_t launch_step3d(const Grid3& g, dim3 grid, int zrows, cudaStream_t st) {
-  constexpr int NT = TX3 * ty3<S>();
   switch (mode3_of(g)) {
     case M3_TOTAL | M3_ZFULL | M3_CORR:
-      step3d_kernel<S, M3_TOTAL | M3_ZFULL | M3_CORR><<<grid, NT, 0, st>>>(g, zrows);
-      break;
+      return launch_mode3<S, M3_TOTAL | M3_ZFULL | M3_CORR>(g, grid, zrows, st);
     case M3_TOTAL | M3_ZFULL:
-      step3d_kernel<S, M3_TOTAL | M3_ZFULL><<<grid, NT, 0, st>>>(g, zrows);
-      break;
+      return launch_mode3<S, M3_TOTAL | M3_ZFULL>(g, grid, zrows, st);
     case M3_TOTAL | M3_CORR:
-      step3d_kernel<S, M3_TOTAL | M3_CORR><<<grid, NT, 0, st>>>(g, zrows);
-      break;
+      return launch_mode3<S, M3_TOTAL | M3_CORR>(g, grid, zrows, st);
     case M3_TOTAL:
-      step3d_kernel<S, M3_TOTAL><<<grid, NT, 0, st>>>(g, zrows);
-      break;
+      return launch_mode3<S, M3_TOTAL>(g, grid, zrows, st);
     case M3_CORR:
-      step3d_kernel<S, M3_CORR><<<grid, NT, 0, st>>>(g, zrows);
-      break;
+      return launch_mode3<S, M3_CORR>(g, grid, zrows, st);
     default:
-      step3d_kernel<S, 0><<<grid, NT, 0, st>>>(g, zrows);
-      break;
+      return launch_mode3<S, 0>(g, grid, zrows, st);
   }
-  return cudaGetLastError();
 }
 
 template <class S>
