@@ -546,6 +546,22 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = job_value(world, nodes, e2e_steps, e2e_t)
     io_bytes = 2 * 4 * nodes * 8  # four FP64 fields in, four out
     e2e_io_s = max(e2e_t - e2e_steps * per_launch, 1e-12)
+    # the host link's own copy rate for the same bytes (pinned, one copy per
+    # field each way, torch's copies): what the transfers of the e2e leg
+    # could reach at best
+    dev_tmp = [torch.empty((n, n), dtype=torch.float64, device="cuda") for _ in range(4)]
+    link = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for a, d in zip(pinned, dev_tmp):
+            d.copy_(a, non_blocking=True)
+        for d, o in zip(dev_tmp, out):
+            o.copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+        link.append(time.perf_counter() - t0)
+    link_gbs = io_bytes / statistics.median(link) / 1e9
+    del dev_tmp
 
     variants = {}
     cavity = inputs.cavity(n=n, Ra=1e5, dT_over_T0=0.3, seed=3)[0]
@@ -652,6 +668,7 @@ def run_ours(args, rank, world, local_rank):
                     "reps": len(e2e_times), "seconds_median": e2e_t,
                     "seconds_all": e2e_times,
                     "transfer_gbs": io_bytes / e2e_io_s / 1e9,
+                    "link_copy_gbs": link_gbs,
                     "transfer_note": "host<->device bytes (fields in, moments out) / (e2e time "
                                      "- steps x device step time); includes the init and "
                                      "export kernels"},

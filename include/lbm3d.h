@@ -106,6 +106,12 @@ int lbm3d_sync(lbm3d_handle* h);
 /* Steps taken since the last init. */
 int64_t lbm3d_steps_done(const lbm3d_handle* h);
 
+/* Launch shape of the step kernel (no counterpart in the paper; results do
+ * not depend on it): a block owns 32 x tile_rows nodes of (x, y) and marches
+ * along z.  tile_rows = 8 or 16 (16 for LBM_P_FP32 only), 0 = automatic
+ * (8).  LBM_ERR_PARAM for other values. */
+int lbm3d_set_tile(lbm3d_handle* h, int32_t tile_rows);
+
 /* Frees the device state and the handle; NULL-safe. */
 void lbm3d_destroy(lbm3d_handle* h);
 

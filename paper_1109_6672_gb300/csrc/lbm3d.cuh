@@ -239,25 +239,28 @@ __device__ __forceinline__ void store3(const Grid3& g, S* __restrict__ dst, int 
 
 constexpr int TX3 = 32;
 
-template <class S>
-__host__ __device__ constexpr int ty3() {
-  return 8;
-}
-
-// Dynamic shared memory of the step kernel: the parked populations of two
-// planes, [2][38][threads], then the Q ring [3][3][halo tile].
-template <class S>
+// Dynamic shared memory of the step kernel with tiles of TY rows: the parked
+// populations of two planes, [2][38][threads], then the Q ring
+// [3][3][halo tile].
+template <class S, int TY>
 __host__ __device__ constexpr size_t step3d_smem() {
   using C = typename Io<S>::C;
-  return sizeof(C) * ((size_t)2 * NP3 * TX3 * ty3<S>() + 9 * (TX3 + 2) * (ty3<S>() + 2));
+  return sizeof(C) * ((size_t)2 * NP3 * TX3 * TY + 9 * (TX3 + 2) * (TY + 2));
 }
 
-// One time step of every node of the block's tile over z in [z0, z0 + zrows).
-template <class S, int M>
-__global__ void __launch_bounds__(TX3 * 8, (sizeof(S) == 8 ? 1 : 2))
+// Resident blocks per SM the register budget is sized for: two 256-thread
+// blocks (8-row tiles) or one 512-thread block (16-row tiles); FP64 one.
+template <class S, int TY>
+__host__ __device__ constexpr int step3d_min_blocks() {
+  return (sizeof(S) == 8 || TY == 16) ? 1 : 2;
+}
+
+// One time step of every node of the block's 32 x TY tile over z in
+// [z0, z0 + zrows).
+template <class S, int M, int TY>
+__global__ void __launch_bounds__(TX3 * TY, (step3d_min_blocks<S, TY>()))
     step3d_kernel(const Grid3 g, int zrows) {
   using C = typename Io<S>::C;
-  constexpr int TY = ty3<S>();
   constexpr int HX = TX3 + 2, HY = TY + 2, HN = HX * HY, NT = TX3 * TY;
   constexpr int NHALO = HN - NT;
   static_assert(NHALO <= NT, "one halo cell per thread at most");

@@ -6,56 +6,72 @@
 
 namespace lbm3 {
 
-template <class S, int M>
-cudaError_t launch_mode3(const Grid3& g, dim3 grid, int zrows, cudaStream_t st) {
-  constexpr int NT = TX3 * ty3<S>();
-  constexpr size_t SM = step3d_smem<S>();
+template <class S, int M, int TY>
+cudaError_t launch_tile3(const Grid3& g, dim3 grid, int zrows, cudaStream_t st) {
+  constexpr int NT = TX3 * TY;
+  constexpr size_t SM = step3d_smem<S, TY>();
   static bool attr_set = false;  // per process and instantiation (one device attribute)
   if (!attr_set) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(step3d_kernel<S, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SM);
+    const cudaError_t e = cudaFuncSetAttribute(
+        step3d_kernel<S, M, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  step3d_kernel<S, M><<<grid, NT, SM, st>>>(g, zrows);
+  step3d_kernel<S, M, TY><<<grid, NT, SM, st>>>(g, zrows);
   return cudaGetLastError();
 }
 
+// 16-row tiles exist for FP32 storage only (FP64 parks twice the bytes).
+template <class S, int M>
+cudaError_t launch_mode3(const Grid3& g, dim3 grid, int zrows, int ty, cudaStream_t st) {
+  if constexpr (sizeof(S) == 4) {
+    if (ty == 16) return launch_tile3<S, M, 16>(g, grid, zrows, st);
+  }
+  return launch_tile3<S, M, 8>(g, grid, zrows, st);
+}
+
 template <class S>
-cudaError_t launch_step3d(const Grid3& g, dim3 grid, int zrows, cudaStream_t st) {
+cudaError_t launch_step3d(const Grid3& g, dim3 grid, int zrows, int ty, cudaStream_t st) {
   switch (mode3_of(g)) {
     case M3_TOTAL | M3_ZFULL | M3_CORR:
-      return launch_mode3<S, M3_TOTAL | M3_ZFULL | M3_CORR>(g, grid, zrows, st);
+      return launch_mode3<S, M3_TOTAL | M3_ZFULL | M3_CORR>(g, grid, zrows, ty, st);
     case M3_TOTAL | M3_ZFULL:
-      return launch_mode3<S, M3_TOTAL | M3_ZFULL>(g, grid, zrows, st);
+      return launch_mode3<S, M3_TOTAL | M3_ZFULL>(g, grid, zrows, ty, st);
     case M3_TOTAL | M3_CORR:
-      return launch_mode3<S, M3_TOTAL | M3_CORR>(g, grid, zrows, st);
+      return launch_mode3<S, M3_TOTAL | M3_CORR>(g, grid, zrows, ty, st);
     case M3_TOTAL:
-      return launch_mode3<S, M3_TOTAL>(g, grid, zrows, st);
+      return launch_mode3<S, M3_TOTAL>(g, grid, zrows, ty, st);
     case M3_CORR:
-      return launch_mode3<S, M3_CORR>(g, grid, zrows, st);
+      return launch_mode3<S, M3_CORR>(g, grid, zrows, ty, st);
     default:
-      return launch_mode3<S, 0>(g, grid, zrows, st);
+      return launch_mode3<S, 0>(g, grid, zrows, ty, st);
+  }
+}
+
+template <class S, int TY>
+cudaError_t attributes3d_tile(int mode, cudaFuncAttributes* a) {
+  switch (mode) {
+    case M3_TOTAL | M3_ZFULL | M3_CORR:
+      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_TOTAL | M3_ZFULL | M3_CORR, TY>);
+    case M3_TOTAL | M3_ZFULL:
+      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_TOTAL | M3_ZFULL, TY>);
+    case M3_TOTAL | M3_CORR:
+      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_TOTAL | M3_CORR, TY>);
+    case M3_TOTAL:
+      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_TOTAL, TY>);
+    case M3_CORR:
+      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_CORR, TY>);
+    default:
+      return cudaFuncGetAttributes(a, step3d_kernel<S, 0, TY>);
   }
 }
 
 template <class S>
-cudaError_t attributes3d(int mode, cudaFuncAttributes* a) {
-  switch (mode) {
-    case M3_TOTAL | M3_ZFULL | M3_CORR:
-      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_TOTAL | M3_ZFULL | M3_CORR>);
-    case M3_TOTAL | M3_ZFULL:
-      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_TOTAL | M3_ZFULL>);
-    case M3_TOTAL | M3_CORR:
-      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_TOTAL | M3_CORR>);
-    case M3_TOTAL:
-      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_TOTAL>);
-    case M3_CORR:
-      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_CORR>);
-    default:
-      return cudaFuncGetAttributes(a, step3d_kernel<S, 0>);
+cudaError_t attributes3d(int mode, int ty, cudaFuncAttributes* a) {
+  if constexpr (sizeof(S) == 4) {
+    if (ty == 16) return attributes3d_tile<S, 16>(mode, a);
   }
+  return attributes3d_tile<S, 8>(mode, a);
 }
 
 template <class S>

@@ -19,8 +19,9 @@ inline int mode3_of(const Grid3& g) {
   return m;
 }
 
-cudaError_t launch_step3d_f64(const Grid3& g, dim3 grid, int zrows, cudaStream_t st);
-cudaError_t launch_step3d_f32(const Grid3& g, dim3 grid, int zrows, cudaStream_t st);
+// ty: tile rows, 8 or 16 (16 for FP32 storage only)
+cudaError_t launch_step3d_f64(const Grid3& g, dim3 grid, int zrows, int ty, cudaStream_t st);
+cudaError_t launch_step3d_f32(const Grid3& g, dim3 grid, int zrows, int ty, cudaStream_t st);
 cudaError_t launch_aux3d_f64(int what, const Grid3& g, void* buf, const double* const* in,
                              double* const* out, double T0, double* pops, int* flag,
                              double* partial, int blocks, cudaStream_t st);
@@ -28,8 +29,8 @@ cudaError_t launch_aux3d_f32(int what, const Grid3& g, void* buf, const double* 
                              double* const* out, double T0, double* pops, int* flag,
                              double* partial, int blocks, cudaStream_t st);
 // step kernel attributes (registers, for the resident-block count)
-cudaError_t step3d_attributes_f64(int mode, cudaFuncAttributes* attr);
-cudaError_t step3d_attributes_f32(int mode, cudaFuncAttributes* attr);
+cudaError_t step3d_attributes_f64(int mode, int ty, cudaFuncAttributes* attr);
+cudaError_t step3d_attributes_f32(int mode, int ty, cudaFuncAttributes* attr);
 
 enum { AUX3_INIT = 0, AUX3_EXPORT = 1, AUX3_CONSERVED = 2 };
 

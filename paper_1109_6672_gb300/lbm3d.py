@@ -47,6 +47,7 @@ def load() -> ctypes.CDLL:
             "lbm3d_conserved": (ctypes.c_int, [_H, _DP]),
             "lbm3d_sync": (ctypes.c_int, [_H]),
             "lbm3d_steps_done": (ctypes.c_int64, [_H]),
+            "lbm3d_set_tile": (ctypes.c_int, [_H, ctypes.c_int32]),
             "lbm3d_destroy": (None, [_H]),
             "lbm3d_last_error": (ctypes.c_char_p, [_H]),
         }
@@ -141,6 +142,10 @@ class Lbm3d:
 
     def sync(self):
         _check(load().lbm3d_sync(self.h), self.h)
+        return self
+
+    def set_tile(self, tile_rows: int):
+        _check(load().lbm3d_set_tile(self.h, int(tile_rows)), self.h)
         return self
 
     @property
