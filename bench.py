@@ -430,12 +430,22 @@ def large_dT_study(torch, args):
         hot = (-(9 * T[:, 0] - T[:, 1] - 8 * Th) / 3).mean() * n / (Th - Tl)
         return float(hot), float(cold)
 
-    out = {"grid": f"{n}x{n}", "dT_over_T0": 0.6, "Ra": 1e6, "steps": steps}
+    out = {"grid": f"{n}x{n}", "dT_over_T0": 0.6, "Ra": 1e6, "steps": steps,
+           "note": "bf16 / f16: the TMA step kernel, whose 16-bit T recovery ends in one FP32 "
+                   "subtraction of deviation terms; bf16_fp64_recovery: the register-pull "
+                   "kernel (launch variant 128), which forms rho E in FP64 from the FP32 "
+                   "deviation sums (its other arithmetic also rounds in another order)"}
     ref = None
-    for name, q in (("f64", lbm.LBM_P_FP64), ("f32", lbm.LBM_P_FP32),
-                    ("f16", lbm.LBM_P_FP32_FP16), ("bf16", lbm.LBM_P_FP32_BF16)):
+    mom_bf16 = None
+    dTw = 0.6
+    for name, q, variant in (("f64", lbm.LBM_P_FP64, 0), ("f32", lbm.LBM_P_FP32, 0),
+                             ("f16", lbm.LBM_P_FP32_FP16, 0), ("bf16", lbm.LBM_P_FP32_BF16, 0),
+                             ("bf16_fp64_recovery", lbm.LBM_P_FP32_BF16, 128)):
         p, f = inputs.cavity(n=n, Ra=1e6, dT_over_T0=0.6, seed=3, precision=q)
-        g = lbm.Lbm(p).init(*f)
+        g = lbm.Lbm(p)
+        if variant:
+            g.set_launch(variant)
+        g.init(*f)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g.step(steps)
@@ -454,10 +464,20 @@ def large_dT_study(torch, args):
             rec.update({
                 "T_max_rel": float(np.abs(T - T0_).max() / np.abs(T0_).max()),
                 "T_l2_rel": float(np.sqrt(np.mean((T - T0_) ** 2) / np.mean(T0_ ** 2))),
+                "T_max_over_dT": float(np.abs(T - T0_).max() / dTw),
                 "u_max_over_umax": float(du.max() / umax),
                 "u_l2_over_umax": float(np.sqrt(np.mean(du ** 2)) / umax),
                 "Nu_cold_rel": abs(cold - out["f64"]["Nu_cold"]) / abs(out["f64"]["Nu_cold"]),
             })
+            if name == "bf16":
+                mom_bf16 = mom
+            elif name == "bf16_fp64_recovery" and mom_bf16 is not None:
+                # the two BF16 forms against each other
+                T16 = mom_bf16[3]
+                du16 = np.sqrt((ux - mom_bf16[1]) ** 2 + (uy - mom_bf16[2]) ** 2)
+                rec["vs_bf16_fp32_recovery"] = {
+                    "T_max_over_dT": float(np.abs(T - T16).max() / dTw),
+                    "u_max_over_umax": float(du16.max() / umax)}
         out[name] = rec
     return out
 
@@ -715,8 +735,9 @@ def main():
     ap.add_argument("--e2e-reps", type=int, default=3)
     ap.add_argument("--n3d", type=int, default=256,
                     help="side of the D3Q19 box variant (0: skip it)")
-    ap.add_argument("--config3-steps", type=int, default=0,
-                    help="run the large-dT cavity precision study for this many steps")
+    ap.add_argument("--config3-steps", type=int, default=200000,
+                    help="steps of the large-dT cavity precision study (1024^2, about three "
+                         "minutes at 200 000; 0 skips it)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
