@@ -355,6 +355,17 @@ def batch_and_serving(torch, args):
     for key, prec in (("serving", lbm.LBM_P_FP32_BF16), ("serving_f16", lbm.LBM_P_FP32_FP16),
                       ("serving_f32", lbm.LBM_P_FP32)):
         served(key, prec, trace, desc, factor)
+    if args.config5_sample > 0:
+        # a sample of the configured ranges (sides 32-2048, 1e3-1e5 steps), the
+        # first requests of the configured seeded stream, load 0.7, BF16
+        trace = serve.make_trace(args.config5_sample, seed=5, rate=50.0)
+        factor = serve.load_factor_scale(trace, glups_bf16, load=0.7)
+        serve.scale_arrivals(trace, factor)
+        desc = (f"the first {args.config5_sample} requests of the configured stream: 70 % "
+                "cavity (side 32-2048, dT/T0 0.01-0.6, Ra 1e4-1e6) / 30 % Couette (ny 17-257), "
+                "1e3-1e5 steps, Poisson arrivals (seed 5) time-scaled to 0.7 of the BF16 batched "
+                "throughput")
+        served("serving_config5_sample", lbm.LBM_P_FP32_BF16, trace, desc, factor)
     if args.config5:
         # the configured trace: 500 requests, cavity sides 32-2048, 1e3-1e5
         # steps, Couette ny 17-257, time-scaled to load 0.7
@@ -730,6 +741,9 @@ def main():
                          "to 1e5, load 0.7: about 20 minutes per storage) in these storages, "
                          "comma-separated: bf16, f32")
     ap.add_argument("--serve-pool-gb", type=int, default=24)
+    ap.add_argument("--config5-sample", type=int, default=40,
+                    help="requests of the configured serving stream served by default (about "
+                         "90 s at 40; 0 skips it)")
     ap.add_argument("--batch-err-grids", type=int, default=4)
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--e2e-reps", type=int, default=3)

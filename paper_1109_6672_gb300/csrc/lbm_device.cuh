@@ -214,7 +214,8 @@ __device__ __forceinline__ unsigned sr_hash(const Grid& g, int x, int y) {
 }
 
 // Random words of a node: the linear congruential sequence
-// x -> 1664525 x + 1013904223 (mod 2^32) started at the node's hash h.
+// x -> 1664525 x + 1013904223 (mod 2^32) started at the node's hash h (the
+// 32-bit generator published in Press et al., Numerical Recipes, ch. 7).
 // Word k + 1 rounds stream k: population k (0..17) of the node's own stores;
 // 18 + a / 27 + a: wall values of f_a / h_a that the node writes into ghost
 // slots.  The node's own stores walk the sequence one multiply-add per value;
