@@ -191,7 +191,10 @@ int lbm_create_in(const lbm_params* p, void* cuda_stream, void* device_buffer, i
 
 /* Sets the state to equilibrium (Eq. 18a, Eq. 18b or the Eq. 38 form) at the
  * given host fields (nx*ny doubles each; T in the units of T0; the paper
- * leaves the initial state free).  Resets the step counter.  Synchronous. */
+ * leaves the initial state free).  Resets the step counter.  Synchronous.
+ * The fields travel in row chunks on a transfer stream of the handle while
+ * earlier chunks are initialised on its own stream (pinned host memory lets
+ * the two overlap). */
 int lbm_init(lbm_handle* h, const double* rho, const double* ux, const double* uy,
              const double* T);
 

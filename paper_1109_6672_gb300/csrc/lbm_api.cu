@@ -40,6 +40,11 @@ struct lbm_handle {
   double* out4 = nullptr;     // reduction result
   int* status = nullptr;      // device error word of the step kernels
   int* nonfinite = nullptr;   // device flag of export_kernel (lbm_moments)
+  // host transfers in row chunks: copies on `xfer`, kernels on `stream`,
+  // linked by one event per chunk, so each chunk's kernel overlaps the next
+  // chunk's copies
+  cudaStream_t xfer = nullptr;
+  cudaEvent_t chunk_ev[8] = {};
   double* staging = nullptr;  // device staging for host transfers
   size_t staging_bytes = 0;
   std::string err;
@@ -436,6 +441,13 @@ int create_impl(const lbm_params* p, void* stream, void* ext, int64_t ext_bytes,
     delete h;
     return fail(nullptr, LBM_ERR_OOM, "cudaMalloc of the host-transfer staging failed");
   }
+  e = cudaStreamCreateWithFlags(&h->xfer, cudaStreamNonBlocking);
+  for (int k = 0; k < 8 && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&h->chunk_ev[k], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    lbm_destroy(h);
+    return fail(nullptr, LBM_ERR_CUDA, std::string("transfer stream: ") + cudaGetErrorString(e));
+  }
   // ghost slots that no rule writes are never read; zero everything once so
   // the buffers hold defined values
   e = cudaMemsetAsync(h->base, 0, need, h->stream);
@@ -558,6 +570,18 @@ int lbm_init_device(lbm_handle* h, const double* rho, const double* ux, const do
   return LBM_OK;
 }
 
+namespace {
+
+// Row chunks of the host transfers: [y0, y1) of chunk k of kc.
+constexpr int XFER_CHUNKS = 8;
+void chunk_rows(int ny, int k, int kc, int& y0, int& y1) {
+  const int per = (ny + kc - 1) / kc;
+  y0 = std::min(ny, k * per);
+  y1 = std::min(ny, y0 + per);
+}
+
+}  // namespace
+
 int lbm_init(lbm_handle* h, const double* rho, const double* ux, const double* uy,
              const double* T) {
   if (!h) return LBM_ERR_PARAM;
@@ -565,14 +589,45 @@ int lbm_init(lbm_handle* h, const double* rho, const double* ux, const double* u
   const size_t n = (size_t)h->p.nx * h->p.ny;
   int rc = ensure_staging(h, 4 * n * sizeof(double));
   if (rc) return rc;
+  // row chunks: the four fields' rows of chunk k are copied on the transfer
+  // stream, then chunk k is initialised on the handle's stream while chunk
+  // k + 1 is copied.  The transfer stream first waits for the work already
+  // on the handle's stream (which may still read the staging).
+  cudaError_t e = cudaEventRecord(h->chunk_ev[0], h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->xfer, h->chunk_ev[0], 0);
   const double* src[4] = {rho, ux, uy, T};
-  for (int k = 0; k < 4; ++k) {
-    cudaError_t e = cudaMemcpyAsync(h->staging + k * n, src[k], n * sizeof(double),
-                                    cudaMemcpyHostToDevice, h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy");
+  Grid g = h->grid;
+  void* dst = buf_ptr(h, 0);
+  const double invT0 = 1.0 / h->p.T0;
+  const int kc = std::min(XFER_CHUNKS, h->p.ny);
+  for (int k = 0; k < kc && e == cudaSuccess; ++k) {
+    int y0, y1;
+    chunk_rows(h->p.ny, k, kc, y0, y1);
+    if (y1 <= y0) continue;
+    const long long i0 = (long long)y0 * h->p.nx, i1 = (long long)y1 * h->p.nx;
+    for (int f = 0; f < 4 && e == cudaSuccess; ++f)
+      e = cudaMemcpyAsync(h->staging + f * n + i0, src[f] + i0, (i1 - i0) * sizeof(double),
+                          cudaMemcpyHostToDevice, h->xfer);
+    if (e == cudaSuccess) e = cudaEventRecord(h->chunk_ev[k], h->xfer);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->chunk_ev[k], 0);
+    if (e != cudaSuccess) break;
+    const double* st = h->staging;
+    dispatch(h->p.precision, [&](auto* tag) {
+      using S = std::remove_pointer_t<decltype(tag)>;
+      init_kernel<S><<<grid_blocks(i1 - i0), 256, 0, h->stream>>>(
+          g, static_cast<S*>(dst), st, st + n, st + 2 * n, st + 3 * n, invT0, i0, i1);
+      return 0;
+    });
+    e = cudaGetLastError();
   }
-  rc = lbm_init_device(h, h->staging, h->staging + n, h->staging + 2 * n, h->staging + 3 * n);
-  if (rc) return rc;
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(h->xfer);
+    return cuda_fail(h, e, "host-to-device transfer or init kernel");
+  }
+  h->cur = 0;
+  h->steps = 0;
+  h->ready = true;
+  h->lost = false;
   return lbm_sync(h);
 }
 
@@ -731,20 +786,42 @@ int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy, double* T) {
   const size_t n = (size_t)h->p.nx * h->p.ny;
   int rc = ensure_staging(h, 4 * n * sizeof(double));
   if (rc) return rc;
+  // row chunks: chunk k is exported on the handle's stream (after the steps
+  // enqueued there), then copied to the host on the transfer stream while
+  // chunk k + 1 is exported
   cudaError_t e = cudaMemsetAsync(h->nonfinite, 0, sizeof(int), h->stream);
-  if (e != cudaSuccess) return cuda_fail(h, e, "memset");
-  rc = export_impl(h, h->staging, h->staging + n, h->staging + 2 * n, h->staging + 3 * n, nullptr,
-                   h->nonfinite);
-  if (rc) return rc;
   double* dst[4] = {rho, ux, uy, T};
-  for (int k = 0; k < 4; ++k) {
-    e = cudaMemcpyAsync(dst[k], h->staging + k * n, n * sizeof(double), cudaMemcpyDeviceToHost,
-                        h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "device-to-host copy");
+  Grid g = h->grid;
+  const void* src = buf_ptr(h, h->cur);
+  const double T0 = h->p.T0;
+  const int kc = std::min(XFER_CHUNKS, h->p.ny);
+  for (int k = 0; k < kc && e == cudaSuccess; ++k) {
+    int y0, y1;
+    chunk_rows(h->p.ny, k, kc, y0, y1);
+    if (y1 <= y0) continue;
+    const long long i0 = (long long)y0 * h->p.nx, i1 = (long long)y1 * h->p.nx;
+    double* st = h->staging;
+    int* flag = h->nonfinite;
+    dispatch(h->p.precision, [&](auto* tag) {
+      using S = std::remove_pointer_t<decltype(tag)>;
+      export_kernel<S><<<grid_blocks(i1 - i0), 256, 0, h->stream>>>(
+          g, static_cast<const S*>(src), st, st + n, st + 2 * n, st + 3 * n, T0, nullptr, flag,
+          i0, i1);
+      return 0;
+    });
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(h->chunk_ev[k], h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->xfer, h->chunk_ev[k], 0);
+    for (int f = 0; f < 4 && e == cudaSuccess; ++f)
+      e = cudaMemcpyAsync(dst[f] + i0, h->staging + f * n + i0, (i1 - i0) * sizeof(double),
+                          cudaMemcpyDeviceToHost, h->xfer);
   }
   int bad = 0;
-  e = cudaMemcpyAsync(&bad, h->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-  if (e != cudaSuccess) return cuda_fail(h, e, "device-to-host copy");
+  if (e == cudaSuccess)  // the last chunk's event orders the flag after every export
+    e = cudaMemcpyAsync(&bad, h->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, h->xfer);
+  const cudaError_t es = cudaStreamSynchronize(h->xfer);
+  if (e == cudaSuccess) e = es;
+  if (e != cudaSuccess) return cuda_fail(h, e, "export kernel or device-to-host transfer");
   rc = lbm_sync(h);
   if (rc) return rc;
   if (bad) return fail(h, LBM_ERR_NONFINITE, "non-finite moment");
@@ -871,6 +948,12 @@ void lbm_destroy(lbm_handle* h) {
   drop_step_graphs(h);
   if (h->owns && h->base) cudaFree(h->base);
   if (h->partial) cudaFree(h->partial);
+  if (h->xfer) {
+    cudaStreamSynchronize(h->xfer);
+    cudaStreamDestroy(h->xfer);
+  }
+  for (int k = 0; k < 8; ++k)
+    if (h->chunk_ev[k]) cudaEventDestroy(h->chunk_ev[k]);
   if (h->staging) cudaFree(h->staging);
   delete h;
 }

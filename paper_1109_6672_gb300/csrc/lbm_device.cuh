@@ -944,12 +944,15 @@ __device__ __forceinline__ void init_pops(const Grid& g, double rho, double ux, 
   }
 }
 
+// Nodes [i0, i1) (row-major index; i1 < 0: to the end), so that a caller can
+// initialise a grid chunk by chunk as its fields arrive.
 template <class S>
 __global__ void init_kernel(const Grid g, S* buf, const double* __restrict__ rho,
                             const double* __restrict__ ux, const double* __restrict__ uy,
-                            const double* __restrict__ T, double invT0) {
-  const long long n = (long long)g.nx * g.ny;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+                            const double* __restrict__ T, double invT0, long long i0 = 0,
+                            long long i1 = -1) {
+  const long long n = i1 < 0 ? (long long)g.nx * g.ny : i1;
+  for (long long i = i0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(i % g.nx), y = (int)(i / g.nx);
     double p[NPOP];
@@ -1001,21 +1004,23 @@ __device__ __forceinline__ void moments_fp64(const Grid& g, const double p[NPOP]
     th = g.pd.six_b * sh / r;
 }
 
-// rho, u, T (FP64) and optionally the canonical populations [18][ny][nx].
-// nonfinite (may be NULL): set to 1 when any exported moment is NaN or
-// infinite, so the host need not scan the fields.
+// rho, u, T (FP64) and optionally the canonical populations [18][ny][nx],
+// of nodes [i0, i1) (i1 < 0: to the end).  nonfinite (may be NULL): set to 1
+// when any exported moment is NaN or infinite, so the host need not scan the
+// fields.
 template <class S>
 __global__ void export_kernel(const Grid g, const S* __restrict__ buf, double* rho, double* ux,
                               double* uy, double* T, double T0, double* pops,
-                              int* nonfinite = nullptr) {
-  const long long n = (long long)g.nx * g.ny;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+                              int* nonfinite = nullptr, long long i0 = 0, long long i1 = -1) {
+  const long long nn = (long long)g.nx * g.ny;
+  const long long n = i1 < 0 ? nn : i1;
+  for (long long i = i0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(i % g.nx), y = (int)(i / g.nx);
     double p[NPOP];
     pull_fp64<S>(g, buf, x, y, p);
     if (pops) {
-      for (int a = 0; a < NPOP; ++a) pops[(long long)a * n + i] = p[a];
+      for (int a = 0; a < NPOP; ++a) pops[(long long)a * nn + i] = p[a];
     }
     if (rho) {
       double r, vx, vy, th, sh;
