@@ -25,7 +25,20 @@
  *   - time discretisation: Eqs. 33-36 (BGK, omega = 2/(2 tau + 1), the sign
  *     of the C term read as + as in the D2Q9 oracle), or Eq. 38 with the
  *     internal-energy h^eq = b R T f^eq / 2; moments Eq. 35, Eq. 37.
- * Every side is periodic (the 3-D statement covers the bulk scheme only).
+ * The x and y sides are periodic; each z side is periodic or a halfway wall
+ * (at z = -1/2 and z = nz - 1/2) with the D2Q9 oracle's wall rules carried
+ * to D3Q19: for a population a leaving through the wall, with b its
+ * opposite, f_b(node, t+1) = f*_a - 2 (odd part of f^eq_a at the node's rho
+ * and theta and the wall velocity); h on an isothermal wall by the
+ * equilibrium of a ghost node one spacing outside (u_g = 2 u_w - u,
+ * theta_g = max(2 theta_w - theta, theta_w / 2), rho_g = rho theta /
+ * theta_g) plus the node's own non-equilibrium part, h_b = h^eq_b(ghost) +
+ * (h*_b - h^eq_b)(node); h on an adiabatic wall h_b = h*_a - 2 (odd part of
+ * h^eq_a at (rho, u_w, theta)).  Across a wall the derivative of D in the
+ * correction takes the ghost D_g = 2 D_w - D(node), D_w = D at the node's
+ * rho and the wall's u_w, theta_w (theta of the node on an adiabatic wall):
+ * D is linear in Q = rho u (1 - theta), so this is the D2Q9 oracle's mirror
+ * ghost Q_g = 2 Q_w - Q.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
  * load this file; only the tests, the smoke check and the benchmark's CPU
@@ -57,6 +70,7 @@ static double weight3(int a) {
 }
 
 enum { O3_E_TOTAL = 0, O3_E_INTERNAL = 1 };
+enum { O3_PERIODIC = 0, O3_WALL_ISOTHERMAL = 1, O3_WALL_ADIABATIC = 2 };
 
 typedef struct {
   int32_t nx, ny, nz;
@@ -65,6 +79,9 @@ typedef struct {
   int32_t z_full;       /* 1: Z = e.u - u^2/2; 0: Z = e.u */
   double tau_f, tau_h;  /* continuous-time relaxation times */
   double R, T0, b;      /* R T0 = 1/3; b degrees of freedom */
+  int32_t bc_z[2];      /* sides z- and z+: O3_PERIODIC or a wall */
+  double u_wall_z[2][3];
+  double T_wall_z[2];
 } o3_params;
 
 typedef struct {
@@ -300,15 +317,81 @@ static void phase1(o3_state* s, int nthreads) {
   }
 }
 
-/* G_ij = sum_k dD_ijk/dx_k by the central differences of Eq. 50. */
+/* D of the ghost node across wall side `side` (0: z-, 1: z+) of node i. */
+static void wall_ghost_D(const o3_state* s, long i, int side, double Dg[27]) {
+  const o3_params* p = &s->p;
+  const double RT0 = p->R * p->T0;
+  double thw = p->bc_z[side] == O3_WALL_ISOTHERMAL ? p->T_wall_z[side] / p->T0 : s->theta[i];
+  double Dw[27];
+  o3_defect(RT0, s->rho[i], p->u_wall_z[side], thw, Dw);
+  for (int m = 0; m < 27; ++m) Dg[m] = 2.0 * Dw[m] - s->D[27 * i + m];
+}
+
+/* G_ij = sum_k dD_ijk/dx_k by the central differences of Eq. 50 (the ghost D
+ * across a z wall). */
 static void node_G(const o3_state* s, int x, int y, int z, double G[9]) {
   const o3_params* p = &s->p;
+  const long i = idx3(p, x, y, z);
   for (int ij = 0; ij < 9; ++ij) G[ij] = 0.0;
   for (int k = 0; k < 3; ++k) {
     int dx = k == 0, dy = k == 1, dz = k == 2;
+    double gp[27], gm[27];
     const double* Dp = &s->D[27 * idx3(p, x + dx, y + dy, z + dz)];
     const double* Dm = &s->D[27 * idx3(p, x - dx, y - dy, z - dz)];
+    if (k == 2 && z == p->nz - 1 && p->bc_z[1] != O3_PERIODIC) {
+      wall_ghost_D(s, i, 1, gp);
+      Dp = gp;
+    }
+    if (k == 2 && z == 0 && p->bc_z[0] != O3_PERIODIC) {
+      wall_ghost_D(s, i, 0, gm);
+      Dm = gm;
+    }
     for (int ij = 0; ij < 9; ++ij) G[ij] += 0.5 * (Dp[3 * ij + k] - Dm[3 * ij + k]);
+  }
+}
+
+/* Index of the opposite velocity. */
+static int opp3(int a) {
+  for (int b = 0; b < Q3; ++b)
+    if (E3[b][0] == -E3[a][0] && E3[b][1] == -E3[a][1] && E3[b][2] == -E3[a][2]) return b;
+  return a;
+}
+
+/* Population a leaving node i through a z wall comes back into node i as
+ * the opposite population b (the rules in the header).  fs, hs: the node's
+ * post-collision populations; heq: its h^eq. */
+static void wall_bounce(const o3_params* p, int a, double rho, const double u[3], double th,
+                        const double fs[Q3], const double hs[Q3], const double heq[Q3],
+                        double* fn[Q3], double* hn[Q3], long i) {
+  const double RT0 = p->R * p->T0;
+  const int side = E3[a][2] < 0 ? 0 : 1;
+  const int b = opp3(a);
+  const double* uw = p->u_wall_z[side];
+  /* equilibria at the node's rho and theta and the wall velocity */
+  double fw[Q3], hw[Q3];
+  double Ew = 0.5 * (p->b * RT0 * th + uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2]);
+  o3_feq(RT0, rho, uw, th, fw);
+  if (p->energy_model == O3_E_TOTAL)
+    o3_heq(RT0, rho, uw, th, Ew, fw, hw);
+  else
+    o3_heq_internal(RT0, p->b, th, fw, hw);
+  fn[b][i] = fs[a] + (fw[b] - fw[a]); /* f*_a - 2 (odd part of f^eq_a) */
+  if (p->bc_z[side] == O3_WALL_ISOTHERMAL) {
+    const double thw = p->T_wall_z[side] / p->T0;
+    double thg = 2.0 * thw - th;
+    if (thg < 0.5 * thw) thg = 0.5 * thw;
+    const double rg = rho * th / thg;
+    double ug[3], fg[Q3], hg[Q3];
+    for (int d = 0; d < 3; ++d) ug[d] = 2.0 * uw[d] - u[d];
+    double Eg = 0.5 * (p->b * RT0 * thg + ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2]);
+    o3_feq(RT0, rg, ug, thg, fg);
+    if (p->energy_model == O3_E_TOTAL)
+      o3_heq(RT0, rg, ug, thg, Eg, fg, hg);
+    else
+      o3_heq_internal(RT0, p->b, thg, fg, hg);
+    hn[b][i] = hg[b] + (hs[b] - heq[b]); /* the ghost's equilibrium + the node's h*_b - h^eq_b */
+  } else {
+    hn[b][i] = hs[a] + (hw[b] - hw[a]); /* h*_a - 2 (odd part of h^eq_a) */
   }
 }
 
@@ -332,24 +415,33 @@ static void phase2(o3_state* s, int nthreads) {
           node_G(s, x, y, z, G);
           o3_correction(G, C);
         }
-        double feq[Q3], heq[Q3];
+        double feq[Q3], heq[Q3], fs[Q3], hs[Q3];
         equilibria(p, rho, u, th, s->es[i], feq, heq);
         for (int a = 0; a < Q3; ++a) {
           double fb = s->f[a][i], hb = s->h[a][i];
           double fneq = fb - feq[a];
           /* Eq. 34 (+ (1 - w_f/2) C) */
-          double fs = fb - wf * fneq + (1.0 - 0.5 * wf) * C[a];
+          fs[a] = fb - wf * fneq + (1.0 - 0.5 * wf) * C[a];
           /* Eq. 36 or Eq. 38 */
-          double hs = hb - wh * (hb - heq[a]);
+          hs[a] = hb - wh * (hb - heq[a]);
           if (p->energy_model == O3_E_TOTAL) {
             double eu = E3[a][0] * u[0] + E3[a][1] * u[1] + E3[a][2] * u[2];
             double Z = p->z_full ? eu - 0.5 * usq : eu;
-            hs += (wh - wf) * Z * (fneq + 0.5 * C[a]);
+            hs[a] += (wh - wf) * Z * (fneq + 0.5 * C[a]);
+          }
+        }
+        for (int a = 0; a < Q3; ++a) {
+          const int zt = z + E3[a][2];
+          const int side = zt < 0 ? 0 : (zt >= p->nz ? 1 : -1);
+          if (side >= 0 && p->bc_z[side] != O3_PERIODIC) {
+            /* halfway wall: back into this node as the opposite population */
+            wall_bounce(p, a, rho, u, th, fs, hs, heq, s->fn, s->hn, i);
+            continue;
           }
           /* streaming to x + e_a (periodic) */
-          long j = idx3(p, x + E3[a][0], y + E3[a][1], z + E3[a][2]);
-          s->fn[a][j] = fs;
-          s->hn[a][j] = hs;
+          long j = idx3(p, x + E3[a][0], y + E3[a][1], zt);
+          s->fn[a][j] = fs[a];
+          s->hn[a][j] = hs[a];
         }
       }
 }

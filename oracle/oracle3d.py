@@ -20,6 +20,7 @@ BUILD = HERE / "_build"
 LIB = BUILD / "liblbm3d_oracle.so"
 
 E_TOTAL, E_INTERNAL = 0, 1
+PERIODIC, WALL_ISOTHERMAL, WALL_ADIABATIC = 0, 1, 2
 
 
 class O3Params(ctypes.Structure):
@@ -37,6 +38,9 @@ class O3Params(ctypes.Structure):
         ("R", ctypes.c_double),
         ("T0", ctypes.c_double),
         ("b", ctypes.c_double),
+        ("bc_z", ctypes.c_int32 * 2),
+        ("u_wall_z", (ctypes.c_double * 3) * 2),
+        ("T_wall_z", ctypes.c_double * 2),
     ]
 
 
@@ -103,6 +107,12 @@ def make_params(p: dict) -> O3Params:
     o.z_full = int(p.get("z_full", 1))
     o.tau_f, o.tau_h = float(p["tau_f"]), float(p["tau_h"])
     o.R, o.T0, o.b = float(p["R"]), float(p["T0"]), float(p["b"])
+    for k in range(2):
+        o.bc_z[k] = int(p.get("bc_z", [0, 0])[k])
+        o.T_wall_z[k] = float(p.get("T_wall_z", [1.0, 1.0])[k])
+        uw = p.get("u_wall_z", [[0.0] * 3] * 2)[k]
+        for d in range(3):
+            o.u_wall_z[k][d] = float(uw[d])
     return o
 
 
@@ -153,7 +163,8 @@ def correction(G) -> np.ndarray:
 # ---- whole-grid state ------------------------------------------------------
 
 class Oracle3d:
-    """One 3-D periodic grid advanced by the oracle.  Arrays are [nz, ny, nx]."""
+    """One 3-D grid advanced by the oracle (x, y periodic; z periodic or
+    walled).  Arrays are [nz, ny, nx]."""
 
     def __init__(self, params: dict):
         self.p = dict(params)

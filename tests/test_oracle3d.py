@@ -270,3 +270,58 @@ def test_viscous_heating_of_a_decaying_shear_wave():
         want = nu * k * k * A0 ** 2 / (2 * cp) * (math.exp(-2 * nu * k * k * t) -
                                                     math.exp(-a * t)) / (a - 2 * nu * k * k)
         assert T2 == pytest.approx(want, rel=0.03), t
+
+
+# ---- z walls (halfway, the D2Q9 wall rules carried to D3Q19) ------------------
+
+def _couette3d(H, U, nu, Pr, b, steps):
+    tau_f = nu / RT0
+    p = inputs.base_params3d(2, 2, H, tau_f=tau_f, tau_h=tau_f / Pr, b=b,
+                             bc_z=[o3.WALL_ISOTHERMAL, o3.WALL_ISOTHERMAL],
+                             u_wall_z=[[0.0, 0.0, 0.0], [U, 0.0, 0.0]], T_wall_z=[1.0, 1.0])
+    o = o3.Oracle3d(p).init(*inputs.uniform_fields3d(2, 2, H, seed=0))
+    o.step(steps, threads=4)
+    return o.moments()
+
+
+def test_couette_3d_closed_form():
+    """Flow in x between halfway walls in z (H = nz): u = U (z + 1/2)/H and
+    theta - 1 = Pr U^2 / ((b + 2) R T0) eta (1 - eta) (viscous heating, the
+    closed form of the thermal Couette flow with both walls at T0)."""
+    H, U, nu, Pr, b = 16, 1.0 / 3.0, 0.2, 3.0, 5.0
+    rho, ux, uy, uz, T = _couette3d(H, U, nu, Pr, b, 12000)
+    eta = (np.arange(H) + 0.5) / H
+    # at Ma = 0.49 the compressible flow departs from the linear profile by
+    # 1.9e-3 U (measured); the heating parabola holds to 0.35 %
+    assert np.abs(ux[:, 0, 0] - U * eta).max() < 3e-3 * U
+    assert np.abs(uz).max() < 1e-10 and np.abs(uy).max() < 1e-12
+    rise = Pr * U * U / ((b + 2) * RT0) * eta * (1 - eta)
+    assert np.abs((T[:, 0, 0] - 1) - rise).max() < 0.02 * rise.max()
+
+
+def test_closed_adiabatic_box_conserves_mass_and_energy_3d():
+    p = inputs.base_params3d(5, 4, 6, tau_f=0.35, tau_h=0.5, b=5.0,
+                             bc_z=[o3.WALL_ADIABATIC, o3.WALL_ADIABATIC])
+    f = inputs.uniform_fields3d(5, 4, 6, seed=8, u_amp=0.03, T_amp=0.04, rho_amp=0.02)
+    o = o3.Oracle3d(p).init(*f)
+    c0 = o.conserved()
+    o.step(300)
+    c1 = o.conserved()
+    assert abs(c1[0] - c0[0]) <= 1e-13 * c0[0]  # mass
+    assert abs(c1[4] - c0[4]) <= 1e-13 * c0[4]  # total energy (walls at rest)
+
+
+def test_isothermal_walls_conduct_3d():
+    """No flow, walls at theta 1.05 and 0.95: the steady temperature is the
+    linear conduction profile through the wall values at z = -1/2 and
+    H - 1/2 (to the ghost extrapolation's second order)."""
+    H = 12
+    p = inputs.base_params3d(2, 2, H, tau_f=0.3, tau_h=0.4, b=5.0,
+                             energy_model=inputs.E_INTERNAL,
+                             bc_z=[o3.WALL_ISOTHERMAL, o3.WALL_ISOTHERMAL], T_wall_z=[1.05, 0.95])
+    o = o3.Oracle3d(p).init(*inputs.uniform_fields3d(2, 2, H, seed=0))
+    o.step(20000, threads=4)
+    rho, ux, uy, uz, T = o.moments()
+    eta = (np.arange(H) + 0.5) / H
+    assert np.abs(T[:, 0, 0] - (1.05 - 0.1 * eta)).max() < 1e-3 * 0.1
+    assert max(np.abs(ux).max(), np.abs(uy).max(), np.abs(uz).max()) < 1e-8
