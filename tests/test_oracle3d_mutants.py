@@ -29,7 +29,7 @@ MUTANTS = [
      "Eq. 34: the correction term with the printed minus sign"),
     ("kappa_weighted", "kappa /= Q3;", "kappa = 1.0 / 3.0;",
      "correction: the constant part not making sum C vanish"),
-    ("coupling_reversed", "hs += (wh - wf) * Z", "hs += (wf - wh) * Z",
+    ("coupling_reversed", "hs[a] += (wh - wf) * Z", "hs[a] += (wf - wh) * Z",
      "Eq. 36: (omega_h - omega_f) reversed"),
     ("omega_one_over_tau", "const double wf = 2.0 / (2.0 * p->tau_f + 1.0);",
      "const double wf = 1.0 / p->tau_f;", "below Eq. 34: omega_f = 1 / tau_f"),
