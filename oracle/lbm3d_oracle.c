@@ -34,11 +34,15 @@
  * theta_g = max(2 theta_w - theta, theta_w / 2), rho_g = rho theta /
  * theta_g) plus the node's own non-equilibrium part, h_b = h^eq_b(ghost) +
  * (h*_b - h^eq_b)(node); h on an adiabatic wall h_b = h*_a - 2 (odd part of
- * h^eq_a at (rho, u_w, theta)).  Across a wall the derivative of D in the
- * correction takes the ghost D_g = 2 D_w - D(node), D_w = D at the node's
- * rho and the wall's u_w, theta_w (theta of the node on an adiabatic wall):
- * D is linear in Q = rho u (1 - theta), so this is the D2Q9 oracle's mirror
- * ghost Q_g = 2 Q_w - Q.
+ * h^eq_a at (rho, u_w, theta)), for total energy plus the work of the wall
+ * on the pair, u_w . (f_b e_b - f*_a e_a) (the energy a moving wall gives
+ * the gas is its velocity times the momentum it gives; without this term
+ * a moving adiabatic wall would hold the total energy flux, not the heat
+ * flux, at zero, and the gas under it would cool).  Across a wall the
+ * derivative of D in the correction takes the ghost D_g = 2 D_w - D(node),
+ * D_w = D at the node's rho and the wall's u_w, theta_w (theta of the node
+ * on an adiabatic wall): D is linear in Q = rho u (1 - theta), so this is
+ * the D2Q9 oracle's mirror ghost Q_g = 2 Q_w - Q.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
  * load this file; only the tests, the smoke check and the benchmark's CPU
@@ -392,6 +396,13 @@ static void wall_bounce(const o3_params* p, int a, double rho, const double u[3]
     hn[b][i] = hg[b] + (hs[b] - heq[b]); /* the ghost's equilibrium + the node's h*_b - h^eq_b */
   } else {
     hn[b][i] = hs[a] + (hw[b] - hw[a]); /* h*_a - 2 (odd part of h^eq_a) */
+    if (p->energy_model == O3_E_TOTAL) {
+      /* total energy: plus the wall's work on the pair, u_w . (f_b e_b -
+       * f*_a e_a), so that no heat crosses a moving wall */
+      double work = 0.0;
+      for (int d = 0; d < 3; ++d) work += uw[d] * (fn[b][i] * E3[b][d] - fs[a] * E3[a][d]);
+      hn[b][i] += work;
+    }
   }
 }
 
@@ -472,6 +483,16 @@ void o3_moments(const o3_state* s, double* rho, double* ux, double* uy, double* 
     uz[i] = u[2];
     T[i] = th * s->p.T0;
   }
+}
+
+/* G_ij = sum_k dD_ijk/dx_k of the current state at every node, the
+ * argument of the correction term, into G[n][9] (row-major i, j). */
+void o3_gradients(o3_state* s, double* G) {
+  const o3_params* p = &s->p;
+  phase1(s, 1);
+  for (int z = 0; z < p->nz; ++z)
+    for (int y = 0; y < p->ny; ++y)
+      for (int x = 0; x < p->nx; ++x) node_G(s, x, y, z, &G[9 * idx3(p, x, y, z)]);
 }
 
 /* Sums of rho, rho u (3) and hbar over the grid. */

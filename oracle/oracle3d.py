@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
         _lib.o3_step.argtypes = [ctypes.c_void_p, ctypes.c_long, ctypes.c_int]
         _lib.o3_moments.argtypes = [ctypes.c_void_p, dp, dp, dp, dp, dp]
         _lib.o3_conserved.argtypes = [ctypes.c_void_p, dp]
+        _lib.o3_gradients.argtypes = [ctypes.c_void_p, dp]
         _lib.o3_get_pops.argtypes = [ctypes.c_void_p, dp]
         _lib.o3_set_pops.argtypes = [ctypes.c_void_p, dp]
         _lib.o3_feq.argtypes = [ctypes.c_double, ctypes.c_double, dp, ctypes.c_double, dp]
@@ -196,6 +197,14 @@ class Oracle3d:
         out = [np.empty(self.shape) for _ in range(5)]
         lib().o3_moments(self._h, *[_dp(v) for v in out])
         return tuple(out)  # rho, ux, uy, uz, T
+
+    def gradients(self) -> np.ndarray:
+        """G[z, y, x, i, j] = sum_k dD_ijk/dx_k (lattice units) of the current
+        state, the argument of the correction term (Eq. 50's differences,
+        the mirror ghost across a z wall)."""
+        out = np.empty(self.shape + (3, 3))
+        lib().o3_gradients(self._h, _dp(out))
+        return out
 
     def conserved(self) -> np.ndarray:
         out = np.zeros(5)

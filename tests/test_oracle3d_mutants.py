@@ -38,6 +38,18 @@ MUTANTS = [
     ("T_without_kinetic_energy",
      "T = 2.0 / (p->b * p->R) * (sh / r - 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));",
      "T = 2.0 / (p->b * p->R) * (sh / r);", "Eq. 37: kinetic energy not subtracted"),
+    ("wall_moving_sign", "fn[b][i] = fs[a] + (fw[b] - fw[a]);",
+     "fn[b][i] = fs[a] + (fw[a] - fw[b]);", "moving wall: the odd part added, not subtracted"),
+    ("adiabatic_wall_without_work", "hn[b][i] += work;", "hn[b][i] += 0.0 * work;",
+     "adiabatic moving wall: the wall's work dropped"),
+    ("isothermal_h_plain_bounce", "hn[b][i] = hg[b] + (hs[b] - heq[b]);", "hn[b][i] = hs[a];",
+     "isothermal wall: h bounced back like an adiabatic one"),
+    ("ghost_D_zero_gradient", "Dg[m] = 2.0 * Dw[m] - s->D[27 * i + m];",
+     "Dg[m] = s->D[27 * i + m];", "Eq. 50 across a wall: a zero-gradient ghost"),
+    ("ghost_D_without_wall_value", "Dg[m] = 2.0 * Dw[m] - s->D[27 * i + m];",
+     "Dg[m] = -s->D[27 * i + m];", "Eq. 50 across a wall: the mirror without D_w"),
+    ("ghost_theta_at_wall", "double thg = 2.0 * thw - th;", "double thg = thw;",
+     "isothermal wall: the ghost at the wall temperature, not extrapolated"),
 ]
 
 
