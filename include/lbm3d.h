@@ -3,7 +3,8 @@
  * double-distribution-function thermal lattice Boltzmann method of Li, Luo,
  * He, Gao and Tao (arXiv:1109.6672).  The paper builds the model on D2Q9 and
  * states that its formulation extends to three dimensions (Sec. V); this is
- * that extension, BGK scheme (Sec. III.C.1), every side periodic:
+ * that extension, BGK scheme (Sec. III.C.1), x and y periodic, each z side
+ * periodic or a halfway wall:
  *
  *   - f^eq: Eq. 18a with D = 3; h^eq: Eq. 18b with D = 3 (total energy,
  *     Eq. 36 with the (omega_h - omega_f) Z_a coupling), or the internal-
@@ -18,7 +19,19 @@
  *     quadratic polynomial of e_a with no constant moment (the counterpart of
  *     Eq. 49);
  *   - time step: Eq. 34 (with +(1 - omega_f/2) C_a) and Eq. 36 / Eq. 38;
- *     moments Eq. 35 and Eq. 37.
+ *     moments Eq. 35 and Eq. 37;
+ *   - z walls (not in the paper, which uses non-equilibrium extrapolation;
+ *     the rules of lbm.h carried to D3Q19), halfway at z = -1/2 and
+ *     nz - 1/2: a population a leaving through the wall comes back as its
+ *     opposite b with f_b = f*_a - 2 (odd part of Eq. 18a at the node's rho
+ *     and theta and the wall velocity); h on an isothermal wall
+ *     h_b = h^eq_b(ghost) + (h*_b - h^eq_b) with the ghost one spacing
+ *     outside at u_g = 2 u_w - u, theta_g = max(2 theta_w - theta,
+ *     theta_w / 2), rho_g = rho theta / theta_g; h on an adiabatic wall
+ *     h_b = h*_a - 2 (odd part of h^eq_a at (rho, u_w, theta)), for total
+ *     energy plus the wall's work on the pair u_w . (f_b e_b - f*_a e_a)
+ *     (a moving adiabatic wall passes its work, not heat); Eq. 50 across a
+ *     wall takes the mirror ghost Q_g = 2 rho u_w (1 - theta_w) - Q.
  *
  * Velocity set (index a: e_a), weights 1/3 (a = 0), 1/18 (1-6), 1/36 (7-18):
  *   0 (0,0,0)  1 (1,0,0)  2 (-1,0,0)  3 (0,1,0)   4 (0,-1,0)   5 (0,0,1)
@@ -55,6 +68,12 @@ typedef struct {
   int32_t correction;   /* 1: C_a as above; 0: omitted                        */
   int32_t z_full;       /* total energy: 1 Z = e.u - u^2/2, 0 Z = e.u         */
   int32_t precision;    /* LBM_P_FP64 or LBM_P_FP32                           */
+  int32_t bc_z[2];      /* z- and z+ sides: LBM_BC_PERIODIC,                  */
+                        /* LBM_BC_WALL_ISOTHERMAL or                          */
+                        /* LBM_BC_WALL_ADIABATIC (halfway walls, see above);  */
+                        /* x and y are always periodic                        */
+  double u_wall_z[2][3];  /* wall velocities of the z sides                   */
+  double T_wall_z[2];     /* wall temperatures (isothermal walls), > 0        */
 } lbm3d_params;
 
 typedef struct lbm3d_handle lbm3d_handle;
@@ -67,8 +86,9 @@ int64_t lbm3d_state_bytes(const lbm3d_params* p);
 /* Validates *p and allocates the state and the staging of host transfers
  * (5 nx ny nz doubles) on the current device; binds the handle to
  * cuda_stream (NULL: the legacy default stream).  Errors: LBM_ERR_PARAM
- * (nx, ny or nz < 1, tau <= 0, R T0 != 1/3, b < 3, an unknown model or
- * precision, 2^31 nodes or more), LBM_ERR_OOM, LBM_ERR_CUDA.  *out is NULL
+ * (nx, ny or nz < 1, tau <= 0, R T0 != 1/3, b < 3, an unknown model,
+ * precision or z side, a non-finite wall velocity, a wall temperature <= 0,
+ * 2^31 nodes or more), LBM_ERR_OOM, LBM_ERR_CUDA.  *out is NULL
  * on error. */
 int lbm3d_create(const lbm3d_params* p, void* cuda_stream, lbm3d_handle** out);
 

@@ -33,7 +33,7 @@
 // of Q in shared memory, then collides the plane below, whose own moments
 // the thread kept in registers and whose pulled populations it parked in
 // shared memory (a per-thread column, two planes deep, so no barrier guards
-// it).  Every side is periodic.
+// it).  x and y are periodic; each z side periodic or a halfway wall.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -75,7 +75,11 @@ struct Phys3 {
   C omega_f, omega_h;  // 2 / (2 tau + 1)
   C kz;                // omega_h - omega_f (Eq. 36)
   C b6, six_b;         // b / 6, 6 / b
+  C uw[2][3];          // wall velocities of the z- and z+ sides
+  C thw[2];            // wall theta = T_w / T0 (isothermal walls)
 };
+
+enum { BC3_PERIODIC = 0, BC3_ISO = 1, BC3_ADIA = 2 };
 
 struct Grid3 {
   void* src;
@@ -83,6 +87,7 @@ struct Grid3 {
   int nx, ny, nz, pitch;
   long long lp, zs;  // line stride (38 pitch) and plane stride ((ny + 2) lp)
   int energy_model, correction, z_full;
+  int bc_z[2];  // z- and z+ sides: BC3_PERIODIC or a halfway wall
   Phys3<double> pd;
   Phys3<float> pf;
 };
@@ -215,6 +220,85 @@ __device__ __forceinline__ void correction3(const C dq[3][3], C cc[Q19]) {
   cc[17] = cc[18] = dyz - oyz;  // e_y e_z = -1
 }
 
+// f^eq and h^eq of one direction a at (rho, u, theta) with the specific
+// energy es (the expressions of equilibria3 for that direction).
+template <class C, bool TOTAL>
+__device__ __forceinline__ void eq_one3(int a, C rho, C ux, C uy, C uz, C th, C es, C& f, C& h) {
+  const C usq = ux * ux + uy * uy + uz * uz;
+  const C A0 = C(1) - C(1.5) * usq;
+  const C eu = C(e3x(a)) * ux + C(e3y(a)) * uy + C(e3z(a)) * uz;
+  const bool axis = e3sq(a) == 1;
+  const C w = axis ? w3<C>(1) : w3<C>(7);
+  const C even = (axis ? A0 : A0 + C(1.5) * (th - C(1))) + C(4.5) * eu * eu;
+  const C odd = (axis ? C(6) - C(3) * th : C(1.5) + C(1.5) * th) * eu;
+  f = rho * w * (even + odd);
+  if constexpr (TOTAL) {
+    const C p = rho * th * (C(1) / C(3));
+    const C he = C(-3) * usq + C(9) * eu * eu + (axis ? C(0) : C(1.5) * th);
+    h = es * f + w * p * (he + C(3) * eu);
+  } else {
+    h = es * f;
+  }
+}
+
+// The populations of node (x, y, z) that leave through a z wall come back
+// into the node as their opposites (halfway walls at z = -1/2 and
+// nz - 1/2): with b the opposite of a, f_b = f*_a - 2 (odd part of f^eq_a at
+// the node's rho and theta and the wall velocity); h on an isothermal wall
+// h_b = h^eq_b(ghost) + (h*_b - h^eq_b), the ghost one spacing outside at
+// u_g = 2 u_w - u, theta_g = max(2 theta_w - theta, theta_w / 2),
+// rho_g = rho theta / theta_g; h on an adiabatic wall h_b = h*_a - 2 (odd
+// part of h^eq_a at (rho, u_w, theta)), for total energy plus the wall's
+// work on the pair u_w . (f_b e_b - f*_a e_a) = -(e_a . u_w)(f_b + f*_a)
+// (no heat crosses a moving adiabatic wall; its work does).  Each goes to
+// the slot from which the node pulls b: x - e_b = x + e_a, a ghost plane.
+template <class S, bool TOTAL>
+__device__ __forceinline__ void zwall_writes3(const Grid3& g, S* __restrict__ dst, int x, int y,
+                                              int z, const typename Io<S>::C v[NP3],
+                                              const typename Io<S>::C heq[Q19],
+                                              typename Io<S>::C rho, typename Io<S>::C ux,
+                                              typename Io<S>::C uy, typename Io<S>::C uz,
+                                              typename Io<S>::C th) {
+  using C = typename Io<S>::C;
+  const Phys3<C>& k = phys3<C>(g);
+#pragma unroll
+  for (int a = 1; a < Q19; ++a) {
+    if (e3z(a) == 0) continue;
+    const int side = e3z(a) < 0 ? 0 : 1;
+    if ((side == 0 ? z != 0 : z != g.nz - 1) || g.bc_z[side] == BC3_PERIODIC) continue;
+    const int b = (a & 1) ? a + 1 : a - 1;  // opposite
+    const C uwx = k.uw[side][0], uwy = k.uw[side][1], uwz = k.uw[side][2];
+    const C euw = C(e3x(a)) * uwx + C(e3y(a)) * uwy + C(e3z(a)) * uwz;
+    const bool axis = e3sq(a) == 1;
+    const C w = axis ? w3<C>(1) : w3<C>(7);
+    const C fodd = rho * w * (axis ? C(6) - C(3) * th : C(1.5) + C(1.5) * th) * euw;
+    const long long o = slot3(g, 0, x + e3x(a), y + e3y(a), z + e3z(a));
+    const C fb = v[a] - C(2) * fodd;
+    dst[o + (long long)b * g.pitch] = Io<S>::from(fb);
+    C hin;
+    if (g.bc_z[side] == BC3_ISO) {
+      const C thg = fmax(C(2) * k.thw[side] - th, C(0.5) * k.thw[side]);
+      const C ugx = C(2) * uwx - ux, ugy = C(2) * uwy - uy, ugz = C(2) * uwz - uz;
+      const C esg = TOTAL ? k.b6 * thg + C(0.5) * (ugx * ugx + ugy * ugy + ugz * ugz) : k.b6 * thg;
+      C fg, hg;
+      eq_one3<C, TOTAL>(b, rho * th / thg, ugx, ugy, ugz, thg, esg, fg, hg);
+      hin = hg + (v[Q19 + b] - heq[b]);
+    } else {
+      C hodd;
+      if constexpr (TOTAL) {
+        const C E = k.b6 * th + C(0.5) * (uwx * uwx + uwy * uwy + uwz * uwz);
+        hodd = E * fodd + w * (rho * th * (C(1) / C(3))) * C(3) * euw;
+      } else {
+        hodd = k.b6 * th * fodd;
+      }
+      hin = v[Q19 + a] - C(2) * hodd;
+      // total energy: the wall's work on the pair, u_w . (f_b e_b - f*_a e_a)
+      if constexpr (TOTAL) hin -= euw * (fb + v[a]);
+    }
+    dst[o + (long long)(Q19 + b) * g.pitch] = Io<S>::from(hin);
+  }
+}
+
 // Store of the 38 post-collision values of node (x, y, z) at its own slots,
 // and for a node on a face the periodic copies into the ghost slots: the
 // node at w = wrap(x + e_a) pulls population a from w - e_a.
@@ -230,6 +314,9 @@ __device__ __forceinline__ void store3(const Grid3& g, S* __restrict__ dst, int 
   for (int q = 1; q < Q19; ++q) {
     const int dx = x + e3x(q), dy = y + e3y(q), dz = z + e3z(q);
     if (dx >= 0 && dx < g.nx && dy >= 0 && dy < g.ny && dz >= 0 && dz < g.nz) continue;
+    // through a z wall: zwall_writes3 takes it
+    if ((dz < 0 && g.bc_z[0] != BC3_PERIODIC) || (dz >= g.nz && g.bc_z[1] != BC3_PERIODIC))
+      continue;
     const int sx = wrap3(dx, g.nx) - e3x(q), sy = wrap3(dy, g.ny) - e3y(q),
               sz = wrap3(dz, g.nz) - e3z(q);
     dst[slot3(g, q, sx, sy, sz)] = Io<S>::from(v[q]);
@@ -334,11 +421,29 @@ __global__ void __launch_bounds__(TX3 * TY, (step3d_min_blocks<S, TY>()))
     if (zc >= z0 && mine) {
       const int sm = (s + 1) % 3, s0 = (s + 2) % 3;  // planes r - 2 and r - 1
       C dq[3][3];  // dq[k][j] = dQ_j / dx_k
+      // across a z wall Eq. 50 takes the mirror ghost 2 Q_w - Q(node),
+      // Q_w = rho u_w (1 - theta_w) (theta_w: the node's own on an adiabatic
+      // wall)
+      const bool wb = zc == 0 && g.bc_z[0] != BC3_PERIODIC;
+      const bool wt = zc == nz - 1 && g.bc_z[1] != BC3_PERIODIC;
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         dq[0][j] = C(0.5) * (qs[s0][j][cell + 1] - qs[s0][j][cell - 1]);
         dq[1][j] = C(0.5) * (qs[s0][j][cell + HX] - qs[s0][j][cell - HX]);
-        dq[2][j] = C(0.5) * (qs[s][j][cell] - qs[sm][j][cell]);
+        C up = qs[s][j][cell], dn = qs[sm][j][cell];
+        if (wb || wt) {
+          const Phys3<C>& k = phys3<C>(g);
+          const C q0 = qs[s0][j][cell];
+          if (wt) {
+            const C thw = g.bc_z[1] == BC3_ISO ? k.thw[1] : pth;
+            up = C(2) * prho * k.uw[1][j] * (C(1) - thw) - q0;
+          }
+          if (wb) {
+            const C thw = g.bc_z[0] == BC3_ISO ? k.thw[0] : pth;
+            dn = C(2) * prho * k.uw[0][j] * (C(1) - thw) - q0;
+          }
+        }
+        dq[2][j] = C(0.5) * (up - dn);
       }
       C cc[Q19];
       if constexpr ((M & M3_CORR) != 0) {
@@ -369,6 +474,8 @@ __global__ void __launch_bounds__(TX3 * TY, (step3d_min_blocks<S, TY>()))
         v[Q19 + a] = hs;
       }
       store3<S>(g, dst, x, y, zc, v);
+      if ((zc == 0 && g.bc_z[0] != BC3_PERIODIC) || (zc == nz - 1 && g.bc_z[1] != BC3_PERIODIC))
+        zwall_writes3<S, (M & M3_TOTAL) != 0>(g, dst, x, y, zc, v, heq, prho, pux, puy, puz, pth);
     }
     prho = crho;
     pux = cux;

@@ -86,6 +86,26 @@ int validate3(const lbm3d_params* p, std::string& why) {
     why = "precision must be LBM_P_FP64 or LBM_P_FP32";
     return LBM_ERR_PARAM;
   }
+  for (int k = 0; k < 2; ++k) {
+    if (p->bc_z[k] != LBM_BC_PERIODIC && p->bc_z[k] != LBM_BC_WALL_ISOTHERMAL &&
+        p->bc_z[k] != LBM_BC_WALL_ADIABATIC) {
+      why = "bc_z must be LBM_BC_PERIODIC or a wall";
+      return LBM_ERR_PARAM;
+    }
+    for (int d = 0; d < 3; ++d)
+      if (!std::isfinite(p->u_wall_z[k][d])) {
+        why = "u_wall_z must be finite";
+        return LBM_ERR_PARAM;
+      }
+    if (!(p->T_wall_z[k] > 0.0) || !std::isfinite(p->T_wall_z[k])) {
+      why = "T_wall_z must be finite and > 0";
+      return LBM_ERR_PARAM;
+    }
+  }
+  if ((p->bc_z[0] == LBM_BC_PERIODIC) != (p->bc_z[1] == LBM_BC_PERIODIC)) {
+    why = "the z sides are both periodic or both walls";
+    return LBM_ERR_PARAM;
+  }
   return LBM_OK;
 }
 
@@ -108,9 +128,27 @@ void fill_grid3(const lbm3d_params* p, Grid3& g) {
   g.correction = p->correction;
   g.z_full = p->z_full;
   const double wf = 2.0 / (2.0 * p->tau_f + 1.0), wh = 2.0 / (2.0 * p->tau_h + 1.0);
-  g.pd = Phys3<double>{wf, wh, wh - wf, p->b / 6.0, 6.0 / p->b};
-  g.pf = Phys3<float>{(float)wf, (float)wh, (float)(wh - wf), (float)(p->b / 6.0),
-                      (float)(6.0 / p->b)};
+  g.pd = Phys3<double>{};
+  g.pf = Phys3<float>{};
+  g.pd.omega_f = wf;
+  g.pd.omega_h = wh;
+  g.pd.kz = wh - wf;
+  g.pd.b6 = p->b / 6.0;
+  g.pd.six_b = 6.0 / p->b;
+  g.pf.omega_f = (float)wf;
+  g.pf.omega_h = (float)wh;
+  g.pf.kz = (float)(wh - wf);
+  g.pf.b6 = (float)(p->b / 6.0);
+  g.pf.six_b = (float)(6.0 / p->b);
+  for (int k = 0; k < 2; ++k) {
+    g.bc_z[k] = p->bc_z[k];
+    g.pd.thw[k] = p->T_wall_z[k] / p->T0;
+    g.pf.thw[k] = (float)g.pd.thw[k];
+    for (int d = 0; d < 3; ++d) {
+      g.pd.uw[k][d] = p->u_wall_z[k][d];
+      g.pf.uw[k][d] = (float)p->u_wall_z[k][d];
+    }
+  }
 }
 
 void* buf_ptr3(const lbm3d_handle* h, int b) {

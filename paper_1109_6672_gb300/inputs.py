@@ -202,7 +202,7 @@ def cavity_large_dT(Ra: float = 1e5, n: int | None = None, mu_r: float | None = 
 # ---- three-dimensional (D3Q19) workloads ------------------------------------
 
 def base_params3d(nx: int, ny: int, nz: int, **kw) -> dict:
-    """Parameters of a 3-D grid (every side periodic): the same physical
+    """Parameters of a 3-D grid (periodic unless bc_z is given): the same physical
     parameters as base_params, without walls or gravity."""
     p = dict(nx=int(nx), ny=int(ny), nz=int(nz), tau_f=0.3, tau_h=0.3 / 0.71, R=1.0 / 3.0,
              T0=1.0, b=3.0, energy_model=E_TOTAL, correction=1, z_full=1, precision=P_FP64)

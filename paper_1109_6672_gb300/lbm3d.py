@@ -23,6 +23,8 @@ class lbm3d_params(ctypes.Structure):
         ("R", ctypes.c_double), ("T0", ctypes.c_double), ("b", ctypes.c_double),
         ("energy_model", ctypes.c_int32), ("correction", ctypes.c_int32),
         ("z_full", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("bc_z", ctypes.c_int32 * 2), ("u_wall_z", (ctypes.c_double * 3) * 2),
+        ("T_wall_z", ctypes.c_double * 2),
     ]
 
 
@@ -68,6 +70,12 @@ def make_params(p: dict) -> lbm3d_params:
     o.correction = int(p.get("correction", 1))
     o.z_full = int(p.get("z_full", 1))
     o.precision = int(p.get("precision", LBM_P_FP64))
+    for k in range(2):
+        o.bc_z[k] = int(p.get("bc_z", [0, 0])[k])
+        o.T_wall_z[k] = float(p.get("T_wall_z", [1.0, 1.0])[k])
+        uw = p.get("u_wall_z", [[0.0] * 3] * 2)[k]
+        for d in range(3):
+            o.u_wall_z[k][d] = float(uw[d])
     return o
 
 

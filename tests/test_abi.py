@@ -150,7 +150,9 @@ def test_3d_state_bytes_and_validation_without_gpu(lib):
     assert lbm3d.lbm3d_state_bytes(dict(p, precision=lbm.LBM_P_FP64)) == 2 * n
     for bad in (dict(p, tau_f=0.0), dict(p, R=1.0), dict(p, b=2.0), dict(p, nz=0),
                 dict(p, precision=lbm.LBM_P_FP32_BF16), dict(p, energy_model=3),
-                dict(p, correction=2), dict(p, nx=2048, ny=2048, nz=1024)):
+                dict(p, correction=2), dict(p, nx=2048, ny=2048, nz=1024),
+                dict(p, bc_z=[1, 0]), dict(p, bc_z=[3, 3]), dict(p, bc_z=[1, 1], T_wall_z=[0.0, 1.0]),
+                dict(p, bc_z=[1, 1], u_wall_z=[[float("nan"), 0, 0], [0, 0, 0]])):
         with pytest.raises(lbm.LbmError) as e:
             lbm3d.lbm3d_state_bytes(bad)
         assert e.value.status == lbm.LBM_ERR_PARAM

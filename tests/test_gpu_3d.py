@@ -120,3 +120,86 @@ def test_bench_box_full_size_3d():
     assert abs(c1[0] - c0[0]) <= 1e-6 * c0[0]
     assert abs(c1[4] - c0[4]) <= 1e-6 * c0[4]
     g32.close()
+
+
+WALLS = {
+    "iso_moving": dict(bc_z=[1, 1], u_wall_z=[[0.0, 0.0, 0.0], [0.05, -0.02, 0.0]],
+                       T_wall_z=[1.03, 0.98]),
+    "adiabatic": dict(bc_z=[2, 2], u_wall_z=[[0.01, 0.0, 0.0], [0.0, 0.0, 0.0]]),
+    "iso_adia": dict(bc_z=[1, 2], T_wall_z=[1.04, 1.0]),
+}
+
+
+@pytest.mark.parametrize("walls", list(WALLS))
+@pytest.mark.parametrize("mode", ["total_zfull_corr", "internal_corr", "total"])
+@pytest.mark.parametrize("shape", [(4, 3, 5), (37, 11, 9)], ids=["4x3x5", "37x11x9"])
+def test_fp64_parity_3d_walls(shape, mode, walls):
+    p, f = _case(shape, mode, lbm.LBM_P_FP64)
+    p.update(WALLS[walls])
+    o = o3.Oracle3d(p).init(*f).step(30)
+    g = Lbm3d(p).init(*f).step(30)
+    assert _rel(g.pops(), o.pops()) <= 1e-12
+    g.close()
+
+
+@pytest.mark.parametrize("tile", [8, 16])
+def test_fp32_parity_3d_walls(tile):
+    p, f = _case((37, 21, 9), "total_zfull_corr", lbm.LBM_P_FP32)
+    p.update(WALLS["iso_moving"])
+    o = o3.Oracle3d(dict(p, precision=lbm.LBM_P_FP64)).init(*f).step(30)
+    g = Lbm3d(p).set_tile(tile).init(*f).step(30)
+    assert _rel(g.pops(), o.pops()) <= 2e-5
+    g.close()
+
+
+def test_fp64_parity_3d_walls_long():
+    """400 steps with a fast moving wall and several z ranges per column of
+    blocks: the wall planes meet block boundaries and the x-y tile edges."""
+    p, f = _case((33, 9, 40), "total_zfull_corr", lbm.LBM_P_FP64)
+    # b = 5: with b = 3 the D3Q19 h^eq loses positivity where theta > 1 and
+    # this flow overflows in the oracle too
+    p.update(b=5.0, bc_z=[1, 2], u_wall_z=[[0.0, 0.0, 0.0], [0.2, 0.1, 0.0]],
+             T_wall_z=[1.05, 1.0])
+    o = o3.Oracle3d(p).init(*f).step(400, threads=8)
+    g = Lbm3d(p).init(*f).step(400)
+    # FP64 rounding, grown over 400 steps
+    assert _rel(g.pops(), o.pops()) <= 1e-11
+    g.close()
+
+
+def test_couette_3d_gpu_closed_form():
+    """The 3-D thermal Couette flow on the GPU (FP64): flow in x between the
+    z walls, the top moving; u linear and the viscous-heating parabola (a
+    4 x 4 cross-section seeded with 1e-10 noise at Pr = 1, where the BGK step
+    damps modes oblique to z)."""
+    H, U, nu, Pr, b = 16, 1.0 / 3.0, 0.2, 1.0, 5.0
+    tau_f = nu / inputs.RT0
+    p = inputs.base_params3d(4, 4, H, tau_f=tau_f, tau_h=tau_f / Pr, b=b,
+                             bc_z=[1, 1], u_wall_z=[[0.0, 0.0, 0.0], [U, 0.0, 0.0]])
+    g = Lbm3d(p).init(*inputs.uniform_fields3d(4, 4, H, seed=0, u_amp=1e-10)).step(6000)
+    rho, ux, uy, uz, T = g.moments()
+    g.close()
+    eta = (np.arange(H) + 0.5) / H
+    assert np.abs(ux[:, 0, 0] - U * eta).max() < 1.5e-3 * U
+    assert np.abs(uz).max() < 1e-10 and np.abs(uy).max() < 1e-10
+    rise = Pr * U * U / ((b + 2) * inputs.RT0) * eta * (1 - eta)
+    assert np.abs((T[:, 0, 0] - 1) - rise).max() < 0.02 * rise.max()
+
+
+@pytest.mark.parametrize("precision", [lbm.LBM_P_FP64, lbm.LBM_P_FP32], ids=["fp64", "fp32"])
+def test_couette_3d_gpu_adiabatic_moving_wall(precision):
+    """Bottom wall at rest and T0, top wall moving and adiabatic: its work
+    enters the gas, no heat crosses it, and the heating follows
+    theta - 1 = Pr U^2 / ((b + 2) R T0) (2 eta - eta^2) (0.1 % in the
+    oracle at H = 16)."""
+    H, U, nu, Pr, b = 16, 0.2, 0.2, 1.0, 5.0
+    tau_f = nu / inputs.RT0
+    p = inputs.base_params3d(2, 2, H, tau_f=tau_f, tau_h=tau_f / Pr, b=b, precision=precision,
+                             bc_z=[1, 2], u_wall_z=[[0.0, 0.0, 0.0], [U, 0.0, 0.0]])
+    g = Lbm3d(p).init(*inputs.uniform_fields3d(2, 2, H, seed=0)).step(8000)
+    rho, ux, uy, uz, T = g.moments()
+    g.close()
+    eta = (np.arange(H) + 0.5) / H
+    assert np.abs(ux[:, 0, 0] - U * eta).max() < 2e-4 * U
+    rise = Pr * U * U / ((b + 2) * inputs.RT0) * (2 * eta - eta * eta)
+    assert np.abs((T[:, 0, 0] - 1) - rise).max() < 2e-3 * rise.max()
