@@ -36,7 +36,9 @@
  *         theta_w / 2),
  *         rho_g = rho theta / theta_g;
  *      h, adiabatic wall: bounce-back plus twice the odd part of h^eq at the
- *         boundary node's (rho, theta) and the wall velocity;
+ *         boundary node's (rho, theta) and the wall velocity, for total energy
+ *         plus the wall's work on the bounced pair u_w . (f_b e_b - f*_a e_a)
+ *         (a moving adiabatic wall passes its work, not heat);
  *      corners: a population leaving across two walls uses the x-side wall;
  *      Eq. 50 across a wall: mirror ghost Q_g = 2 rho u_w (1 - theta_w) - Q.
  *  - Open x sides, for the attenuation-driven acoustic streaming of Sec. IV.B
@@ -61,8 +63,10 @@
  *    pressure carried to G by hydrostatic balance (rho_G theta_G =
  *    rho_F (theta_F - 3 g n_y), since p = rho R T); its
  *    pre-collision populations are its equilibria plus F's non-equilibrium
- *    part (for h on an adiabatic wall, without that part's normal energy
- *    flux); it collides like a fluid node (force of its own density, no
+ *    part (for h on an adiabatic wall, without that part's normal heat
+ *    flux: the normal moment of h^neq - Z f^neq, Z = e.u_w - |u_w|^2/2 the
+ *    Eq. 36 coupling at the wall velocity, so that a moving wall's viscous
+ *    work passes); it collides like a fluid node (force of its own density, no
  *    correction term) and sends its populations into the domain.  A corner
  *    ghost at the end of an x side's column feeds the corner node (the x side
  *    wins); Eq. 50 across such a wall keeps the mirror ghost above.  Written

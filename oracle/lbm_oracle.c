@@ -50,7 +50,10 @@
  *     h_in = h^eq(ghost) + (h* - h^eq)(node);
  *   - h on adiabatic walls: bounce-back plus twice the odd part of h^eq at
  *     (rho, u_w, theta) of the node (zero total-energy flux through a wall at
- *     rest);
+ *     rest), for total energy plus the work of the wall on the pair,
+ *     u_w . (f_b e_b - f*_a e_a): the energy a moving wall gives the gas is
+ *     its velocity times the momentum it gives, so heat, not work, is what
+ *     the wall stops;
  *   - a population leaving through a corner across two walls takes the
  *     x-side wall's rule;
  *   - Eq. 50 across a wall uses the mirror ghost Q_g = 2 Q_w - Q(node),
@@ -81,7 +84,9 @@
  * hydrostatic term).  Its pre-collision
  * populations are its equilibria plus F's non-equilibrium part
  * fbar(F) - f^eq(F) (likewise for h; on an adiabatic wall without the normal
- * energy flux that part carries), and it collides like any node, with
+ * heat flux that part carries: the normal moment of h^neq - Z f^neq, Z the
+ * coupling of Eq. 36 at the wall velocity, so that the viscous work Z f^neq
+ * of a moving wall still passes), and it collides like any node, with
  * the Guo force of its own density and no correction term; G emits the
  * post-collision populations pointing into the domain, and what leaves
  * through the side is dropped.
@@ -624,6 +629,9 @@ static void phase2(orc_state* s, int nthreads) {
         } else {
           double B = 0.5 * (hw[side][b] - hw[side][a]); /* odd part of h^eq */
           s->hn[b][i] = hs[a] + 2.0 * B;
+          if (p->energy_model == ORC_E_TOTAL)
+            s->hn[b][i] += uwx * (s->fn[b][i] * EX[b] - fs[a] * EX[a]) +
+                           uwy * (s->fn[b][i] * EY[b] - fs[a] * EY[a]);
         }
       }
 
@@ -660,13 +668,18 @@ static void phase2(orc_state* s, int nthreads) {
           hbG[a] = eqhG[a] + (hb[a] - heq[a]);
         }
         if (p->bc[side] == ORC_WALL_ADIABATIC) {
-          /* an adiabatic wall node carries no normal energy flux: the
-           * normal moment of the borrowed h non-equilibrium part is taken
-           * out (its energy and tangential moments are untouched) */
+          /* an adiabatic wall node carries no normal heat flux: the normal
+           * moment of the borrowed h non-equilibrium part, less the viscous
+           * work Z f^neq it carries at the wall velocity (h - Z f relaxes at
+           * the thermal rate in Eq. 36), is taken out (its energy and
+           * tangential moments are untouched) */
           double qn = 0.0, wn = 0.0;
           for (int a = 0; a < 9; ++a) {
             const double en = EX[a] * nxo + EY[a] * nyo;
-            qn += en * (hb[a] - heq[a]);
+            double Zw = 0.0;
+            if (p->energy_model == ORC_E_TOTAL)
+              Zw = EX[a] * uwx + EY[a] * uwy - (p->z_full ? 0.5 * (uwx * uwx + uwy * uwy) : 0.0);
+            qn += en * ((hb[a] - heq[a]) - Zw * (fb[a] - feq[a]));
             wn += W[a] * en * en;
           }
           for (int a = 0; a < 9; ++a) hbG[a] -= W[a] * (EX[a] * nxo + EY[a] * nyo) * qn / wn;

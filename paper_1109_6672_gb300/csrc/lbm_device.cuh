@@ -472,7 +472,9 @@ __device__ __forceinline__ void put(const Grid& g, S* dst, int a, int x, int y,
 }
 
 // Ghost-slot writes of a boundary node (x, y): periodic copies and the wall
-// rules.  v[0..8] = f*, v[9..17] = h*, v[18..26] = h^eq of the node.  A
+// rules (adiabatic walls of the total-energy model add the wall's work on the
+// bounced pair, u_w . (f_b e_b - f*_a e_a): no heat crosses a moving
+// adiabatic wall, its work does).  v[0..8] = f*, v[9..17] = h*, v[18..26] = h^eq of the node.  A
 // population leaving through a corner takes the x side's rule when that side
 // is a wall, else the y side's.  SKIPX: the populations that leave through the
 // x sides (x wall or periodic in both directions) are written by xedge_writes.
@@ -508,12 +510,18 @@ __device__ __noinline__ void boundary_writes(const Grid& g, S* __restrict__ dst,
       have = side;
     }
     const int b = opp(a);  // reflected direction; node (x, y) pulls it from d
-    put<S>(g, dst, b, dx, dy, v[a] + (fw[b] - fw[a]), hs, 18 + b);
+    const C fb = v[a] + (fw[b] - fw[a]);
+    put<S>(g, dst, b, dx, dy, fb, hs, 18 + b);
     C hin;
-    if (g.bc[side] == BC_ISO)
+    if (g.bc[side] == BC_ISO) {
       hin = hw[b] + (v[9 + b] - v[18 + b]);
-    else
+    } else {
       hin = v[9 + a] + (hw[b] - hw[a]);
+      if (g.energy_model == E_TOTAL) {  // the wall's work u_w . (f_b e_b - f*_a e_a)
+        const Phys<C>& k = phys<C>(g);
+        hin -= (C(ex(a)) * k.uw[side][0] + C(ey(a)) * k.uw[side][1]) * (fb + v[a]);
+      }
+    }
     put<S>(g, dst, 9 + b, dx, dy, hin, hs, 27 + b);
   }
 }
@@ -565,7 +573,8 @@ __device__ __forceinline__ void xedge_one(const Grid& g, S* __restrict__ dst, in
     const C lin = diag ? C(3) * th : C(3) - C(1.5) * (th - C(1));
     const C fodd = rho * w * lin * euw;  // odd part of f^eq_A at (rho, u_w, theta)
     const unsigned hs = Io<S>::sr ? sr_hash(g, x, y) : 0u;
-    put<S>(g, dst, B, dx, dy, v[A] - C(2) * fodd, hs, 18 + B);
+    const C fb = v[A] - C(2) * fodd;
+    put<S>(g, dst, B, dx, dy, fb, hs, 18 + B);
     C hin;
     if (g.bc[XS] == BC_ISO) {
       // ghost temperature linear through the wall value, floored at half of
@@ -584,6 +593,7 @@ __device__ __forceinline__ void xedge_one(const Grid& g, S* __restrict__ dst, in
         hodd = k.b6 * th * fodd;
       }
       hin = v[9 + A] - C(2) * hodd;
+      if (total) hin -= euw * (fb + v[A]);  // the wall's work u_w . (f_b e_b - f*_a e_a)
     }
     put<S>(g, dst, 9 + B, dx, dy, hin, hs, 27 + B);
     return;

@@ -153,14 +153,19 @@ __device__ void nee_ghost(const Grid& g, const S* __restrict__ src, S* __restric
   C fqG[9], hqG[9], fb[9], hb[9];
   collision_equilibria<C>(rG, uwx, uwy, thG, EsG, kp.b6, total, fqG, hqG);
   C hn[9], qn = C(0);
+  const C zw2 = (total && g.z_full) ? C(0.5) * (uwx * uwx + uwy * uwy) : C(0);
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
-    fb[a] = fqG[a] + ((pref<S>(g, a) + d[a]) - feq[a]);
+    const C fneq = (pref<S>(g, a) + d[a]) - feq[a];
+    fb[a] = fqG[a] + fneq;
     hn[a] = (pref<S>(g, 9 + a) + d[9 + a]) - heq[a];
-    qn += C(ex(a) * nxo + ey(a) * nyo) * hn[a];
+    // the heat part of h^neq: less the viscous work Z f^neq at the wall
+    // velocity (h - Z f relaxes at the thermal rate, Eq. 36)
+    const C zw = total ? C(ex(a)) * uwx + C(ey(a)) * uwy - zw2 : C(0);
+    qn += C(ex(a) * nxo + ey(a) * nyo) * (hn[a] - zw * fneq);
   }
-  // an adiabatic wall node carries no normal energy flux: the normal moment
-  // of the borrowed h non-equilibrium part is taken out (sum w e_n^2 = 1/3)
+  // an adiabatic wall node carries no normal heat flux: that part's normal
+  // moment is taken out (sum w e_n^2 = 1/3); a moving wall's work passes
   const bool adia = g.bc[side] != BC_ISO;
 #pragma unroll
   for (int a = 0; a < 9; ++a) {

@@ -254,10 +254,18 @@ class Brute:
                               else heq_internal(tG, p["b"], fG))
                         fbG = np.array(fG) + self.F[:, fy, fx] - feq[:, fy, fx]
                         hneq = self.H[:, fy, fx] - heq[:, fy, fx]
-                        if p["bc"][side] == ADIA:  # no normal energy flux at the wall node
+                        if p["bc"][side] == ADIA:  # no normal heat flux at the wall node
                             nxo, nyo = [(-1, 0), (1, 0), (0, -1), (0, 1)][side]
                             en = EX * nxo + EY * nyo
-                            hneq = hneq - W * en * (en @ hneq) / (W @ (en * en))
+                            # the heat part of h^neq: less the viscous work
+                            # Z f^neq at the wall velocity (total energy)
+                            heat = hneq
+                            if p["energy_model"] == 0:
+                                Zw = EX * uw[0] + EY * uw[1]
+                                if p["z_full"]:
+                                    Zw = Zw - 0.5 * (uw[0] ** 2 + uw[1] ** 2)
+                                heat = hneq - Zw * (self.F[:, fy, fx] - feq[:, fy, fx])
+                            hneq = hneq - W * en * (en @ heat) / (W @ (en * en))
                         hbG = np.array(hG) + hneq
                         CG = np.array([W[k] * (3 * EY[k] * (-rG * p["g"]) + 9 * (
                             (EX[k] * uw[0] + EY[k] * uw[1]) * EY[k] * (-rG * p["g"]) -
@@ -286,6 +294,9 @@ class Brute:
                         ha = (heq_total(r, uw[0], uw[1], t, p["b"], fa) if p["energy_model"] == 0
                               else heq_internal(t, p["b"], fa))
                         Hn[a, y, x] = hs[o, y, x] + (ha[a] - ha[o])
+                        if p["energy_model"] == 0:  # the moving wall's work on the pair
+                            Hn[a, y, x] += (EX[a] * uw[0] + EY[a] * uw[1]) * (
+                                Fn[a, y, x] + fs[o, y, x])
         self.F, self.H = Fn, Hn
 
     def pops(self):

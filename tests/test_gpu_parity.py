@@ -214,3 +214,27 @@ def test_graph_replay_equals_single_launches(name, precision):
         np.testing.assert_array_equal(c.pops(), d.pops())
         for g in (a, b, c, d):
             g.close()
+
+
+@pytest.mark.parametrize("nee", [False, True], ids=["halfway", "nee"])
+@pytest.mark.parametrize("precision", [lbm.LBM_P_FP64, lbm.LBM_P_FP32], ids=["fp64", "fp32"])
+def test_couette_adiabatic_moving_wall_gpu(precision, nee):
+    """Bottom wall at rest and T0, top wall moving and adiabatic: the wall's
+    work enters the gas, no heat crosses it, and the heating follows
+    theta - 1 = Pr U^2 / ((b + 2) R T0) (2 eta - eta^2) (halfway walls at
+    eta = (y + 1/2) / H: 0.1 % at H = 16 in the oracle; walls of
+    non-equilibrium extrapolation on the ghost nodes, eta = (y + 1) / (H + 1):
+    exact in the oracle)."""
+    H, U, nu, Pr, b = 16, 0.2, 0.2, 1.0, 5.0
+    tau_f = nu / inputs.RT0
+    p = inputs.base_params(4, H, tau_f=tau_f, tau_h=tau_f / Pr, b=b, precision=precision,
+                           bc=[P, P, ISO, ADI], u_wall=[[0, 0], [0, 0], [0, 0], [U, 0]],
+                           wall_nee=12 if nee else 0)
+    g = lbm.Lbm(p).init(*inputs.uniform_fields(4, H, seed=0)).step(8000)
+    rho, ux, uy, T = g.moments()
+    g.close()
+    eta = (np.arange(H) + 1.0) / (H + 1) if nee else (np.arange(H) + 0.5) / H
+    assert np.abs(ux[:, 0] - U * eta).max() < 1e-5 * U
+    rise = Pr * U * U / ((b + 2) * inputs.RT0) * (2 * eta - eta * eta)
+    # FP32 storage adds about 1e-6 to theta (6e-5 of the rise)
+    assert np.abs((T[:, 0] - 1) - rise).max() < (5e-4 if nee else 2e-3) * rise.max()

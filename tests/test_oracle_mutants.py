@@ -89,6 +89,15 @@ MUTANTS = [
     ("nee_adiabatic_first_order", "thG = fmax((4.0 * th - s->theta[i2]) / 3.0, 0.5 * th);",
      "thG = th;", "adiabatic non-equilibrium wall: zero slope to first order only",
      ["test_oracle_nee.py::test_nee_table1_couette_pr1"]),
+    ("adiabatic_wall_without_work",
+     "if (p->energy_model == ORC_E_TOTAL)\n            s->hn[b][i] += uwx",
+     "if (0)\n            s->hn[b][i] += uwx",
+     "adiabatic halfway wall: the moving wall's work dropped",
+     ["test_oracle_physics.py::test_couette_adiabatic_moving_wall"]),
+    ("nee_adiabatic_removes_work", "qn += en * ((hb[a] - heq[a]) - Zw * (fb[a] - feq[a]));",
+     "qn += en * (hb[a] - heq[a]);",
+     "adiabatic non-equilibrium wall: the viscous work taken out with the heat flux",
+     ["test_oracle_nee.py::test_nee_couette_adiabatic_moving_wall"]),
 ]
 
 

@@ -36,6 +36,8 @@ CASES = {
     "x_nee_y_periodic": dict(bc=[1, 1, 0, 0], wall_nee=3, T_wall=[1.1, 0.9, 1, 1]),
     "mrt_all": dict(bc=[1, 2, 2, 1], wall_nee=15, collision=1, s_e=1.3, s_q=1.6,
                     T_wall=[1.1, 1, 1, 0.95]),
+    "adiabatic_moving": dict(bc=[0, 0, 2, 2], wall_nee=12, u_wall=[[0, 0], [0, 0], [0.03, 0],
+                                                                     [-0.04, 0]]),
 }
 
 
@@ -82,6 +84,26 @@ def test_nee_couette_viscous_heating():
     Pr = p["tau_f"] / p["tau_h"]
     rise = Pr * U ** 2 / ((p["b"] + 2) * RT0) * eta * (1 - eta)
     assert np.abs((T[:, 0] - 1) - rise).max() < 0.01 * rise.max()
+
+
+@pytest.mark.parametrize("collision", [O.BGK, O.MRT], ids=["bgk", "mrt"])
+def test_nee_couette_adiabatic_moving_wall(collision):
+    """Bottom wall at rest and T0, top wall moving and adiabatic, both of
+    non-equilibrium extrapolation (walls on the ghost nodes, eta = (y + 1) /
+    (ny + 1)): no heat crosses the moving wall, its viscous work does, and the
+    heating is theta - 1 = Pr U^2 / ((b + 2) R T0) (2 eta - eta^2), exact to
+    the steady state's convergence (measured 6e-12 at ny = 8)."""
+    H, U, nu, Pr, b = 8, 0.2, 0.2, 1.0, 5.0
+    tau_f = nu / RT0
+    p = inputs.base_params(2, H, tau_f=tau_f, tau_h=tau_f / Pr, b=b, collision=collision,
+                           bc=[0, 0, inputs.WALL_ISOTHERMAL, inputs.WALL_ADIABATIC],
+                           u_wall=[[0, 0], [0, 0], [0, 0], [U, 0]], wall_nee=12)
+    rho, ux, uy, T = O.Oracle(p).init(*inputs.uniform_fields(2, H, seed=0)).step(
+        3000, threads=4).moments()
+    eta = (np.arange(H) + 1.0) / (H + 1)
+    assert np.abs(ux[:, 0] - U * eta).max() < 1e-10 * U
+    rise = Pr * U * U / ((b + 2) * RT0) * (2 * eta - eta * eta)
+    assert np.abs((T[:, 0] - 1) - rise).max() < 1e-8 * rise.max()
 
 
 def test_nee_large_dt_cavity_has_no_spurious_flow():
