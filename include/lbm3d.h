@@ -127,10 +127,20 @@ int lbm3d_sync(lbm3d_handle* h);
 int64_t lbm3d_steps_done(const lbm3d_handle* h);
 
 /* Launch shape of the step kernel (no counterpart in the paper; results do
- * not depend on it): a block owns 32 x tile_rows nodes of (x, y) and marches
- * along z.  tile_rows = 8 or 16 (16 for LBM_P_FP32 only), 0 = automatic
- * (8).  LBM_ERR_PARAM for other values. */
+ * not depend on it beyond FP32 rounding): a block owns 32 x tile_rows nodes
+ * of (x, y) and marches along z.  tile_rows = 8 or 16 (16 for LBM_P_FP32
+ * only), with the halo ring on the tile's first threads; 0 = automatic
+ * (LBM_P_FP64: 8 rows; LBM_P_FP32: 4 rows with halo warps, see
+ * lbm3d_set_launch).  LBM_ERR_PARAM for other values. */
 int lbm3d_set_tile(lbm3d_handle* h, int32_t tile_rows);
+
+/* Launch shape of the step kernel with the halo option (no counterpart in
+ * the paper; results do not depend on it): tile_rows as above (0 =
+ * automatic, halo_warps then ignored) and halo_warps = 1 to give the tile's
+ * one-node halo ring warps of its own instead of a second pull on the
+ * tile's first threads.  Shapes (tile_rows, halo_warps): (8, 0); for
+ * LBM_P_FP32 also (16, 0), (4, 1) and (8, 1).  LBM_ERR_PARAM otherwise. */
+int lbm3d_set_launch(lbm3d_handle* h, int32_t tile_rows, int32_t halo_warps);
 
 /* Frees the device state and the handle; NULL-safe. */
 void lbm3d_destroy(lbm3d_handle* h);

@@ -326,36 +326,60 @@ __device__ __forceinline__ void store3(const Grid3& g, S* __restrict__ dst, int 
 
 constexpr int TX3 = 32;
 
+// Cells of the one-node halo ring around a 32 x TY tile, and the threads of a
+// block: one per tile cell, plus (SPLIT) whole warps of their own for the
+// halo cells; otherwise the tile's first threads take a halo cell each too.
+template <int TY>
+__host__ __device__ constexpr int nhalo3() {
+  return 2 * (TX3 + 2) + 2 * TY;
+}
+template <int TY, bool SPLIT>
+__host__ __device__ constexpr int threads3() {
+  return TX3 * TY + (SPLIT ? (nhalo3<TY>() + 31) / 32 * 32 : 0);
+}
+
 // Dynamic shared memory of the step kernel with tiles of TY rows: the parked
-// populations of two planes, [2][38][threads], then the Q ring
-// [3][3][halo tile].
+// populations of two planes, [2][38][tile cells], then the Q ring
+// [4][3][halo tile].
 template <class S, int TY>
 __host__ __device__ constexpr size_t step3d_smem() {
   using C = typename Io<S>::C;
-  return sizeof(C) * ((size_t)2 * NP3 * TX3 * TY + 9 * (TX3 + 2) * (TY + 2));
+  return sizeof(C) * ((size_t)2 * NP3 * TX3 * TY + 12 * (TX3 + 2) * (TY + 2));
 }
 
 // Resident blocks per SM the register budget is sized for: two 256-thread
-// blocks (8-row tiles) or one 512-thread block (16-row tiles); FP64 one.
-template <class S, int TY>
+// blocks (8-row tiles), two 224-thread blocks (4-row tiles with halo warps)
+// or one block otherwise; FP64 one.
+template <class S, int TY, bool SPLIT>
 __host__ __device__ constexpr int step3d_min_blocks() {
-  return (sizeof(S) == 8 || TY == 16) ? 1 : 2;
+  return sizeof(S) == 8 ? 1 : ((SPLIT ? TY <= 4 : TY == 8) ? 2 : 1);
 }
 
 // One time step of every node of the block's 32 x TY tile over z in
-// [z0, z0 + zrows).
-template <class S, int M, int TY>
-__global__ void __launch_bounds__(TX3 * TY, (step3d_min_blocks<S, TY>()))
+// [z0, z0 + zrows).  Per plane r: pull the populations of plane r (each
+// tile cell: parked in shared memory for the collision a plane later) and
+// form Q = rho u (1 - theta) of the tile and its halo ring into a 4-plane
+// ring; one barrier; collide plane r - 1.  With four planes in the ring the
+// slot written at plane r + 1 was last read by the collision of plane r - 2,
+// which every thread finished before the barrier of plane r, so one barrier
+// per plane suffices (and threads that are done with the collision go on
+// pulling the next plane while the others collide).
+template <class S, int M, int TY, bool SPLIT>
+__global__ void __launch_bounds__(threads3<TY, SPLIT>(), (step3d_min_blocks<S, TY, SPLIT>()))
     step3d_kernel(const Grid3 g, int zrows) {
   using C = typename Io<S>::C;
   constexpr int HX = TX3 + 2, HY = TY + 2, HN = HX * HY, NT = TX3 * TY;
   constexpr int NHALO = HN - NT;
-  static_assert(NHALO <= NT, "one halo cell per thread at most");
+  static_assert(NHALO == nhalo3<TY>(), "halo ring");
+  static_assert(SPLIT || NHALO <= NT, "one halo cell per thread at most");
   extern __shared__ __align__(16) unsigned char smem3[];
   C* park = reinterpret_cast<C*>(smem3);  // [2][NP3][NT]
-  C(*qs)[3][HN] = reinterpret_cast<C(*)[3][HN]>(park + 2 * NP3 * NT);  // [3][3][HN]
+  C(*qs)[3][HN] = reinterpret_cast<C(*)[3][HN]>(park + 2 * NP3 * NT);  // [4][3][HN]
 
-  const int t = threadIdx.x, tx = t % TX3, ty = t / TX3;
+  const int t = threadIdx.x;
+  const bool interior = !SPLIT || t < NT;  // owns a tile cell
+  const int hk = SPLIT ? t - NT : t;      // halo cell index, if in [0, NHALO)
+  const int tx = t % TX3, ty = t / TX3;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int x0 = blockIdx.x * TX3, y0 = blockIdx.y * TY, z0 = blockIdx.z * zrows;
   if (z0 >= nz) return;
@@ -366,20 +390,20 @@ __global__ void __launch_bounds__(TX3 * TY, (step3d_min_blocks<S, TY>()))
   // this thread's interior cell and node
   const int cell = (ty + 1) * HX + tx + 1;
   const int x = x0 + tx, y = y0 + ty;
-  const bool mine = x < nx && y < ny;
+  const bool mine = interior && x < nx && y < ny;
   const int wx = wrap3(x % nx, nx), wy = wrap3(y % ny, ny);  // wrapped (ragged tiles)
-  // halo cell of this thread (t < NHALO): the ring around the tile
+  // halo cell of this thread: the ring around the tile
   int hcell = -1, hx = 0, hy = 0;
-  if (t < NHALO) {
+  if (hk >= 0 && hk < NHALO) {
     int cx, cy;
-    if (t < HX) {
-      cx = t;
+    if (hk < HX) {
+      cx = hk;
       cy = 0;
-    } else if (t < 2 * HX) {
-      cx = t - HX;
+    } else if (hk < 2 * HX) {
+      cx = hk - HX;
       cy = HY - 1;
     } else {
-      const int k = t - 2 * HX;  // the side columns, rows 1 .. HY - 2
+      const int k = hk - 2 * HX;  // the side columns, rows 1 .. HY - 2
       cx = (k & 1) ? HX - 1 : 0;
       cy = 1 + (k >> 1);
     }
@@ -390,12 +414,11 @@ __global__ void __launch_bounds__(TX3 * TY, (step3d_min_blocks<S, TY>()))
 
   C prho = 1, pux = 0, puy = 0, puz = 0, pth = 1, pes = 0;
   for (int r = z0 - 1; r <= z1; ++r) {
-    const int s = (r - z0 + 1) % 3;
+    const int s = (r - z0 + 1) & 3;
     const int zr = wrap3(r, nz);
-    __syncthreads();  // the previous plane's collision is done with slot s
     // moments of plane r: this thread's cell (wrapped), and its halo cell
-    C crho, cux, cuy, cuz, cth, ces;
-    {
+    C crho = 1, cux = 0, cuy = 0, cuz = 0, cth = 1, ces = 0;
+    if (interior) {
       C d[NP3];
       pull3<S>(g, src, wx, wy, zr, d);
       C* pk = park + (r & 1) * NP3 * NT + t;
@@ -419,7 +442,7 @@ __global__ void __launch_bounds__(TX3 * TY, (step3d_min_blocks<S, TY>()))
     __syncthreads();
     const int zc = r - 1;  // plane to collide
     if (zc >= z0 && mine) {
-      const int sm = (s + 1) % 3, s0 = (s + 2) % 3;  // planes r - 2 and r - 1
+      const int sm = (s + 2) & 3, s0 = (s + 3) & 3;  // planes r - 2 and r - 1
       C dq[3][3];  // dq[k][j] = dQ_j / dx_k
       // across a z wall Eq. 50 takes the mirror ghost 2 Q_w - Q(node),
       // Q_w = rho u_w (1 - theta_w) (theta_w: the node's own on an adiabatic

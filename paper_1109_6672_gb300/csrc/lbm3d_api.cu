@@ -23,8 +23,10 @@ struct lbm3d_handle {
   Grid3 grid{};
   dim3 launch{};
   int zrows = 0;
-  int tile = 0;     // tile rows asked for: 0 (automatic), 8 or 16
-  int tile_rows = 8;  // tile rows in use
+  int tile = 0;       // tile rows asked for: 0 (automatic), 4, 8 or 16
+  int tile_split = 0;  // separate halo warps asked for (tile != 0)
+  int tile_rows = 8;   // tile rows in use
+  int split = 0;       // separate halo warps in use
   double* staging = nullptr;  // 5 n doubles (host transfers), later 38 n (get_state)
   size_t staging_bytes = 0;
   double* partial = nullptr;  // reduction partials + result + flag
@@ -182,26 +184,39 @@ cudaError_t aux(lbm3d_handle* h, int what, void* buf, const double* const* in, d
                           h->stream);
 }
 
-// Launch shape: 32 x TY tiles of (x, y), TY = 8 unless asked otherwise (16
-// rows, FP32 only, cut the one-node halo ring from 33 % to 20 % of a tile's
-// moments but fit one 512-thread block per SM instead of two 256-thread
-// ones: 9.2 against 10.3 GLUPS at 256^3); the z range of a block chosen so
-// that the grid is about four waves of resident blocks.
+// Launch shape: 32 x TY tiles of (x, y).  Automatic: FP64 8 rows; FP32 4
+// rows with separate halo warps (two 224-thread blocks per SM), which at
+// 256^3 ran at 11.1 GLUPS against 10.3 for 8 rows with the halo ring on the
+// tile's first threads (those threads pulled twice per plane while the rest
+// of the block waited), 9.2 for 8 rows with halo warps (one 352-thread block
+// per SM by registers) and 9.0 for 16 rows (one 512-thread block).  The z
+// range of a block is chosen so that the grid is about four waves of
+// resident blocks.
+size_t smem3(bool f64, int ty) {
+  if (f64) return step3d_smem<double, 8>();
+  return ty == 16 ? step3d_smem<float, 16>()
+                  : (ty == 4 ? step3d_smem<float, 4>() : step3d_smem<float, 8>());
+}
+int threads_of3(int ty, int split) {
+  if (!split) return TX3 * ty;
+  return ty == 4 ? threads3<4, true>() : threads3<8, true>();
+}
 void choose_launch(lbm3d_handle* h) {
   const bool f64 = h->p.precision == LBM_P_FP64;
-  h->tile_rows = f64 ? 8 : (h->tile ? h->tile : 8);
+  h->tile_rows = f64 ? 8 : (h->tile ? h->tile : 4);
+  h->split = f64 ? 0 : (h->tile ? h->tile_split : 1);
   const int TYr = h->tile_rows;
   const int tx = (h->p.nx + TX3 - 1) / TX3, ty = (h->p.ny + TYr - 1) / TYr;
   cudaFuncAttributes a{};
   const int mode = mode3_of(h->grid);
-  const cudaError_t e = f64 ? step3d_attributes_f64(mode, TYr, &a)
-                            : step3d_attributes_f32(mode, TYr, &a);
+  const cudaError_t e = f64 ? step3d_attributes_f64(mode, TYr, h->split, &a)
+                            : step3d_attributes_f32(mode, TYr, h->split, &a);
   int per_sm = 1;
-  if (e == cudaSuccess && a.numRegs > 0) per_sm = std::max(1, 65536 / (a.numRegs * TX3 * TYr));
+  if (e == cudaSuccess && a.numRegs > 0)
+    per_sm = std::max(1, 65536 / (a.numRegs * threads_of3(TYr, h->split)));
   // and by shared memory (the parked populations and the Q ring, plus the
   // 1 KB the hardware reserves per block, of 228 KB per SM)
-  const size_t smem = f64 ? step3d_smem<double, 8>()
-                          : (TYr == 16 ? step3d_smem<float, 16>() : step3d_smem<float, 8>());
+  const size_t smem = smem3(f64, TYr);
   per_sm = std::max(1, std::min(per_sm, (int)(233472 / (smem + 1024))));
   const long long resident = (long long)per_sm * std::max(1, h->num_sms);
   const long long chunks =
@@ -300,9 +315,9 @@ int lbm3d_step(lbm3d_handle* h, int64_t n) {
     g.src = buf_ptr3(h, h->cur);
     g.dst = buf_ptr3(h, h->cur ^ 1);
     const cudaError_t e = h->p.precision == LBM_P_FP64
-                              ? launch_step3d_f64(g, h->launch, h->zrows, 8, h->stream)
+                              ? launch_step3d_f64(g, h->launch, h->zrows, 8, 0, h->stream)
                               : launch_step3d_f32(g, h->launch, h->zrows, h->tile_rows,
-                                                  h->stream);
+                                                  h->split, h->stream);
     if (e != cudaSuccess) return cuda_fail3(h, e, "step kernel launch");
     h->cur ^= 1;
     ++h->steps;
@@ -381,15 +396,30 @@ int lbm3d_sync(lbm3d_handle* h) {
 
 int64_t lbm3d_steps_done(const lbm3d_handle* h) { return h ? h->steps : LBM_ERR_PARAM; }
 
+int lbm3d_set_launch(lbm3d_handle* h, int32_t tile_rows, int32_t halo_warps) {
+  if (!h) return LBM_ERR_PARAM;
+  if (tile_rows != 0) {
+    const bool f32 = h->p.precision == LBM_P_FP32;
+    const bool ok = (tile_rows == 8 && halo_warps == 0) ||
+                    (f32 && ((tile_rows == 16 && halo_warps == 0) ||
+                             ((tile_rows == 4 || tile_rows == 8) && halo_warps == 1)));
+    if (!ok)
+      return fail3(h, LBM_ERR_PARAM,
+                   "launch shapes: (8, 0); for FP32 storage also (16, 0), (4, 1), (8, 1)");
+  }
+  h->tile = tile_rows;
+  h->tile_split = tile_rows ? halo_warps : 0;
+  choose_launch(h);
+  return LBM_OK;
+}
+
 int lbm3d_set_tile(lbm3d_handle* h, int32_t tile_rows) {
   if (!h) return LBM_ERR_PARAM;
   if (tile_rows != 0 && tile_rows != 8 && tile_rows != 16)
     return fail3(h, LBM_ERR_PARAM, "tile_rows must be 0 (automatic), 8 or 16");
   if (tile_rows == 16 && h->p.precision == LBM_P_FP64)
     return fail3(h, LBM_ERR_PARAM, "16-row tiles are built for FP32 storage only");
-  h->tile = tile_rows;
-  choose_launch(h);
-  return LBM_OK;
+  return lbm3d_set_launch(h, tile_rows, 0);
 }
 
 void lbm3d_destroy(lbm3d_handle* h) {

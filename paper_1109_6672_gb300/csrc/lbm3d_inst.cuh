@@ -6,72 +6,78 @@
 
 namespace lbm3 {
 
-template <class S, int M, int TY>
+template <class S, int M, int TY, bool SPLIT>
 cudaError_t launch_tile3(const Grid3& g, dim3 grid, int zrows, cudaStream_t st) {
-  constexpr int NT = TX3 * TY;
   constexpr size_t SM = step3d_smem<S, TY>();
   static bool attr_set = false;  // per process and instantiation (one device attribute)
   if (!attr_set) {
     const cudaError_t e = cudaFuncSetAttribute(
-        step3d_kernel<S, M, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
+        step3d_kernel<S, M, TY, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  step3d_kernel<S, M, TY><<<grid, NT, SM, st>>>(g, zrows);
+  step3d_kernel<S, M, TY, SPLIT><<<grid, threads3<TY, SPLIT>(), SM, st>>>(g, zrows);
   return cudaGetLastError();
 }
 
-// 16-row tiles exist for FP32 storage only (FP64 parks twice the bytes).
+// Launch shapes (tile rows, separate halo warps): (8, no) for both
+// precisions; for FP32 storage also (16, no), (4, yes) and (8, yes).
 template <class S, int M>
-cudaError_t launch_mode3(const Grid3& g, dim3 grid, int zrows, int ty, cudaStream_t st) {
+cudaError_t launch_mode3(const Grid3& g, dim3 grid, int zrows, int ty, int split,
+                         cudaStream_t st) {
   if constexpr (sizeof(S) == 4) {
-    if (ty == 16) return launch_tile3<S, M, 16>(g, grid, zrows, st);
+    if (ty == 16) return launch_tile3<S, M, 16, false>(g, grid, zrows, st);
+    if (ty == 4 && split) return launch_tile3<S, M, 4, true>(g, grid, zrows, st);
+    if (ty == 8 && split) return launch_tile3<S, M, 8, true>(g, grid, zrows, st);
   }
-  return launch_tile3<S, M, 8>(g, grid, zrows, st);
+  return launch_tile3<S, M, 8, false>(g, grid, zrows, st);
 }
 
 template <class S>
-cudaError_t launch_step3d(const Grid3& g, dim3 grid, int zrows, int ty, cudaStream_t st) {
+cudaError_t launch_step3d(const Grid3& g, dim3 grid, int zrows, int ty, int split,
+                          cudaStream_t st) {
   switch (mode3_of(g)) {
     case M3_TOTAL | M3_ZFULL | M3_CORR:
-      return launch_mode3<S, M3_TOTAL | M3_ZFULL | M3_CORR>(g, grid, zrows, ty, st);
+      return launch_mode3<S, M3_TOTAL | M3_ZFULL | M3_CORR>(g, grid, zrows, ty, split, st);
     case M3_TOTAL | M3_ZFULL:
-      return launch_mode3<S, M3_TOTAL | M3_ZFULL>(g, grid, zrows, ty, st);
+      return launch_mode3<S, M3_TOTAL | M3_ZFULL>(g, grid, zrows, ty, split, st);
     case M3_TOTAL | M3_CORR:
-      return launch_mode3<S, M3_TOTAL | M3_CORR>(g, grid, zrows, ty, st);
+      return launch_mode3<S, M3_TOTAL | M3_CORR>(g, grid, zrows, ty, split, st);
     case M3_TOTAL:
-      return launch_mode3<S, M3_TOTAL>(g, grid, zrows, ty, st);
+      return launch_mode3<S, M3_TOTAL>(g, grid, zrows, ty, split, st);
     case M3_CORR:
-      return launch_mode3<S, M3_CORR>(g, grid, zrows, ty, st);
+      return launch_mode3<S, M3_CORR>(g, grid, zrows, ty, split, st);
     default:
-      return launch_mode3<S, 0>(g, grid, zrows, ty, st);
+      return launch_mode3<S, 0>(g, grid, zrows, ty, split, st);
   }
 }
 
-template <class S, int TY>
+template <class S, int TY, bool SPLIT>
 cudaError_t attributes3d_tile(int mode, cudaFuncAttributes* a) {
   switch (mode) {
     case M3_TOTAL | M3_ZFULL | M3_CORR:
-      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_TOTAL | M3_ZFULL | M3_CORR, TY>);
+      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_TOTAL | M3_ZFULL | M3_CORR, TY, SPLIT>);
     case M3_TOTAL | M3_ZFULL:
-      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_TOTAL | M3_ZFULL, TY>);
+      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_TOTAL | M3_ZFULL, TY, SPLIT>);
     case M3_TOTAL | M3_CORR:
-      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_TOTAL | M3_CORR, TY>);
+      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_TOTAL | M3_CORR, TY, SPLIT>);
     case M3_TOTAL:
-      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_TOTAL, TY>);
+      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_TOTAL, TY, SPLIT>);
     case M3_CORR:
-      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_CORR, TY>);
+      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_CORR, TY, SPLIT>);
     default:
-      return cudaFuncGetAttributes(a, step3d_kernel<S, 0, TY>);
+      return cudaFuncGetAttributes(a, step3d_kernel<S, 0, TY, SPLIT>);
   }
 }
 
 template <class S>
-cudaError_t attributes3d(int mode, int ty, cudaFuncAttributes* a) {
+cudaError_t attributes3d(int mode, int ty, int split, cudaFuncAttributes* a) {
   if constexpr (sizeof(S) == 4) {
-    if (ty == 16) return attributes3d_tile<S, 16>(mode, a);
+    if (ty == 16) return attributes3d_tile<S, 16, false>(mode, a);
+    if (ty == 4 && split) return attributes3d_tile<S, 4, true>(mode, a);
+    if (ty == 8 && split) return attributes3d_tile<S, 8, true>(mode, a);
   }
-  return attributes3d_tile<S, 8>(mode, a);
+  return attributes3d_tile<S, 8, false>(mode, a);
 }
 
 template <class S>

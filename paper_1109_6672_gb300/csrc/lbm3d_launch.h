@@ -19,9 +19,11 @@ inline int mode3_of(const Grid3& g) {
   return m;
 }
 
-// ty: tile rows, 8 or 16 (16 for FP32 storage only)
-cudaError_t launch_step3d_f64(const Grid3& g, dim3 grid, int zrows, int ty, cudaStream_t st);
-cudaError_t launch_step3d_f32(const Grid3& g, dim3 grid, int zrows, int ty, cudaStream_t st);
+// ty: tile rows; split: separate halo warps (launch_mode3 lists the shapes)
+cudaError_t launch_step3d_f64(const Grid3& g, dim3 grid, int zrows, int ty, int split,
+                              cudaStream_t st);
+cudaError_t launch_step3d_f32(const Grid3& g, dim3 grid, int zrows, int ty, int split,
+                              cudaStream_t st);
 cudaError_t launch_aux3d_f64(int what, const Grid3& g, void* buf, const double* const* in,
                              double* const* out, double T0, double* pops, int* flag,
                              double* partial, int blocks, cudaStream_t st);
@@ -29,8 +31,8 @@ cudaError_t launch_aux3d_f32(int what, const Grid3& g, void* buf, const double* 
                              double* const* out, double T0, double* pops, int* flag,
                              double* partial, int blocks, cudaStream_t st);
 // step kernel attributes (registers, for the resident-block count)
-cudaError_t step3d_attributes_f64(int mode, int ty, cudaFuncAttributes* attr);
-cudaError_t step3d_attributes_f32(int mode, int ty, cudaFuncAttributes* attr);
+cudaError_t step3d_attributes_f64(int mode, int ty, int split, cudaFuncAttributes* attr);
+cudaError_t step3d_attributes_f32(int mode, int ty, int split, cudaFuncAttributes* attr);
 
 enum { AUX3_INIT = 0, AUX3_EXPORT = 1, AUX3_CONSERVED = 2 };
 

@@ -50,6 +50,7 @@ def load() -> ctypes.CDLL:
             "lbm3d_sync": (ctypes.c_int, [_H]),
             "lbm3d_steps_done": (ctypes.c_int64, [_H]),
             "lbm3d_set_tile": (ctypes.c_int, [_H, ctypes.c_int32]),
+            "lbm3d_set_launch": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int32]),
             "lbm3d_destroy": (None, [_H]),
             "lbm3d_last_error": (ctypes.c_char_p, [_H]),
         }
@@ -154,6 +155,10 @@ class Lbm3d:
 
     def set_tile(self, tile_rows: int):
         _check(load().lbm3d_set_tile(self.h, int(tile_rows)), self.h)
+        return self
+
+    def set_launch(self, tile_rows: int, halo_warps: int):
+        _check(load().lbm3d_set_launch(self.h, int(tile_rows), int(halo_warps)), self.h)
         return self
 
     @property

@@ -49,28 +49,32 @@ def test_fp64_parity_3d(shape, mode):
     g.close()
 
 
-@pytest.mark.parametrize("tile", [8, 16])
+SHAPES = [(8, 0), (16, 0), (4, 1), (8, 1)]  # FP32 launch shapes (tile rows, halo warps)
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=[f"{a}x{b}" for a, b in SHAPES])
 @pytest.mark.parametrize("mode", ["total_zfull_corr", "internal_corr"])
-def test_fp32_parity_3d(mode, tile):
+def test_fp32_parity_3d(mode, shape):
     p, f = _case((37, 21, 9), mode, lbm.LBM_P_FP32)
     o = o3.Oracle3d(dict(p, precision=lbm.LBM_P_FP64)).init(*f).step(30)
-    g = Lbm3d(p).set_tile(tile).init(*f).step(30)
+    g = Lbm3d(p).set_launch(*shape).init(*f).step(30)
     assert _rel(g.pops(), o.pops()) <= 2e-5
     g.close()
 
 
 def test_fp32_tiles_agree():
-    """The two tile shapes compute the same step; they are separate template
+    """The launch shapes compute the same step; they are separate template
     instantiations, whose FMA contractions the compiler may choose
     differently, so they agree to the FP32 rounding accumulated over the
     steps (measured 1.8e-6 of the populations after 20 steps of these noisy
     fields; each is within 2e-5 of the FP64 oracle, test_fp32_parity_3d)."""
     p, f = _case((70, 33, 12), "total_zfull_corr", lbm.LBM_P_FP32)
     a = Lbm3d(p).set_tile(8).init(*f).step(20)
-    b = Lbm3d(p).set_tile(16).init(*f).step(20)
-    assert _rel(a.pops(), b.pops()) <= 1e-5
+    for shape in SHAPES[1:]:
+        b = Lbm3d(p).set_launch(*shape).init(*f).step(20)
+        assert _rel(a.pops(), b.pops()) <= 1e-5, shape
+        b.close()
     a.close()
-    b.close()
 
 
 def test_set_tile_validation():
@@ -80,6 +84,15 @@ def test_set_tile_validation():
         g.set_tile(16)
     with pytest.raises(lbm.LbmError):
         g.set_tile(12)
+    for shape in [(4, 1), (8, 1), (16, 0), (4, 0), (16, 1), (8, 2)]:
+        with pytest.raises(lbm.LbmError):
+            g.set_launch(*shape)  # FP64: (8, 0) only
+    g.set_launch(8, 0).set_launch(0, 0)
+    g.close()
+    g = Lbm3d(dict(p, precision=lbm.LBM_P_FP32))
+    for shape in [(4, 0), (16, 1), (8, 2), (12, 0)]:
+        with pytest.raises(lbm.LbmError):
+            g.set_launch(*shape)
     g.close()
 
 
@@ -142,12 +155,12 @@ def test_fp64_parity_3d_walls(shape, mode, walls):
     g.close()
 
 
-@pytest.mark.parametrize("tile", [8, 16])
-def test_fp32_parity_3d_walls(tile):
+@pytest.mark.parametrize("shape", SHAPES, ids=[f"{a}x{b}" for a, b in SHAPES])
+def test_fp32_parity_3d_walls(shape):
     p, f = _case((37, 21, 9), "total_zfull_corr", lbm.LBM_P_FP32)
     p.update(WALLS["iso_moving"])
     o = o3.Oracle3d(dict(p, precision=lbm.LBM_P_FP64)).init(*f).step(30)
-    g = Lbm3d(p).set_tile(tile).init(*f).step(30)
+    g = Lbm3d(p).set_launch(*shape).init(*f).step(30)
     assert _rel(g.pops(), o.pops()) <= 2e-5
     g.close()
 
