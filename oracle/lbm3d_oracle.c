@@ -44,6 +44,12 @@
  * on an adiabatic wall): D is linear in Q = rho u (1 - theta), so this is
  * the D2Q9 oracle's mirror ghost Q_g = 2 Q_w - Q.
  *
+ * Parity unpinned, in part: the -u^2/2 part of Z_a in the Eq. 36 coupling
+ * (the full Z form).  No closed form or decay rate the paper fixes depends
+ * on it (Z_a reduces to e_a.u at the Navier-Stokes level); it is checked
+ * only against an independent NumPy restatement of the step
+ * (tests/brute_lbm3d.py), which also restates the z walls.
+ *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
  * load this file; only the tests, the smoke check and the benchmark's CPU
  * baseline do.  It shares no code, header, table or constant with the CUDA

@@ -1,0 +1,234 @@
+"""Independent NumPy restatement of one step of the D3Q19 extension of the
+coupled DDF scheme (arXiv:1109.6672, Sec. III.C.1 with D = 3), used only to
+cross-check the C oracle (oracle/lbm3d_oracle.c) on tiny grids.  It is written
+separately from the oracle and takes different routes to the same quantities:
+
+* Eq. 18a and Eq. 18b are expanded per speed shell (rest, axis, face
+  diagonal) by hand, with R T0 = 1/3, instead of being evaluated from the
+  generic Hermite forms;
+* the deviation of the third-order moment is written out (D_iii = Q_i,
+  D_iik = D_iki = D_kii = Q_k / 6 for i != k, zero with three distinct
+  indices, Q = rho u (1 - theta)) instead of being summed over the lattice,
+  and the correction's second-moment conditions are solved in closed form
+  (A_kk = (G_kk + 4/7 tr G) / 6, A_ij = G_ij / 8, kappa = 10/19) instead of
+  by elimination;
+* moments are array contractions; streaming is pull-based (np.roll); the
+  z walls are applied on the pull, from the receiving node's side.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# the population order of the C ABI and of the oracle
+E = np.array([(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+              (1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 0, 1), (-1, 0, -1), (1, 0, -1),
+              (-1, 0, 1), (0, 1, 1), (0, -1, -1), (0, 1, -1), (0, -1, 1)])
+E2 = (E * E).sum(1)
+W = np.where(E2 == 0, 1 / 3, np.where(E2 == 1, 1 / 18, 1 / 36))
+OPP = np.array([int(np.flatnonzero((E == -e).all(1))[0]) for e in E])
+PERIODIC, ISO, ADIA = 0, 1, 2
+KAPPA = 10.0 / 19.0
+
+
+def feq_shells(rho, u, th):
+    """Eq. 18a, D = 3, R T0 = 1/3, per shell (u: [3, ...]):
+    rest  rho/3  [1 - 3/2 u^2 - 3/2 (th - 1)]
+    axis  rho/18 [1 + (6 - 3 th) eu + 9/2 eu^2 - 3/2 u^2]
+    diag  rho/36 [1 + (3/2 + 3/2 th) eu + 9/2 eu^2 - 3/2 u^2 + 3/2 (th - 1)]"""
+    usq = (u * u).sum(0)
+    out = []
+    for a in range(19):
+        eu = E[a, 0] * u[0] + E[a, 1] * u[1] + E[a, 2] * u[2]
+        if E2[a] == 0:
+            t = 1 - 1.5 * usq - 1.5 * (th - 1)
+        elif E2[a] == 1:
+            t = 1 + (6 - 3 * th) * eu + 4.5 * eu * eu - 1.5 * usq
+        else:
+            t = 1 + (1.5 + 1.5 * th) * eu + 4.5 * eu * eu - 1.5 * usq + 1.5 * (th - 1)
+        out.append(rho * W[a] * t)
+    return np.array(out)
+
+
+def heq_total(rho, u, th, b, f):
+    """Eq. 18b, D = 3, R T0 = 1/3, per shell: h = E f + w p B with p = rho th / 3,
+    E = b th / 6 + u^2 / 2 and
+    rest  B = -3 u^2 - 3/2 th
+    axis  B = 3 eu + 9 eu^2 - 3 u^2
+    diag  B = 3 eu + 9 eu^2 - 3 u^2 + 3/2 th"""
+    usq = (u * u).sum(0)
+    En = b * th / 6 + 0.5 * usq
+    p = rho * th / 3
+    out = []
+    for a in range(19):
+        eu = E[a, 0] * u[0] + E[a, 1] * u[1] + E[a, 2] * u[2]
+        if E2[a] == 0:
+            B = -3 * usq - 1.5 * th
+        elif E2[a] == 1:
+            B = 3 * eu + 9 * eu * eu - 3 * usq
+        else:
+            B = 3 * eu + 9 * eu * eu - 3 * usq + 1.5 * th
+        out.append(En * f[a] + W[a] * p * B)
+    return np.array(out)
+
+
+def heq_internal(th, b, f):
+    """The internal-energy form under Eq. 38: b R T f / 2 = b th f / 6."""
+    return b * th / 6 * f
+
+
+def correction(dQ):
+    """C_a from dQ[k, j] = dQ_j/dx_k (arrays over the grid): G_ij =
+    sum_k dD_ijk/dx_k with the D above, then the closed-form A."""
+    G = np.zeros((3, 3) + dQ.shape[2:])
+    for i in range(3):
+        for j in range(3):
+            for k in range(3):
+                if i == j == k:
+                    Dc = dQ[k, i]  # dD_iii/dx_i = dQ_i/dx_i
+                elif i == j:
+                    Dc = dQ[k, k] / 6 if k != i else 0  # D_iik = Q_k / 6
+                elif i == k:
+                    Dc = dQ[k, j] / 6  # D_iji = Q_j / 6
+                elif j == k:
+                    Dc = dQ[k, i] / 6  # D_ijj = Q_i / 6
+                else:
+                    Dc = 0
+                G[i, j] = G[i, j] + Dc
+    tr = G[0, 0] + G[1, 1] + G[2, 2]
+    A = np.zeros_like(G)
+    for i in range(3):
+        A[i, i] = (G[i, i] + 4.0 / 7.0 * tr) / 6
+        for j in range(3):
+            if j != i:
+                A[i, j] = 0.5 * (G[i, j] + G[j, i]) / 8
+    trA = A[0, 0] + A[1, 1] + A[2, 2]
+    C = []
+    for a in range(19):
+        c = -KAPPA * trA
+        for i in range(3):
+            for j in range(3):
+                c = c + A[i, j] * E[a, i] * E[a, j]
+        C.append(c)
+    return np.array(C)
+
+
+class Brute3d:
+    """Arrays [nz, ny, nx]; parameters as the oracle's dictionary."""
+
+    def __init__(self, p: dict):
+        self.p = dict(p)
+        self.shape = (int(p["nz"]), int(p["ny"]), int(p["nx"]))
+        self.total = int(p.get("energy_model", 0)) == 0
+        self.bc = list(p.get("bc_z", [PERIODIC, PERIODIC]))
+        self.uw = np.array(p.get("u_wall_z", [[0.0] * 3, [0.0] * 3]), dtype=float)
+        self.thw = np.array(p.get("T_wall_z", [1.0, 1.0]), dtype=float) / p["T0"]
+
+    def _eq(self, rho, u, th):
+        f = feq_shells(rho, u, th)
+        h = heq_total(rho, u, th, self.p["b"], f) if self.total else heq_internal(th, self.p["b"], f)
+        return f, h
+
+    def init(self, rho, ux, uy, uz, T):
+        rho, ux, uy, uz, T = [np.broadcast_to(np.asarray(v, float), self.shape).copy()
+                              for v in (rho, ux, uy, uz, T)]
+        self.F, self.H = self._eq(rho, np.array([ux, uy, uz]), T / self.p["T0"])
+        return self
+
+    def moments(self):
+        rho = self.F.sum(0)
+        u = np.tensordot(E.T.astype(float), self.F, axes=(1, 0)) / rho
+        es = self.H.sum(0) / rho
+        if self.total:
+            th = 6 / self.p["b"] * (es - 0.5 * (u * u).sum(0))
+        else:
+            th = 6 / self.p["b"] * es
+        return rho, u, th
+
+    def pops(self):
+        return np.concatenate([self.F, self.H], 0)
+
+    def _grad(self, Q, rho, th):
+        """dQ[k, j] = dQ_j / dx_k by central differences; across a z wall the
+        mirror ghost 2 rho u_w (1 - theta_w) - Q (theta_w: the node's own on
+        an adiabatic wall)."""
+        dQ = np.zeros((3,) + Q.shape)
+        for k, ax in ((0, 2), (1, 1), (2, 0)):
+            up = np.roll(Q, -1, axis=1 + ax)
+            dn = np.roll(Q, 1, axis=1 + ax)
+            if k == 2:
+                for side, sl in ((0, 0), (1, -1)):
+                    if self.bc[side] == PERIODIC:
+                        continue
+                    thw = self.thw[side] if self.bc[side] == ISO else th[sl]
+                    ghost = 2 * rho[sl] * self.uw[side][:, None, None] * (1 - thw) - Q[:, sl]
+                    if side == 0:
+                        dn[:, 0] = ghost
+                    else:
+                        up[:, -1] = ghost
+            dQ[k] = 0.5 * (up - dn)
+        return dQ
+
+    def step(self, n: int = 1):
+        for _ in range(n):
+            self._step()
+        return self
+
+    def _step(self):
+        p = self.p
+        wf = 2 / (2 * p["tau_f"] + 1)
+        wh = 2 / (2 * p["tau_h"] + 1)
+        rho, u, th = self.moments()
+        if int(p.get("correction", 1)):
+            C = correction(self._grad(rho * u * (1 - th), rho, th))
+        else:
+            C = np.zeros_like(self.F)
+        feq, heq = self._eq(rho, u, th)
+        # Eq. 37 / Eq. 38: h^eq from the node's own energy (sum h = rho E)
+        es = self.H.sum(0) / rho
+        if self.total:
+            f = feq_shells(rho, u, th)
+            usq = (u * u).sum(0)
+            heq = heq_total(rho, u, th, p["b"], f) + (es - (p["b"] * th / 6 + 0.5 * usq)) * f
+        fneq = self.F - feq
+        fs = self.F - wf * fneq + (1 - 0.5 * wf) * C
+        hs = self.H - wh * (self.H - heq)
+        if self.total:
+            usq = (u * u).sum(0)
+            for a in range(19):
+                eu = E[a, 0] * u[0] + E[a, 1] * u[1] + E[a, 2] * u[2]
+                Z = eu - 0.5 * usq if int(p.get("z_full", 1)) else eu
+                hs[a] = hs[a] + (wh - wf) * Z * (fneq[a] + 0.5 * C[a])
+        # pull streaming (periodic), then the populations that came through
+        # a z wall replaced from the receiving node's side
+        Fn = np.empty_like(fs)
+        Hn = np.empty_like(hs)
+        for a in range(19):
+            sh = (E[a, 2], E[a, 1], E[a, 0])
+            Fn[a] = np.roll(fs[a], sh, axis=(0, 1, 2))
+            Hn[a] = np.roll(hs[a], sh, axis=(0, 1, 2))
+        nz = self.shape[0]
+        for b in range(19):
+            if E[b, 2] == 0:
+                continue
+            side = 0 if E[b, 2] > 0 else 1  # b arrives at z = 0 from below, or at nz - 1
+            if self.bc[side] == PERIODIC:
+                continue
+            z = 0 if side == 0 else nz - 1
+            a = OPP[b]  # what left the node through the wall
+            r, t = rho[z], th[z]
+            uw = self.uw[side][:, None, None] * np.ones((1,) + r.shape)
+            fw, hw = self._eq(r, uw, t)  # the node's rho, theta and the wall velocity
+            Fn[b, z] = fs[a, z] + (fw[b] - fw[a])
+            if self.bc[side] == ISO:
+                tg = np.maximum(2 * self.thw[side] - t, 0.5 * self.thw[side])
+                rg = r * t / tg
+                ug = 2 * uw - u[:, z]
+                fg, hg = self._eq(rg, ug, tg)
+                Hn[b, z] = hg[b] + (hs[b, z] - heq[b, z])
+            else:
+                hin = hs[a, z] + (hw[b] - hw[a])
+                if self.total:  # the moving wall's work on the pair
+                    ea_uw = E[a, 0] * uw[0] + E[a, 1] * uw[1] + E[a, 2] * uw[2]
+                    hin = hin - ea_uw * (Fn[b, z] + fs[a, z])
+                Hn[b, z] = hin
+        self.F, self.H = Fn, Hn
