@@ -33,8 +33,9 @@
  *         the boundary node's rho and theta and the wall velocity;
  *      h, isothermal wall: non-equilibrium extrapolation from a ghost node one
  *         spacing outside, with u_g = 2 u_w - u, theta_g = max(2 theta_w - theta,
- *         theta_w / 2),
- *         rho_g = rho theta / theta_g;
+ *         theta_w / 2) and the node's pressure carried to the ghost by
+ *         hydrostatic balance, rho_g theta_g = rho (theta - 3 g n_y), n_y the
+ *         wall's outward normal (0 on x walls);
  *      h, adiabatic wall: bounce-back plus twice the odd part of h^eq at the
  *         boundary node's (rho, theta) and the wall velocity, for total energy
  *         plus the wall's work on the bounced pair u_w . (f_b e_b - f*_a e_a)

@@ -44,6 +44,10 @@
  * on an adiabatic wall): D is linear in Q = rho u (1 - theta), so this is
  * the D2Q9 oracle's mirror ghost Q_g = 2 Q_w - Q.
  *
+ * Gravity along -z (g > 0, the internal-energy model, as the paper's cavity
+ * runs it): Guo's force term of Eq. 51 carried to D = 3 enters beside C_a,
+ * and the velocity carries the half-force shift of the text under Eq. 51.
+ *
  * Parity unpinned, in part: the -u^2/2 part of Z_a in the Eq. 36 coupling
  * (the full Z form).  No closed form or decay rate the paper fixes depends
  * on it (Z_a reduces to e_a.u at the Navier-Stokes level); it is checked
@@ -92,6 +96,7 @@ typedef struct {
   int32_t bc_z[2];      /* sides z- and z+: O3_PERIODIC or a wall */
   double u_wall_z[2][3];
   double T_wall_z[2];
+  double g;             /* gravity along -z: force density a = (0, 0, -rho g) */
 } o3_params;
 
 typedef struct {
@@ -301,6 +306,8 @@ static void node_moments(const o3_state* s, long i, double* rho, double u[3], do
     for (int d = 0; d < 3; ++d) j[d] += E3[a][d] * s->f[a][i];
     sh += s->h[a][i];
   }
+  /* Eq. 35 with the half-force shift (under Eq. 51): rho u = sum e f + a / 2 */
+  j[2] -= 0.5 * r * p->g;
   for (int d = 0; d < 3; ++d) u[d] = j[d] / r;
   double T;
   if (p->energy_model == O3_E_TOTAL)
@@ -431,6 +438,16 @@ static void phase2(o3_state* s, int nthreads) {
           double G[9];
           node_G(s, x, y, z, G);
           o3_correction(G, C);
+        }
+        if (p->g != 0.0) {
+          /* Guo's force term, entering with C (Eq. 51 carried to D = 3):
+           * F_a = w_a [(e_a - u).a / RT0 + (e_a.u)(e_a.a) / RT0^2] */
+          const double az = -rho * p->g;
+          for (int a = 0; a < Q3; ++a) {
+            const double eu = E3[a][0] * u[0] + E3[a][1] * u[1] + E3[a][2] * u[2];
+            const double ea = E3[a][2] * az;
+            C[a] += weight3(a) * ((ea - u[2] * az) / RT0 + eu * ea / (RT0 * RT0));
+          }
         }
         double feq[Q3], heq[Q3], fs[Q3], hs[Q3];
         equilibria(p, rho, u, th, s->es[i], feq, heq);

@@ -45,8 +45,11 @@
  *   - h on isothermal walls: non-equilibrium extrapolation (the paper's wall
  *     method, ref. [45]) from a ghost node one spacing outside the node, with
  *     u_g = 2 u_w - u, theta_g = 2 theta_w - theta (linear through the wall
- *     value at the halfway point), floored at theta_w / 2, and
- *     rho_g = rho theta / theta_g (equal pressure across the wall):
+ *     value at the halfway point), floored at theta_w / 2, and the node's
+ *     pressure carried to the ghost by hydrostatic balance, rho_g theta_g =
+ *     rho (theta - 3 g n_y), n_y the wall's outward normal (equal pressure
+ *     across an x wall, or without gravity; without the hydrostatic term a
+ *     floor or ceiling under gravity sat g / (2 R) off its temperature):
  *     h_in = h^eq(ghost) + (h* - h^eq)(node);
  *   - h on adiabatic walls: bounce-back plus twice the odd part of h^eq at
  *     (rho, u_w, theta) of the node (zero total-energy flux through a wall at
@@ -608,7 +611,8 @@ static void phase2(orc_state* s, int nthreads) {
            * the ghost a vanishing or negative temperature, where the
            * equal-pressure ghost density diverges */
           double thg = iso ? fmax(2.0 * thw - th, 0.5 * thw) : th;
-          double rg = iso ? rho * th / thg : rho;
+          const int nyo = side == 2 ? -1 : (side == 3 ? 1 : 0);
+          double rg = iso ? rho * (th - 3.0 * p->g * nyo) / thg : rho;
           double ugx = iso ? 2.0 * uwx - ux : uwx;
           double ugy = iso ? 2.0 * uwy - uy : uwy;
           double fg[9];

@@ -41,6 +41,7 @@ class O3Params(ctypes.Structure):
         ("bc_z", ctypes.c_int32 * 2),
         ("u_wall_z", (ctypes.c_double * 3) * 2),
         ("T_wall_z", ctypes.c_double * 2),
+        ("g", ctypes.c_double),
     ]
 
 
@@ -108,6 +109,7 @@ def make_params(p: dict) -> O3Params:
     o.z_full = int(p.get("z_full", 1))
     o.tau_f, o.tau_h = float(p["tau_f"]), float(p["tau_h"])
     o.R, o.T0, o.b = float(p["R"]), float(p["T0"]), float(p["b"])
+    o.g = float(p.get("g", 0.0))
     for k in range(2):
         o.bc_z[k] = int(p.get("bc_z", [0, 0])[k])
         o.T_wall_z[k] = float(p.get("T_wall_z", [1.0, 1.0])[k])

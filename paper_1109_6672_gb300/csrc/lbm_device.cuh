@@ -458,7 +458,11 @@ __device__ void wall_equilibria(const Grid& g, int side, C rho, C ux, C uy, C th
   equilibria<C>(rho, uwx, uwy, th, k.b6, total, fw, tmp);
   if (g.bc[side] == BC_ISO) {
     const C thg = fmax(C(2) * k.thw[side] - th, C(0.5) * k.thw[side]);  // floored: see xedge_one
-    const C rg = rho * th / thg;
+    // the node's pressure carried to the ghost by hydrostatic balance
+    // (rho_g theta_g = rho (theta - 3 g n_y), n_y the outward normal of a y
+    // side; equal pressure across an x side)
+    const int ny_out = side == 2 ? -1 : (side == 3 ? 1 : 0);
+    const C rg = rho * (th - C(3) * k.g * C(ny_out)) / thg;
     equilibria<C>(rg, C(2) * uwx - ux, C(2) * uwy - uy, thg, k.b6, total, tmp, hw);
   } else {
     for (int a = 0; a < 9; ++a) hw[a] = tmp[a];

@@ -282,9 +282,12 @@ class Brute:
                     Fn[a, y, x] = fs[o, y, x] + (fw[a] - fw[o])
                     if iso:
                         # ghost node one spacing outside: linear in u and theta
-                        # through the wall, equal pressure
+                        # through the wall; its pressure the node's less the
+                        # hydrostatic drop over the spacing (y sides)
                         tg = max(2 * thw - t, 0.5 * thw)
-                        rg, ugx, ugy = r * t / tg, 2 * uw[0] - ux[y, x], 2 * uw[1] - uy[y, x]
+                        ny_out = [0, 0, -1, 1][side]
+                        rg = r * (t - 3 * p["g"] * ny_out) / tg
+                        ugx, ugy = 2 * uw[0] - ux[y, x], 2 * uw[1] - uy[y, x]
                         fg = feq_shells(rg, ugx, ugy, tg)
                         hg = (heq_total(rg, ugx, ugy, tg, p["b"], fg) if p["energy_model"] == 0
                               else heq_internal(tg, p["b"], fg))

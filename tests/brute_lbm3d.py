@@ -13,7 +13,8 @@ separately from the oracle and takes different routes to the same quantities:
   (A_kk = (G_kk + 4/7 tr G) / 6, A_ij = G_ij / 8, kappa = 10/19) instead of
   by elimination;
 * moments are array contractions; streaming is pull-based (np.roll); the
-  z walls are applied on the pull, from the receiving node's side.
+  z walls are applied on the pull, from the receiving node's side;
+* gravity along -z: Guo's force term with the half-force velocity shift.
 """
 from __future__ import annotations
 
@@ -136,7 +137,9 @@ class Brute3d:
 
     def moments(self):
         rho = self.F.sum(0)
-        u = np.tensordot(E.T.astype(float), self.F, axes=(1, 0)) / rho
+        j = np.tensordot(E.T.astype(float), self.F, axes=(1, 0))
+        j[2] = j[2] - 0.5 * rho * float(self.p.get("g", 0.0))  # half the force a = -rho g e_z
+        u = j / rho
         es = self.H.sum(0) / rho
         if self.total:
             th = 6 / self.p["b"] * (es - 0.5 * (u * u).sum(0))
@@ -182,6 +185,14 @@ class Brute3d:
             C = correction(self._grad(rho * u * (1 - th), rho, th))
         else:
             C = np.zeros_like(self.F)
+        g = float(p.get("g", 0.0))
+        if g:
+            # Guo's force term with cs^2 = 1/3, a = (0, 0, -rho g):
+            # w [3 (e - u).a + 9 (e.u)(e.a)]
+            az = -rho * g
+            for a in range(19):
+                eu = E[a, 0] * u[0] + E[a, 1] * u[1] + E[a, 2] * u[2]
+                C[a] = C[a] + W[a] * (3 * (E[a, 2] - u[2]) * az + 9 * eu * E[a, 2] * az)
         feq, heq = self._eq(rho, u, th)
         # Eq. 37 / Eq. 38: h^eq from the node's own energy (sum h = rho E)
         es = self.H.sum(0) / rho

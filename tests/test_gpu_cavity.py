@@ -146,7 +146,7 @@ def test_rayleigh_benard_onset_gpu():
     """The Rayleigh-Benard onset on the CUDA path (FP64) at a fourth of the
     oracle test's stratification (H = 64, g H / (R T0) = 0.014): growth
     rates at 0.95, 1.0 and 1.05 Ra_c interpolate to Ra_c = 1707.76 within
-    1.5 % (measured 0.45 %; the oracle pin at H = 32 brackets it)."""
+    1 % (the oracle pin at H = 32 brackets it)."""
     from test_oracle_convection import RA_C, growth_rate, rb_case
 
     H = 64
@@ -159,4 +159,4 @@ def test_rayleigh_benard_onset_gpu():
     r = sorted(rates)
     slope, icpt = np.polyfit(r, [rates[k] for k in r], 1)
     assert slope > 0, rates
-    assert abs(-icpt / slope - 1.0) < 0.015, (rates, -icpt / slope * RA_C)
+    assert abs(-icpt / slope - 1.0) < 0.01, (rates, -icpt / slope * RA_C)

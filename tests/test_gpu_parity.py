@@ -46,6 +46,9 @@ CASES = {
                             energy_model=inputs.E_INTERNAL, b=5.0,
                             u_wall=[[0, 0.01], [0, -0.02], [0.03, 0], [-0.02, 0.01]]),
                        (0.02, 0.03, 0.02)),
+    "gravity_iso_floor_ceiling": (dict(nx=70, ny=33, bc=[P, P, ISO, ISO], T_wall=[1, 1, 1.05, 0.95],
+                                       energy_model=inputs.E_INTERNAL, b=5.0, g=1e-3),
+                                  (0.02, 0.03, 0.02)),
     "narrow_periodic_4x33": (dict(nx=4, ny=33, bc=[P] * 4), (0.02, 0.05, 0.02)),
     "single_column_1x20": (dict(nx=1, ny=20, bc=[P] * 4), (0.02, 0.05, 0.02)),
     "min_walls_3x3": (dict(nx=3, ny=3, bc=[ISO, ISO, ADI, ADI], T_wall=[1.05, 0.95, 1, 1],

@@ -410,3 +410,73 @@ def test_isothermal_walls_conduct_3d():
     eta = (np.arange(H) + 0.5) / H
     assert np.abs(T[:, 0, 0] - (1.05 - 0.1 * eta)).max() < 1e-3 * 0.1
     assert max(np.abs(ux).max(), np.abs(uy).max(), np.abs(uz).max()) < 1e-8
+
+
+# ---- gravity along -z (Guo's force term, internal-energy model) ---------------
+
+def test_gravity_momentum_input_3d():
+    """Periodic box under gravity: the force adds -rho g per node and step to
+    the z momentum (sum e f), exactly, and nothing to x, y or the mass."""
+    g = 1e-3
+    p = inputs.base_params3d(5, 4, 6, b=5.0, energy_model=inputs.E_INTERNAL, g=g)
+    f = inputs.uniform_fields3d(5, 4, 6, seed=3, u_amp=0.02, T_amp=0.03, rho_amp=0.02)
+    o = o3.Oracle3d(p).init(*f)
+    c0 = o.conserved()
+    o.step(50)
+    c1 = o.conserved()
+    assert abs(c1[0] - c0[0]) <= 1e-13 * c0[0]
+    assert abs(c1[1] - c0[1]) < 1e-12 and abs(c1[2] - c0[2]) < 1e-12
+    assert c1[3] - c0[3] == pytest.approx(-50 * g * c0[0], rel=1e-10)
+
+
+def test_hydrostatic_balance_3d():
+    """A closed box between isothermal walls at T0 under gravity settles to
+    rest with dp/dz = -rho g (p = rho R T): the central difference of p over
+    two spacings matches -rho g to the discretisation of an exponential
+    profile ((3 g)^2 / 6 relative) and the velocity vanishes."""
+    g, H = 1e-3, 16
+    p = inputs.base_params3d(2, 2, H, tau_f=0.3, tau_h=0.4, b=5.0, g=g,
+                             energy_model=inputs.E_INTERNAL,
+                             bc_z=[o3.WALL_ISOTHERMAL, o3.WALL_ISOTHERMAL])
+    o = o3.Oracle3d(p).init(*inputs.uniform_fields3d(2, 2, H, seed=0)).step(20000, threads=4)
+    rho, ux, uy, uz, T = o.moments()
+    assert max(np.abs(ux).max(), np.abs(uy).max(), np.abs(uz).max()) < 1e-9
+    pr = rho[:, 0, 0] * T[:, 0, 0] * RT0
+    dp = 0.5 * (pr[2:] - pr[:-2])
+    assert np.abs(dp + rho[1:-1, 0, 0] * g).max() < 1e-4 * g
+
+
+def _rb_growth_3d(ratio, H=32, dT=0.05, tau_f=0.06, Pr=0.71, steps=60000, chunks=30):
+    """The Rayleigh-Benard roll of test_oracle_convection.py in the D3Q19
+    oracle (rolls along y, two nodes deep): sigma H^2 / chi."""
+    nx, nu = 2 * H, tau_f * RT0
+    chi = nu / Pr
+    g = ratio * 1707.76 * nu * chi / (dT * H ** 3)
+    p = inputs.base_params3d(nx, 2, H, tau_f=tau_f, tau_h=tau_f / Pr, b=5.0, g=g,
+                             energy_model=inputs.E_INTERNAL,
+                             bc_z=[o3.WALL_ISOTHERMAL, o3.WALL_ISOTHERMAL],
+                             T_wall_z=[1 + dT / 2, 1 - dT / 2])
+    z = (np.arange(H) + 0.5) / H
+    x = np.arange(nx)
+    T = (1 + dT / 2 - dT * z)[:, None, None] + 1e-3 * dT * (
+        np.sin(math.pi * z)[:, None, None] * np.sin(2 * math.pi * x / nx)[None, None, :])
+    T = T * np.ones((H, 2, nx))
+    rho = np.exp(-3 * g * (np.arange(H) - H / 2))[:, None, None] * np.ones((H, 2, nx))
+    o = o3.Oracle3d(p).init(rho, 0.0, 0.0, 0.0, T)
+    every = steps // chunks
+    E = []
+    for _ in range(chunks):
+        o.step(every, threads=8)
+        E.append(float((o.moments()[3] ** 2).sum()))
+    t = (np.arange(chunks) + 1) * every
+    h = chunks // 2
+    return np.polyfit(t[h:], 0.5 * np.log(np.array(E[h:])), 1)[0] * H * H / chi
+
+
+@pytest.mark.parametrize("ratio,grows", [(0.9, False), (1.15, True)])
+def test_rayleigh_benard_onset_3d(ratio, grows):
+    """Ra_c = 1707.76 (linear stability, rigid isothermal walls): the D3Q19
+    step with gravity and the z walls damps a roll below the onset and
+    amplifies it above (the D2Q9 oracle's pin, test_oracle_convection.py)."""
+    s = _rb_growth_3d(ratio)
+    assert (s > 0.2) if grows else (s < -0.2), s

@@ -21,6 +21,9 @@ CASES = {
     "iso_adiabatic_internal": dict(bc_z=[1, 2], energy_model=inputs.E_INTERNAL,
                                    u_wall_z=[[0.0, 0.0, 0.0], [0.04, 0.0, 0.0]],
                                    T_wall_z=[1.05, 1.0]),
+    "gravity_walls_internal": dict(bc_z=[1, 1], energy_model=inputs.E_INTERNAL, g=2e-3,
+                                   T_wall_z=[1.05, 0.97]),
+    "gravity_periodic_internal": dict(energy_model=inputs.E_INTERNAL, g=2e-3, correction=0),
 }
 
 

@@ -3,6 +3,8 @@ against the velocity set, the BGK scheme it reduces to, an independent NumPy
 restatement, conservation, and the shear-wave closed form."""
 import math
 
+import zlib
+
 import numpy as np
 import pytest
 
@@ -42,7 +44,7 @@ def test_uniform_rates_reduce_to_bgk(name):
     BGK (w_h - w_f)."""
     kw = dict(TINY[name])
     p = inputs.base_params(kw.pop("nx"), kw.pop("ny"), tau_f=0.35, tau_h=0.6, **kw)
-    fields = _fields(p["nx"], p["ny"], seed=hash(name) % 1000)
+    fields = _fields(p["nx"], p["ny"], seed=zlib.crc32(name.encode()) % 1000)
     bgk = orc.Oracle(p).init(*fields).step(40)
     mrt = orc.Oracle(dict(p, collision=orc.MRT)).init(*fields).step(40)
     np.testing.assert_allclose(mrt.pops(), bgk.pops(), rtol=1e-12, atol=1e-14)
@@ -52,7 +54,7 @@ def test_uniform_rates_reduce_to_bgk(name):
 def test_mrt_matches_bruteforce(name):
     kw = dict(TINY[name])
     p = inputs.base_params(kw.pop("nx"), kw.pop("ny"), tau_f=0.35, tau_h=0.6, **kw, **MRT_RATES)
-    fields = _fields(p["nx"], p["ny"], seed=hash(name) % 1000 + 7)
+    fields = _fields(p["nx"], p["ny"], seed=zlib.crc32(name.encode()) % 1000 + 7)
     o = orc.Oracle(p).init(*fields)
     b = Brute(p).init(*fields)
     for _ in range(4):

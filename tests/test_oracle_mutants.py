@@ -94,6 +94,11 @@ MUTANTS = [
      "if (0)\n            s->hn[b][i] += uwx",
      "adiabatic halfway wall: the moving wall's work dropped",
      ["test_oracle_physics.py::test_couette_adiabatic_moving_wall"]),
+    ("iso_ghost_equal_pressure",
+     "double rg = iso ? rho * (th - 3.0 * p->g * nyo) / thg : rho;",
+     "double rg = iso ? rho * th / thg : rho;",
+     "isothermal floor or ceiling under gravity: the ghost without the hydrostatic drop",
+     ["test_oracle_convection.py"]),
     ("nee_adiabatic_removes_work", "qn += en * ((hb[a] - heq[a]) - Zw * (fb[a] - feq[a]));",
      "qn += en * (hb[a] - heq[a]);",
      "adiabatic non-equilibrium wall: the viscous work taken out with the heat flux",
