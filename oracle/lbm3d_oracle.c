@@ -31,8 +31,10 @@
  * opposite, f_b(node, t+1) = f*_a - 2 (odd part of f^eq_a at the node's rho
  * and theta and the wall velocity); h on an isothermal wall by the
  * equilibrium of a ghost node one spacing outside (u_g = 2 u_w - u,
- * theta_g = max(2 theta_w - theta, theta_w / 2), rho_g = rho theta /
- * theta_g) plus the node's own non-equilibrium part, h_b = h^eq_b(ghost) +
+ * theta_g = max(2 theta_w - theta, theta_w / 2), rho_g theta_g =
+ * rho (theta - 3 g n_z), the node's pressure carried across by hydrostatic
+ * balance, n_z the wall's outward normal) plus the node's own
+ * non-equilibrium part, h_b = h^eq_b(ghost) +
  * (h*_b - h^eq_b)(node); h on an adiabatic wall h_b = h*_a - 2 (odd part of
  * h^eq_a at (rho, u_w, theta)), for total energy plus the work of the wall
  * on the pair, u_w . (f_b e_b - f*_a e_a) (the energy a moving wall gives
@@ -397,7 +399,9 @@ static void wall_bounce(const o3_params* p, int a, double rho, const double u[3]
     const double thw = p->T_wall_z[side] / p->T0;
     double thg = 2.0 * thw - th;
     if (thg < 0.5 * thw) thg = 0.5 * thw;
-    const double rg = rho * th / thg;
+    /* the node's pressure carried to the ghost by hydrostatic balance */
+    const double nz_out = side == 0 ? -1.0 : 1.0;
+    const double rg = rho * (th - 3.0 * p->g * nz_out) / thg;
     double ug[3], fg[Q3], hg[Q3];
     for (int d = 0; d < 3; ++d) ug[d] = 2.0 * uw[d] - u[d];
     double Eg = 0.5 * (p->b * RT0 * thg + ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2]);

@@ -232,7 +232,8 @@ class Brute3d:
             Fn[b, z] = fs[a, z] + (fw[b] - fw[a])
             if self.bc[side] == ISO:
                 tg = np.maximum(2 * self.thw[side] - t, 0.5 * self.thw[side])
-                rg = r * t / tg
+                # the node's pressure, less the hydrostatic drop to the ghost
+                rg = r * (t - 3 * float(p.get("g", 0.0)) * (-1 if side == 0 else 1)) / tg
                 ug = 2 * uw - u[:, z]
                 fg, hg = self._eq(rg, ug, tg)
                 Hn[b, z] = hg[b] + (hs[b, z] - heq[b, z])
