@@ -20,6 +20,8 @@
  *     Eq. 49);
  *   - time step: Eq. 34 (with +(1 - omega_f/2) C_a) and Eq. 36 / Eq. 38;
  *     moments Eq. 35 and Eq. 37;
+ *   - gravity along -z (g, internal-energy model): Guo's force term of
+ *     Eq. 51 with D = 3 beside C_a and the half-force shift of u;
  *   - z walls (not in the paper, which uses non-equilibrium extrapolation;
  *     the rules of lbm.h carried to D3Q19), halfway at z = -1/2 and
  *     nz - 1/2: a population a leaving through the wall comes back as its
@@ -27,7 +29,9 @@
  *     and theta and the wall velocity); h on an isothermal wall
  *     h_b = h^eq_b(ghost) + (h*_b - h^eq_b) with the ghost one spacing
  *     outside at u_g = 2 u_w - u, theta_g = max(2 theta_w - theta,
- *     theta_w / 2), rho_g = rho theta / theta_g; h on an adiabatic wall
+ *     theta_w / 2), rho_g theta_g = rho (theta - 3 g n_z) (the node's
+ *     pressure carried across by hydrostatic balance, n_z the outward
+ *     normal); h on an adiabatic wall
  *     h_b = h*_a - 2 (odd part of h^eq_a at (rho, u_w, theta)), for total
  *     energy plus the wall's work on the pair u_w . (f_b e_b - f*_a e_a)
  *     (a moving adiabatic wall passes its work, not heat); Eq. 50 across a
@@ -74,6 +78,9 @@ typedef struct {
                         /* x and y are always periodic                        */
   double u_wall_z[2][3];  /* wall velocities of the z sides                   */
   double T_wall_z[2];     /* wall temperatures (isothermal walls), > 0        */
+  double g;               /* gravity along -z, a = (0, 0, -rho g): Guo's force */
+                          /* term beside C_a (Eq. 51 with D = 3) and the half- */
+                          /* force velocity shift; LBM_E_INTERNAL only, else 0 */
 } lbm3d_params;
 
 typedef struct lbm3d_handle lbm3d_handle;
@@ -88,7 +95,8 @@ int64_t lbm3d_state_bytes(const lbm3d_params* p);
  * cuda_stream (NULL: the legacy default stream).  Errors: LBM_ERR_PARAM
  * (nx, ny or nz < 1, tau <= 0, R T0 != 1/3, b < 3, an unknown model,
  * precision or z side, a non-finite wall velocity, a wall temperature <= 0,
- * 2^31 nodes or more), LBM_ERR_OOM, LBM_ERR_CUDA.  *out is NULL
+ * a non-finite g or g != 0 with total energy, 2^31 nodes or more),
+ * LBM_ERR_OOM, LBM_ERR_CUDA.  *out is NULL
  * on error. */
 int lbm3d_create(const lbm3d_params* p, void* cuda_stream, lbm3d_handle** out);
 

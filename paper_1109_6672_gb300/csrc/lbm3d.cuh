@@ -68,7 +68,7 @@ __host__ __device__ constexpr C w3(int a) {
   return a == 0 ? C(1) / C(3) : (a <= 6 ? C(1) / C(18) : C(1) / C(36));
 }
 
-enum { M3_TOTAL = 1, M3_ZFULL = 2, M3_CORR = 4 };
+enum { M3_TOTAL = 1, M3_ZFULL = 2, M3_CORR = 4, M3_FORCE = 8 };
 
 template <class C>
 struct Phys3 {
@@ -77,6 +77,7 @@ struct Phys3 {
   C b6, six_b;         // b / 6, 6 / b
   C uw[2][3];          // wall velocities of the z- and z+ sides
   C thw[2];            // wall theta = T_w / T0 (isothermal walls)
+  C g;                 // gravity along -z: a = (0, 0, -rho g)
 };
 
 enum { BC3_PERIODIC = 0, BC3_ISO = 1, BC3_ADIA = 2 };
@@ -137,6 +138,7 @@ __device__ __forceinline__ void moments3(const Grid3& g, const C d[NP3], C& rho,
     if (e3z(a)) jz += C(e3z(a)) * (d[a] - d[a + 1]);
   }
   rho = sf;
+  if constexpr ((M & M3_FORCE) != 0) jz -= C(0.5) * rho * k.g;  // rho u = sum e f + a / 2
   const C inv = C(1) / rho;
   ux = jx * inv;
   uy = jy * inv;
@@ -247,7 +249,8 @@ __device__ __forceinline__ void eq_one3(int a, C rho, C ux, C uy, C uz, C th, C 
 // the node's rho and theta and the wall velocity); h on an isothermal wall
 // h_b = h^eq_b(ghost) + (h*_b - h^eq_b), the ghost one spacing outside at
 // u_g = 2 u_w - u, theta_g = max(2 theta_w - theta, theta_w / 2),
-// rho_g = rho theta / theta_g; h on an adiabatic wall h_b = h*_a - 2 (odd
+// rho_g theta_g = rho (theta - 3 g n_z) (the node's pressure carried across
+// by hydrostatic balance); h on an adiabatic wall h_b = h*_a - 2 (odd
 // part of h^eq_a at (rho, u_w, theta)), for total energy plus the wall's
 // work on the pair u_w . (f_b e_b - f*_a e_a) = -(e_a . u_w)(f_b + f*_a)
 // (no heat crosses a moving adiabatic wall; its work does).  Each goes to
@@ -280,8 +283,11 @@ __device__ __forceinline__ void zwall_writes3(const Grid3& g, S* __restrict__ ds
       const C thg = fmax(C(2) * k.thw[side] - th, C(0.5) * k.thw[side]);
       const C ugx = C(2) * uwx - ux, ugy = C(2) * uwy - uy, ugz = C(2) * uwz - uz;
       const C esg = TOTAL ? k.b6 * thg + C(0.5) * (ugx * ugx + ugy * ugy + ugz * ugz) : k.b6 * thg;
+      // the node's pressure carried to the ghost by hydrostatic balance:
+      // rho_g theta_g = rho (theta - 3 g n_z), n_z the outward normal
+      const C rg = rho * (th - C(3) * k.g * C(side == 0 ? -1 : 1)) / thg;
       C fg, hg;
-      eq_one3<C, TOTAL>(b, rho * th / thg, ugx, ugy, ugz, thg, esg, fg, hg);
+      eq_one3<C, TOTAL>(b, rg, ugx, ugy, ugz, thg, esg, fg, hg);
       hin = hg + (v[Q19 + b] - heq[b]);
     } else {
       C hodd;
@@ -475,6 +481,17 @@ __global__ void __launch_bounds__(threads3<TY, SPLIT>(), (step3d_min_blocks<S, T
 #pragma unroll
         for (int a = 0; a < Q19; ++a) cc[a] = C(0);
       }
+      if constexpr ((M & M3_FORCE) != 0) {
+        // Guo's force term beside C (Eq. 51 with D = 3), a = (0, 0, -rho g):
+        // F_a = w_a [3 (e_a - u).a + 9 (e_a.u)(e_a.a)]
+        const C az = -prho * phys3<C>(g).g;
+#pragma unroll
+        for (int a = 0; a < Q19; ++a) {
+          const C eu = C(e3x(a)) * pux + C(e3y(a)) * puy + C(e3z(a)) * puz;
+          const C ea = C(e3z(a)) * az;
+          cc[a] += w3<C>(a) * (C(3) * (ea - puz * az) + C(9) * eu * ea);
+        }
+      }
       C d[NP3];
       const C* pk = park + (zc & 1) * NP3 * NT + t;  // parked by this thread at plane zc
 #pragma unroll
@@ -568,7 +585,7 @@ __global__ void export3d_kernel(const Grid3 g, const S* __restrict__ buf, double
         jz += e3z(a) * p[a];
         sh += p[Q19 + a];
       }
-      const double vx = jx / r, vy = jy / r, vz = jz / r;
+      const double vx = jx / r, vy = jy / r, vz = (jz - 0.5 * r * g.pd.g) / r;
       const double th = g.energy_model == 0
                             ? g.pd.six_b * (sh / r - 0.5 * (vx * vx + vy * vy + vz * vz))
                             : g.pd.six_b * sh / r;

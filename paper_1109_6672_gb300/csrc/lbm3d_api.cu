@@ -108,6 +108,10 @@ int validate3(const lbm3d_params* p, std::string& why) {
     why = "the z sides are both periodic or both walls";
     return LBM_ERR_PARAM;
   }
+  if (!std::isfinite(p->g) || (p->g != 0.0 && p->energy_model != LBM_E_INTERNAL)) {
+    why = "g must be finite, and 0 unless energy_model is LBM_E_INTERNAL";
+    return LBM_ERR_PARAM;
+  }
   return LBM_OK;
 }
 
@@ -142,6 +146,8 @@ void fill_grid3(const lbm3d_params* p, Grid3& g) {
   g.pf.kz = (float)(wh - wf);
   g.pf.b6 = (float)(p->b / 6.0);
   g.pf.six_b = (float)(6.0 / p->b);
+  g.pd.g = p->g;
+  g.pf.g = (float)p->g;
   for (int k = 0; k < 2; ++k) {
     g.bc_z[k] = p->bc_z[k];
     g.pd.thw[k] = p->T_wall_z[k] / p->T0;

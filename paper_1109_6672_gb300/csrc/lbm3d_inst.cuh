@@ -47,6 +47,10 @@ cudaError_t launch_step3d(const Grid3& g, dim3 grid, int zrows, int ty, int spli
       return launch_mode3<S, M3_TOTAL>(g, grid, zrows, ty, split, st);
     case M3_CORR:
       return launch_mode3<S, M3_CORR>(g, grid, zrows, ty, split, st);
+    case M3_FORCE | M3_CORR:
+      return launch_mode3<S, M3_FORCE | M3_CORR>(g, grid, zrows, ty, split, st);
+    case M3_FORCE:
+      return launch_mode3<S, M3_FORCE>(g, grid, zrows, ty, split, st);
     default:
       return launch_mode3<S, 0>(g, grid, zrows, ty, split, st);
   }
@@ -65,6 +69,10 @@ cudaError_t attributes3d_tile(int mode, cudaFuncAttributes* a) {
       return cudaFuncGetAttributes(a, step3d_kernel<S, M3_TOTAL, TY, SPLIT>);
     case M3_CORR:
       return cudaFuncGetAttributes(a, step3d_kernel<S, M3_CORR, TY, SPLIT>);
+    case M3_FORCE | M3_CORR:
+      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_FORCE | M3_CORR, TY, SPLIT>);
+    case M3_FORCE:
+      return cudaFuncGetAttributes(a, step3d_kernel<S, M3_FORCE, TY, SPLIT>);
     default:
       return cudaFuncGetAttributes(a, step3d_kernel<S, 0, TY, SPLIT>);
   }

@@ -16,6 +16,7 @@ inline int mode3_of(const Grid3& g) {
     if (g.z_full) m |= M3_ZFULL;
   }
   if (g.correction) m |= M3_CORR;
+  if (g.pd.g != 0.0) m |= M3_FORCE;  // internal energy only (validated)
   return m;
 }
 

@@ -24,7 +24,7 @@ class lbm3d_params(ctypes.Structure):
         ("energy_model", ctypes.c_int32), ("correction", ctypes.c_int32),
         ("z_full", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("bc_z", ctypes.c_int32 * 2), ("u_wall_z", (ctypes.c_double * 3) * 2),
-        ("T_wall_z", ctypes.c_double * 2),
+        ("T_wall_z", ctypes.c_double * 2), ("g", ctypes.c_double),
     ]
 
 
@@ -71,6 +71,7 @@ def make_params(p: dict) -> lbm3d_params:
     o.correction = int(p.get("correction", 1))
     o.z_full = int(p.get("z_full", 1))
     o.precision = int(p.get("precision", LBM_P_FP64))
+    o.g = float(p.get("g", 0.0))
     for k in range(2):
         o.bc_z[k] = int(p.get("bc_z", [0, 0])[k])
         o.T_wall_z[k] = float(p.get("T_wall_z", [1.0, 1.0])[k])

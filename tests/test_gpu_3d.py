@@ -216,3 +216,79 @@ def test_couette_3d_gpu_adiabatic_moving_wall(precision):
     assert np.abs(ux[:, 0, 0] - U * eta).max() < 2e-4 * U
     rise = Pr * U * U / ((b + 2) * inputs.RT0) * (2 * eta - eta * eta)
     assert np.abs((T[:, 0, 0] - 1) - rise).max() < 2e-3 * rise.max()
+
+
+GRAVITY = {
+    "periodic_corr": dict(energy_model=inputs.E_INTERNAL, b=5.0, g=2e-3),
+    "periodic": dict(energy_model=inputs.E_INTERNAL, b=5.0, g=2e-3, correction=0),
+    "iso_walls_corr": dict(energy_model=inputs.E_INTERNAL, b=5.0, g=2e-3, bc_z=[1, 1],
+                           T_wall_z=[1.04, 0.97], u_wall_z=[[0.0, 0.0, 0.0], [0.03, 0.0, 0.0]]),
+    "iso_adiabatic": dict(energy_model=inputs.E_INTERNAL, b=5.0, g=2e-3, bc_z=[1, 2],
+                          T_wall_z=[1.04, 1.0]),
+}
+
+
+@pytest.mark.parametrize("case", list(GRAVITY))
+@pytest.mark.parametrize("shape", [(4, 3, 5), (37, 11, 9)], ids=["4x3x5", "37x11x9"])
+def test_fp64_parity_3d_gravity(shape, case):
+    p, f = _case(shape, "internal", lbm.LBM_P_FP64)
+    p.update(GRAVITY[case])
+    o = o3.Oracle3d(p).init(*f).step(30)
+    g = Lbm3d(p).init(*f).step(30)
+    assert _rel(g.pops(), o.pops()) <= 1e-12
+    for got, want in zip(g.moments(), o.moments()):
+        assert np.abs(got - want).max() <= 1e-12 * max(np.abs(want).max(), 1e-3)
+    g.close()
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=[f"{a}x{b}" for a, b in SHAPES])
+def test_fp32_parity_3d_gravity(shape):
+    p, f = _case((37, 21, 9), "internal", lbm.LBM_P_FP32)
+    p.update(GRAVITY["iso_walls_corr"])
+    o = o3.Oracle3d(dict(p, precision=lbm.LBM_P_FP64)).init(*f).step(30)
+    g = Lbm3d(p).set_launch(*shape).init(*f).step(30)
+    assert _rel(g.pops(), o.pops()) <= 2e-5
+    g.close()
+
+
+def test_gravity_validation_3d():
+    p, f = _case((8, 8, 8), "total_zfull_corr", lbm.LBM_P_FP64)
+    for bad in (dict(g=1e-3), dict(g=float("nan"), energy_model=inputs.E_INTERNAL)):
+        with pytest.raises(lbm.LbmError):
+            Lbm3d(dict(p, **bad))
+
+
+def test_rayleigh_benard_onset_3d_gpu():
+    """The Rayleigh-Benard layer of test_oracle_convection.py on the D3Q19
+    path (FP64; rolls along y, two nodes deep; H = 32, dT/T0 = 0.05,
+    g H / (R T0) = 0.056): growth rates at 0.95, 1.0 and 1.05 Ra_c
+    interpolate the onset within 1.5 % of Ra_c = 1707.76 (measured 1.0073;
+    1.0014 at H = 64)."""
+    import math
+
+    H, ny, dT, tau_f, Pr = 32, 2, 0.05, 0.06, 0.71
+    nx, nu = 2 * H, tau_f * inputs.RT0
+    chi = nu / Pr
+    rates = {}
+    for ratio in (0.95, 1.0, 1.05):
+        grav = ratio * 1707.76 * nu * chi / (dT * H ** 3)
+        p = inputs.base_params3d(nx, ny, H, tau_f=tau_f, tau_h=tau_f / Pr, b=5.0, g=grav,
+                                 energy_model=inputs.E_INTERNAL, bc_z=[1, 1],
+                                 T_wall_z=[1 + dT / 2, 1 - dT / 2])
+        z = (np.arange(H) + 0.5) / H
+        x = np.arange(nx)
+        T = ((1 + dT / 2 - dT * z)[:, None, None] + 1e-3 * dT * np.sin(math.pi * z)[:, None, None]
+             * np.sin(2 * math.pi * x / nx)[None, None, :]) * np.ones((H, ny, nx))
+        rho = np.exp(-3 * grav * (np.arange(H) - H / 2))[:, None, None] * np.ones((H, ny, nx))
+        g = Lbm3d(p).init(rho, 0.0, 0.0, 0.0, T)
+        steps, chunks = int(2.5 * H * H / chi), 40
+        E = []
+        for _ in range(chunks):
+            g.step(steps // chunks)
+            E.append(float((g.moments()[3] ** 2).sum()))
+        g.close()
+        t = (np.arange(chunks) + 1) * (steps // chunks)
+        rates[ratio] = np.polyfit(t[chunks // 2:], 0.5 * np.log(E[chunks // 2:]), 1)[0] * H * H / chi
+    r = sorted(rates)
+    slope, icpt = np.polyfit(r, [rates[k] for k in r], 1)
+    assert slope > 0 and abs(-icpt / slope - 1.0) < 0.015, rates
