@@ -25,8 +25,10 @@
  *   - time discretisation: Eqs. 33-36 (BGK, omega = 2/(2 tau + 1), the sign
  *     of the C term read as + as in the D2Q9 oracle), or Eq. 38 with the
  *     internal-energy h^eq = b R T f^eq / 2; moments Eq. 35, Eq. 37.
- * The x and y sides are periodic; each z side is periodic or a halfway wall
- * (at z = -1/2 and z = nz - 1/2) with the D2Q9 oracle's wall rules carried
+ * Each side of the box is periodic or a halfway wall (at x = -1/2 and
+ * nx - 1/2, likewise in y and z; a population leaving through an edge of
+ * two walls takes the rule of the first of x, y, z, as the D2Q9 oracle's
+ * corners take the x side's), with the D2Q9 oracle's wall rules carried
  * to D3Q19: for a population a leaving through the wall, with b its
  * opposite, f_b(node, t+1) = f*_a - 2 (odd part of f^eq_a at the node's rho
  * and theta and the wall velocity); h on an isothermal wall by the
@@ -99,7 +101,22 @@ typedef struct {
   double u_wall_z[2][3];
   double T_wall_z[2];
   double g;             /* gravity along -z: force density a = (0, 0, -rho g) */
+  int32_t bc_x[2], bc_y[2]; /* sides x-, x+ and y-, y+, as bc_z */
+  double u_wall_x[2][3], u_wall_y[2][3];
+  double T_wall_x[2], T_wall_y[2];
 } o3_params;
+
+/* Side s = 2 axis + (0: low end, 1: high end) of the box: its boundary
+ * kind, wall velocity and wall temperature. */
+static int side_bc(const o3_params* p, int s) {
+  return s < 2 ? p->bc_x[s] : (s < 4 ? p->bc_y[s - 2] : p->bc_z[s - 4]);
+}
+static const double* side_uw(const o3_params* p, int s) {
+  return s < 2 ? p->u_wall_x[s] : (s < 4 ? p->u_wall_y[s - 2] : p->u_wall_z[s - 4]);
+}
+static double side_Tw(const o3_params* p, int s) {
+  return s < 2 ? p->T_wall_x[s] : (s < 4 ? p->T_wall_y[s - 2] : p->T_wall_z[s - 4]);
+}
 
 typedef struct {
   o3_params p;
@@ -336,33 +353,34 @@ static void phase1(o3_state* s, int nthreads) {
   }
 }
 
-/* D of the ghost node across wall side `side` (0: z-, 1: z+) of node i. */
+/* D of the ghost node across wall side `side` (2 axis + high end) of node i. */
 static void wall_ghost_D(const o3_state* s, long i, int side, double Dg[27]) {
   const o3_params* p = &s->p;
   const double RT0 = p->R * p->T0;
-  double thw = p->bc_z[side] == O3_WALL_ISOTHERMAL ? p->T_wall_z[side] / p->T0 : s->theta[i];
+  double thw = side_bc(p, side) == O3_WALL_ISOTHERMAL ? side_Tw(p, side) / p->T0 : s->theta[i];
   double Dw[27];
-  o3_defect(RT0, s->rho[i], p->u_wall_z[side], thw, Dw);
+  o3_defect(RT0, s->rho[i], side_uw(p, side), thw, Dw);
   for (int m = 0; m < 27; ++m) Dg[m] = 2.0 * Dw[m] - s->D[27 * i + m];
 }
 
 /* G_ij = sum_k dD_ijk/dx_k by the central differences of Eq. 50 (the ghost D
- * across a z wall). */
+ * across a wall). */
 static void node_G(const o3_state* s, int x, int y, int z, double G[9]) {
   const o3_params* p = &s->p;
   const long i = idx3(p, x, y, z);
+  const int c[3] = {x, y, z}, n[3] = {p->nx, p->ny, p->nz};
   for (int ij = 0; ij < 9; ++ij) G[ij] = 0.0;
   for (int k = 0; k < 3; ++k) {
     int dx = k == 0, dy = k == 1, dz = k == 2;
     double gp[27], gm[27];
     const double* Dp = &s->D[27 * idx3(p, x + dx, y + dy, z + dz)];
     const double* Dm = &s->D[27 * idx3(p, x - dx, y - dy, z - dz)];
-    if (k == 2 && z == p->nz - 1 && p->bc_z[1] != O3_PERIODIC) {
-      wall_ghost_D(s, i, 1, gp);
+    if (c[k] == n[k] - 1 && side_bc(p, 2 * k + 1) != O3_PERIODIC) {
+      wall_ghost_D(s, i, 2 * k + 1, gp);
       Dp = gp;
     }
-    if (k == 2 && z == 0 && p->bc_z[0] != O3_PERIODIC) {
-      wall_ghost_D(s, i, 0, gm);
+    if (c[k] == 0 && side_bc(p, 2 * k) != O3_PERIODIC) {
+      wall_ghost_D(s, i, 2 * k, gm);
       Dm = gm;
     }
     for (int ij = 0; ij < 9; ++ij) G[ij] += 0.5 * (Dp[3 * ij + k] - Dm[3 * ij + k]);
@@ -376,16 +394,15 @@ static int opp3(int a) {
   return a;
 }
 
-/* Population a leaving node i through a z wall comes back into node i as
- * the opposite population b (the rules in the header).  fs, hs: the node's
- * post-collision populations; heq: its h^eq. */
-static void wall_bounce(const o3_params* p, int a, double rho, const double u[3], double th,
-                        const double fs[Q3], const double hs[Q3], const double heq[Q3],
-                        double* fn[Q3], double* hn[Q3], long i) {
+/* Population a leaving node i through wall side `side` comes back into
+ * node i as the opposite population b (the rules in the header).  fs, hs:
+ * the node's post-collision populations; heq: its h^eq. */
+static void wall_bounce(const o3_params* p, int side, int a, double rho, const double u[3],
+                        double th, const double fs[Q3], const double hs[Q3],
+                        const double heq[Q3], double* fn[Q3], double* hn[Q3], long i) {
   const double RT0 = p->R * p->T0;
-  const int side = E3[a][2] < 0 ? 0 : 1;
   const int b = opp3(a);
-  const double* uw = p->u_wall_z[side];
+  const double* uw = side_uw(p, side);
   /* equilibria at the node's rho and theta and the wall velocity */
   double fw[Q3], hw[Q3];
   double Ew = 0.5 * (p->b * RT0 * th + uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2]);
@@ -395,12 +412,13 @@ static void wall_bounce(const o3_params* p, int a, double rho, const double u[3]
   else
     o3_heq_internal(RT0, p->b, th, fw, hw);
   fn[b][i] = fs[a] + (fw[b] - fw[a]); /* f*_a - 2 (odd part of f^eq_a) */
-  if (p->bc_z[side] == O3_WALL_ISOTHERMAL) {
-    const double thw = p->T_wall_z[side] / p->T0;
+  if (side_bc(p, side) == O3_WALL_ISOTHERMAL) {
+    const double thw = side_Tw(p, side) / p->T0;
     double thg = 2.0 * thw - th;
     if (thg < 0.5 * thw) thg = 0.5 * thw;
-    /* the node's pressure carried to the ghost by hydrostatic balance */
-    const double nz_out = side == 0 ? -1.0 : 1.0;
+    /* the node's pressure carried to the ghost by hydrostatic balance
+     * (gravity along -z: only the z sides) */
+    const double nz_out = side == 4 ? -1.0 : (side == 5 ? 1.0 : 0.0);
     const double rg = rho * (th - 3.0 * p->g * nz_out) / thg;
     double ug[3], fg[Q3], hg[Q3];
     for (int d = 0; d < 3; ++d) ug[d] = 2.0 * uw[d] - u[d];
@@ -469,15 +487,21 @@ static void phase2(o3_state* s, int nthreads) {
           }
         }
         for (int a = 0; a < Q3; ++a) {
-          const int zt = z + E3[a][2];
-          const int side = zt < 0 ? 0 : (zt >= p->nz ? 1 : -1);
-          if (side >= 0 && p->bc_z[side] != O3_PERIODIC) {
-            /* halfway wall: back into this node as the opposite population */
-            wall_bounce(p, a, rho, u, th, fs, hs, heq, s->fn, s->hn, i);
+          /* a halfway wall crossed (x before y before z when a leaves
+           * through an edge): back into this node as the opposite */
+          const int t[3] = {x + E3[a][0], y + E3[a][1], z + E3[a][2]};
+          const int n[3] = {p->nx, p->ny, p->nz};
+          int side = -1;
+          for (int k = 0; k < 3 && side < 0; ++k) {
+            const int sk = t[k] < 0 ? 2 * k : (t[k] >= n[k] ? 2 * k + 1 : -1);
+            if (sk >= 0 && side_bc(p, sk) != O3_PERIODIC) side = sk;
+          }
+          if (side >= 0) {
+            wall_bounce(p, side, a, rho, u, th, fs, hs, heq, s->fn, s->hn, i);
             continue;
           }
           /* streaming to x + e_a (periodic) */
-          long j = idx3(p, x + E3[a][0], y + E3[a][1], zt);
+          long j = idx3(p, t[0], t[1], t[2]);
           s->fn[a][j] = fs[a];
           s->hn[a][j] = hs[a];
         }

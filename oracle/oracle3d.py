@@ -42,6 +42,12 @@ class O3Params(ctypes.Structure):
         ("u_wall_z", (ctypes.c_double * 3) * 2),
         ("T_wall_z", ctypes.c_double * 2),
         ("g", ctypes.c_double),
+        ("bc_x", ctypes.c_int32 * 2),
+        ("bc_y", ctypes.c_int32 * 2),
+        ("u_wall_x", (ctypes.c_double * 3) * 2),
+        ("u_wall_y", (ctypes.c_double * 3) * 2),
+        ("T_wall_x", ctypes.c_double * 2),
+        ("T_wall_y", ctypes.c_double * 2),
     ]
 
 
@@ -110,12 +116,13 @@ def make_params(p: dict) -> O3Params:
     o.tau_f, o.tau_h = float(p["tau_f"]), float(p["tau_h"])
     o.R, o.T0, o.b = float(p["R"]), float(p["T0"]), float(p["b"])
     o.g = float(p.get("g", 0.0))
-    for k in range(2):
-        o.bc_z[k] = int(p.get("bc_z", [0, 0])[k])
-        o.T_wall_z[k] = float(p.get("T_wall_z", [1.0, 1.0])[k])
-        uw = p.get("u_wall_z", [[0.0] * 3] * 2)[k]
-        for d in range(3):
-            o.u_wall_z[k][d] = float(uw[d])
+    for ax in "xyz":
+        bc, tw, uw = getattr(o, "bc_" + ax), getattr(o, "T_wall_" + ax), getattr(o, "u_wall_" + ax)
+        for k in range(2):
+            bc[k] = int(p.get("bc_" + ax, [0, 0])[k])
+            tw[k] = float(p.get("T_wall_" + ax, [1.0, 1.0])[k])
+            for d in range(3):
+                uw[k][d] = float(p.get("u_wall_" + ax, [[0.0] * 3] * 2)[k][d])
     return o
 
 
@@ -166,8 +173,8 @@ def correction(G) -> np.ndarray:
 # ---- whole-grid state ------------------------------------------------------
 
 class Oracle3d:
-    """One 3-D grid advanced by the oracle (x, y periodic; z periodic or
-    walled).  Arrays are [nz, ny, nx]."""
+    """One 3-D grid advanced by the oracle (each axis periodic or walled).
+    Arrays are [nz, ny, nx]."""
 
     def __init__(self, params: dict):
         self.p = dict(params)

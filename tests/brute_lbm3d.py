@@ -13,7 +13,7 @@ separately from the oracle and takes different routes to the same quantities:
   (A_kk = (G_kk + 4/7 tr G) / 6, A_ij = G_ij / 8, kappa = 10/19) instead of
   by elimination;
 * moments are array contractions; streaming is pull-based (np.roll); the
-  z walls are applied on the pull, from the receiving node's side;
+  walls are applied on the pull, node by node from the receiving side;
 * gravity along -z: Guo's force term with the half-force velocity shift.
 """
 from __future__ import annotations
@@ -120,9 +120,12 @@ class Brute3d:
         self.p = dict(p)
         self.shape = (int(p["nz"]), int(p["ny"]), int(p["nx"]))
         self.total = int(p.get("energy_model", 0)) == 0
-        self.bc = list(p.get("bc_z", [PERIODIC, PERIODIC]))
-        self.uw = np.array(p.get("u_wall_z", [[0.0] * 3, [0.0] * 3]), dtype=float)
-        self.thw = np.array(p.get("T_wall_z", [1.0, 1.0]), dtype=float) / p["T0"]
+        # sides 2 axis + (0 low, 1 high), axes x, y, z
+        self.bc, self.uw, self.thw = [], [], []
+        for ax in "xyz":
+            self.bc += list(p.get("bc_" + ax, [PERIODIC, PERIODIC]))
+            self.uw += [np.array(v, dtype=float) for v in p.get("u_wall_" + ax, [[0.0] * 3] * 2)]
+            self.thw += [float(v) / p["T0"] for v in p.get("T_wall_" + ax, [1.0, 1.0])]
 
     def _eq(self, rho, u, th):
         f = feq_shells(rho, u, th)
@@ -151,23 +154,28 @@ class Brute3d:
         return np.concatenate([self.F, self.H], 0)
 
     def _grad(self, Q, rho, th):
-        """dQ[k, j] = dQ_j / dx_k by central differences; across a z wall the
+        """dQ[k, j] = dQ_j / dx_k by central differences; across a wall the
         mirror ghost 2 rho u_w (1 - theta_w) - Q (theta_w: the node's own on
         an adiabatic wall)."""
         dQ = np.zeros((3,) + Q.shape)
-        for k, ax in ((0, 2), (1, 1), (2, 0)):
+        for k in range(3):
+            ax = 2 - k  # array axis of x, y, z in [nz, ny, nx]
             up = np.roll(Q, -1, axis=1 + ax)
             dn = np.roll(Q, 1, axis=1 + ax)
-            if k == 2:
-                for side, sl in ((0, 0), (1, -1)):
-                    if self.bc[side] == PERIODIC:
-                        continue
-                    thw = self.thw[side] if self.bc[side] == ISO else th[sl]
-                    ghost = 2 * rho[sl] * self.uw[side][:, None, None] * (1 - thw) - Q[:, sl]
-                    if side == 0:
-                        dn[:, 0] = ghost
-                    else:
-                        up[:, -1] = ghost
+            for hi in (0, 1):
+                side = 2 * k + hi
+                if self.bc[side] == PERIODIC:
+                    continue
+                sl = [slice(None)] * 3
+                sl[ax] = -1 if hi else 0
+                sl = tuple(sl)
+                thw = self.thw[side] if self.bc[side] == ISO else th[sl]
+                uw = self.uw[side].reshape((3,) + (1,) * rho[sl].ndim)
+                ghost = 2 * rho[sl] * uw * (1 - thw) - Q[(slice(None),) + sl]
+                if hi:
+                    up[(slice(None),) + sl] = ghost
+                else:
+                    dn[(slice(None),) + sl] = ghost
             dQ[k] = 0.5 * (up - dn)
         return dQ
 
@@ -209,38 +217,51 @@ class Brute3d:
                 eu = E[a, 0] * u[0] + E[a, 1] * u[1] + E[a, 2] * u[2]
                 Z = eu - 0.5 * usq if int(p.get("z_full", 1)) else eu
                 hs[a] = hs[a] + (wh - wf) * Z * (fneq[a] + 0.5 * C[a])
-        # pull streaming (periodic), then the populations that came through
-        # a z wall replaced from the receiving node's side
+        # pull streaming (periodic), then, node by node on the faces, the
+        # populations that came back from a wall replaced from the receiving
+        # node's side (a left through the first walled side it crossed, of
+        # x, y, z; b = its opposite arrives)
         Fn = np.empty_like(fs)
         Hn = np.empty_like(hs)
         for a in range(19):
             sh = (E[a, 2], E[a, 1], E[a, 0])
             Fn[a] = np.roll(fs[a], sh, axis=(0, 1, 2))
             Hn[a] = np.roll(hs[a], sh, axis=(0, 1, 2))
-        nz = self.shape[0]
-        for b in range(19):
-            if E[b, 2] == 0:
-                continue
-            side = 0 if E[b, 2] > 0 else 1  # b arrives at z = 0 from below, or at nz - 1
-            if self.bc[side] == PERIODIC:
-                continue
-            z = 0 if side == 0 else nz - 1
-            a = OPP[b]  # what left the node through the wall
-            r, t = rho[z], th[z]
-            uw = self.uw[side][:, None, None] * np.ones((1,) + r.shape)
-            fw, hw = self._eq(r, uw, t)  # the node's rho, theta and the wall velocity
-            Fn[b, z] = fs[a, z] + (fw[b] - fw[a])
-            if self.bc[side] == ISO:
-                tg = np.maximum(2 * self.thw[side] - t, 0.5 * self.thw[side])
-                # the node's pressure, less the hydrostatic drop to the ghost
-                rg = r * (t - 3 * float(p.get("g", 0.0)) * (-1 if side == 0 else 1)) / tg
-                ug = 2 * uw - u[:, z]
-                fg, hg = self._eq(rg, ug, tg)
-                Hn[b, z] = hg[b] + (hs[b, z] - heq[b, z])
-            else:
-                hin = hs[a, z] + (hw[b] - hw[a])
-                if self.total:  # the moving wall's work on the pair
-                    ea_uw = E[a, 0] * uw[0] + E[a, 1] * uw[1] + E[a, 2] * uw[2]
-                    hin = hin - ea_uw * (Fn[b, z] + fs[a, z])
-                Hn[b, z] = hin
+        nz, ny, nx = self.shape
+        n = (nx, ny, nz)
+        for z in range(nz):
+            for y in range(ny):
+                for x in range(nx):
+                    c = (x, y, z)
+                    if all(0 < c[k] < n[k] - 1 for k in range(3)):
+                        continue
+                    for a in range(1, 19):
+                        side = -1
+                        for k in range(3):
+                            t = c[k] + E[a, k]
+                            sk = 2 * k if t < 0 else (2 * k + 1 if t >= n[k] else -1)
+                            if sk >= 0 and self.bc[sk] != PERIODIC:
+                                side = sk
+                                break
+                        if side < 0:
+                            continue
+                        b = OPP[a]
+                        r, tn = rho[z, y, x], th[z, y, x]
+                        un = u[:, z, y, x]
+                        uw = self.uw[side]
+                        fw, hw = self._eq(r, uw, tn)  # node's rho, theta; wall velocity
+                        Fn[b, z, y, x] = fs[a, z, y, x] + (fw[b] - fw[a])
+                        if self.bc[side] == ISO:
+                            tg = max(2 * self.thw[side] - tn, 0.5 * self.thw[side])
+                            # the node's pressure less the hydrostatic drop
+                            # to the ghost (gravity along -z)
+                            nz_out = -1 if side == 4 else (1 if side == 5 else 0)
+                            rg = r * (tn - 3 * float(p.get("g", 0.0)) * nz_out) / tg
+                            fg, hg = self._eq(rg, 2 * uw - un, tg)
+                            Hn[b, z, y, x] = hg[b] + (hs[b, z, y, x] - heq[b, z, y, x])
+                        else:
+                            hin = hs[a, z, y, x] + (hw[b] - hw[a])
+                            if self.total:  # the moving wall's work on the pair
+                                hin = hin - float(E[a] @ uw) * (Fn[b, z, y, x] + fs[a, z, y, x])
+                            Hn[b, z, y, x] = hin
         self.F, self.H = Fn, Hn

@@ -449,3 +449,76 @@ def test_hydrostatic_balance_3d():
     pr = rho[:, 0, 0] * T[:, 0, 0] * RT0
     dp = 0.5 * (pr[2:] - pr[:-2])
     assert np.abs(dp + rho[1:-1, 0, 0] * g).max() < 1e-4 * g
+
+
+# ---- walls on the x and y sides (the z rules on every side) ---------------------
+
+def _axis_params(ax, n_wall, n_other, **walls):
+    """Grid with the walled axis `ax` ("x" or "y") n_wall long and the other
+    two n_other (periodic), and the arrays' axis of `ax` in [nz, ny, nx]."""
+    dims = {"x": n_other, "y": n_other, "z": n_other}
+    dims[ax] = n_wall
+    p = dict(nx=dims["x"], ny=dims["y"], nz=dims["z"])
+    p.update({k.replace("AX", ax): v for k, v in walls.items()})
+    return p, {"x": 2, "y": 1, "z": 0}[ax]
+
+
+@pytest.mark.parametrize("ax", ["x", "y"])
+def test_couette_3d_side_walls(ax):
+    """The isothermal Couette flow of test_couette_3d_closed_form between
+    walls on the x or the y sides: the moving wall slides along the next
+    axis; u linear and the viscous-heating parabola."""
+    H, U, nu, Pr, b = 16, 1.0 / 3.0, 0.2, 1.0, 5.0
+    tau_f = nu / RT0
+    slide = [0.0, 0.0, 0.0]
+    slide[1 if ax == "x" else 2] = U
+    g, arr = _axis_params(ax, H, 4, bc_AX=[o3.WALL_ISOTHERMAL] * 2,
+                          u_wall_AX=[[0.0] * 3, slide], T_wall_AX=[1.0, 1.0])
+    p = inputs.base_params3d(g.pop("nx"), g.pop("ny"), g.pop("nz"), tau_f=tau_f,
+                             tau_h=tau_f / Pr, b=b, **g)
+    shape = (p["nz"], p["ny"], p["nx"])
+    o = o3.Oracle3d(p).init(*inputs.uniform_fields3d(p["nx"], p["ny"], p["nz"], seed=0,
+                                                      u_amp=1e-10))
+    o.step(6000, threads=4)
+    m = o.moments()
+    prof = lambda v: np.moveaxis(v, arr, 0).reshape(H, -1)[:, 0]  # noqa: E731
+    us = prof(m[2 if ax == "x" else 3])
+    T = prof(m[4])
+    eta = (np.arange(H) + 0.5) / H
+    assert np.abs(us - U * eta).max() < 1.5e-3 * U
+    rise = Pr * U * U / ((b + 2) * RT0) * eta * (1 - eta)
+    assert np.abs((T - 1) - rise).max() < 0.02 * rise.max()
+    assert shape == m[0].shape
+
+
+@pytest.mark.parametrize("ax", ["x", "y"])
+def test_isothermal_side_walls_conduct(ax):
+    """No flow, side walls at theta 1.05 and 0.95: the steady temperature is
+    the linear conduction profile through the halfway wall values."""
+    H = 12
+    g, arr = _axis_params(ax, H, 2, bc_AX=[o3.WALL_ISOTHERMAL] * 2, T_wall_AX=[1.05, 0.95])
+    p = inputs.base_params3d(g.pop("nx"), g.pop("ny"), g.pop("nz"), tau_f=0.3, tau_h=0.4,
+                             b=5.0, energy_model=inputs.E_INTERNAL, **g)
+    o = o3.Oracle3d(p).init(*inputs.uniform_fields3d(p["nx"], p["ny"], p["nz"], seed=0))
+    o.step(20000, threads=4)
+    rho, ux, uy, uz, T = o.moments()
+    eta = (np.arange(H) + 0.5) / H
+    Tp = np.moveaxis(T, arr, 0).reshape(H, -1)[:, 0]
+    assert np.abs(Tp - (1.05 - 0.1 * eta)).max() < 1e-3 * 0.1
+    assert max(np.abs(ux).max(), np.abs(uy).max(), np.abs(uz).max()) < 1e-8
+
+
+def test_closed_box_all_walls_conserves_mass_and_energy_3d():
+    """Walls at rest on all six sides, adiabatic: the populations that leave
+    through faces, edges and corners all come back, so mass and total energy
+    are conserved exactly."""
+    p = inputs.base_params3d(5, 4, 6, tau_f=0.35, tau_h=0.5, b=5.0,
+                             bc_x=[o3.WALL_ADIABATIC] * 2, bc_y=[o3.WALL_ADIABATIC] * 2,
+                             bc_z=[o3.WALL_ADIABATIC] * 2)
+    f = inputs.uniform_fields3d(5, 4, 6, seed=8, u_amp=0.03, T_amp=0.04, rho_amp=0.02)
+    o = o3.Oracle3d(p).init(*f)
+    c0 = o.conserved()
+    o.step(300)
+    c1 = o.conserved()
+    assert abs(c1[0] - c0[0]) <= 1e-13 * c0[0]
+    assert abs(c1[4] - c0[4]) <= 1e-13 * c0[4]

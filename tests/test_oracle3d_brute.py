@@ -1,6 +1,6 @@
 """The D3Q19 oracle against the independent NumPy restatement
 (tests/brute_lbm3d.py) on tiny noisy grids: every physics mode, periodic and
-walled z sides.  This is the only check of the -u^2/2 part of Z_a in the
+walled sides (z alone, x alone, all six, with edges and corners).  This is the only check of the -u^2/2 part of Z_a in the
 Eq. 36 coupling in 3-D, which no closed form or decay rate can see (the
 paper notes that Z_a reduces to e_a.u at the Navier-Stokes level)."""
 import numpy as np
@@ -24,6 +24,14 @@ CASES = {
     "gravity_walls_internal": dict(bc_z=[1, 1], energy_model=inputs.E_INTERNAL, g=2e-3,
                                    T_wall_z=[1.05, 0.97]),
     "gravity_periodic_internal": dict(energy_model=inputs.E_INTERNAL, g=2e-3, correction=0),
+    "x_walls": dict(bc_x=[1, 2], u_wall_x=[[0.0, 0.03, 0.0], [0.0, 0.0, -0.02]],
+                    T_wall_x=[1.05, 1.0]),
+    "box_all_walls": dict(bc_x=[1, 1], bc_y=[2, 2], bc_z=[1, 2], T_wall_x=[1.04, 0.97],
+                          T_wall_z=[1.02, 1.0],
+                          u_wall_y=[[0.02, 0.0, 0.0], [0.0, 0.0, 0.03]],
+                          u_wall_z=[[0.0, 0.0, 0.0], [0.04, -0.01, 0.0]]),
+    "box_internal_gravity": dict(bc_x=[1, 1], bc_y=[2, 2], bc_z=[2, 2], T_wall_x=[1.05, 0.95],
+                                 energy_model=inputs.E_INTERNAL, g=2e-3),
 }
 
 
