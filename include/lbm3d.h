@@ -3,8 +3,8 @@
  * double-distribution-function thermal lattice Boltzmann method of Li, Luo,
  * He, Gao and Tao (arXiv:1109.6672).  The paper builds the model on D2Q9 and
  * states that its formulation extends to three dimensions (Sec. V); this is
- * that extension, BGK scheme (Sec. III.C.1), x and y periodic, each z side
- * periodic or a halfway wall:
+ * that extension, BGK scheme (Sec. III.C.1), each side of the box periodic
+ * or a halfway wall:
  *
  *   - f^eq: Eq. 18a with D = 3; h^eq: Eq. 18b with D = 3 (total energy,
  *     Eq. 36 with the (omega_h - omega_f) Z_a coupling), or the internal-
@@ -22,16 +22,20 @@
  *     moments Eq. 35 and Eq. 37;
  *   - gravity along -z (g, internal-energy model): Guo's force term of
  *     Eq. 51 with D = 3 beside C_a and the half-force shift of u;
- *   - z walls (not in the paper, which uses non-equilibrium extrapolation;
- *     the rules of lbm.h carried to D3Q19), halfway at z = -1/2 and
- *     nz - 1/2: a population a leaving through the wall comes back as its
+ *   - walls (not in the paper, which uses non-equilibrium extrapolation;
+ *     the rules of lbm.h carried to D3Q19), halfway at x = -1/2 and
+ *     nx - 1/2, likewise in y and z; a population leaving through an edge
+ *     where two walled sides meet takes the rule of the first of x, y, z
+ *     (as the D2Q9 corners take the x side's); a population a leaving
+ *     through the wall comes back as its
  *     opposite b with f_b = f*_a - 2 (odd part of Eq. 18a at the node's rho
  *     and theta and the wall velocity); h on an isothermal wall
  *     h_b = h^eq_b(ghost) + (h*_b - h^eq_b) with the ghost one spacing
  *     outside at u_g = 2 u_w - u, theta_g = max(2 theta_w - theta,
  *     theta_w / 2), rho_g theta_g = rho (theta - 3 g n_z) (the node's
- *     pressure carried across by hydrostatic balance, n_z the outward
- *     normal); h on an adiabatic wall
+ *     pressure carried across by hydrostatic balance, n_z the z component
+ *     of the outward normal: 0 on the x and y sides); h on an adiabatic
+ *     wall
  *     h_b = h*_a - 2 (odd part of h^eq_a at (rho, u_w, theta)), for total
  *     energy plus the wall's work on the pair u_w . (f_b e_b - f*_a e_a)
  *     (a moving adiabatic wall passes its work, not heat); Eq. 50 across a
@@ -75,12 +79,17 @@ typedef struct {
   int32_t bc_z[2];      /* z- and z+ sides: LBM_BC_PERIODIC,                  */
                         /* LBM_BC_WALL_ISOTHERMAL or                          */
                         /* LBM_BC_WALL_ADIABATIC (halfway walls, see above);  */
-                        /* x and y are always periodic                        */
+                        /* both periodic or both walls                        */
   double u_wall_z[2][3];  /* wall velocities of the z sides                   */
   double T_wall_z[2];     /* wall temperatures (isothermal walls), > 0        */
   double g;               /* gravity along -z, a = (0, 0, -rho g): Guo's force */
                           /* term beside C_a (Eq. 51 with D = 3) and the half- */
                           /* force velocity shift; LBM_E_INTERNAL only, else 0 */
+  int32_t bc_x[2], bc_y[2]; /* x-, x+ and y-, y+ sides, as bc_z (zeroed: all  */
+                            /* periodic)                                       */
+  double u_wall_x[2][3], u_wall_y[2][3]; /* wall velocities of those sides    */
+  double T_wall_x[2], T_wall_y[2];       /* their wall temperatures, > 0 on   */
+                                         /* an isothermal wall               */
 } lbm3d_params;
 
 typedef struct lbm3d_handle lbm3d_handle;
@@ -94,7 +103,8 @@ int64_t lbm3d_state_bytes(const lbm3d_params* p);
  * (5 nx ny nz doubles) on the current device; binds the handle to
  * cuda_stream (NULL: the legacy default stream).  Errors: LBM_ERR_PARAM
  * (nx, ny or nz < 1, tau <= 0, R T0 != 1/3, b < 3, an unknown model,
- * precision or z side, a non-finite wall velocity, a wall temperature <= 0,
+ * precision or side kind, one side of an axis periodic and the other a
+ * wall, a non-finite wall velocity, a wall temperature <= 0,
  * a non-finite g or g != 0 with total energy, 2^31 nodes or more),
  * LBM_ERR_OOM, LBM_ERR_CUDA.  *out is NULL
  * on error. */

@@ -33,7 +33,7 @@
 // of Q in shared memory, then collides the plane below, whose own moments
 // the thread kept in registers and whose pulled populations it parked in
 // shared memory (a per-thread column, two planes deep, so no barrier guards
-// it).  x and y are periodic; each z side periodic or a halfway wall.
+// it).  Each side of the box is periodic or a halfway wall.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -75,8 +75,8 @@ struct Phys3 {
   C omega_f, omega_h;  // 2 / (2 tau + 1)
   C kz;                // omega_h - omega_f (Eq. 36)
   C b6, six_b;         // b / 6, 6 / b
-  C uw[2][3];          // wall velocities of the z- and z+ sides
-  C thw[2];            // wall theta = T_w / T0 (isothermal walls)
+  C uw[6][3];          // wall velocities of the sides x-, x+, y-, y+, z-, z+
+  C thw[6];            // wall theta = T_w / T0 (isothermal walls)
   C g;                 // gravity along -z: a = (0, 0, -rho g)
 };
 
@@ -88,7 +88,8 @@ struct Grid3 {
   int nx, ny, nz, pitch;
   long long lp, zs;  // line stride (38 pitch) and plane stride ((ny + 2) lp)
   int energy_model, correction, z_full;
-  int bc_z[2];  // z- and z+ sides: BC3_PERIODIC or a halfway wall
+  int bc[6];  // sides x-, x+, y-, y+, z-, z+ (2 axis + high end): BC3_PERIODIC
+              // or a halfway wall
   Phys3<double> pd;
   Phys3<float> pf;
 };
@@ -243,34 +244,74 @@ __device__ __forceinline__ void eq_one3(int a, C rho, C ux, C uy, C uz, C th, C 
   }
 }
 
-// The populations of node (x, y, z) that leave through a z wall come back
-// into the node as their opposites (halfway walls at z = -1/2 and
-// nz - 1/2): with b the opposite of a, f_b = f*_a - 2 (odd part of f^eq_a at
-// the node's rho and theta and the wall velocity); h on an isothermal wall
-// h_b = h^eq_b(ghost) + (h*_b - h^eq_b), the ghost one spacing outside at
-// u_g = 2 u_w - u, theta_g = max(2 theta_w - theta, theta_w / 2),
-// rho_g theta_g = rho (theta - 3 g n_z) (the node's pressure carried across
-// by hydrostatic balance); h on an adiabatic wall h_b = h*_a - 2 (odd
-// part of h^eq_a at (rho, u_w, theta)), for total energy plus the wall's
-// work on the pair u_w . (f_b e_b - f*_a e_a) = -(e_a . u_w)(f_b + f*_a)
-// (no heat crosses a moving adiabatic wall; its work does).  Each goes to
-// the slot from which the node pulls b: x - e_b = x + e_a, a ghost plane.
-template <class S, bool TOTAL>
-__device__ __forceinline__ void zwall_writes3(const Grid3& g, S* __restrict__ dst, int x, int y,
-                                              int z, const typename Io<S>::C v[NP3],
-                                              const typename Io<S>::C heq[Q19],
-                                              typename Io<S>::C rho, typename Io<S>::C ux,
-                                              typename Io<S>::C uy, typename Io<S>::C uz,
-                                              typename Io<S>::C th) {
+// The populations of node (x, y, z) that leave through a wall come back
+// into the node as their opposites (halfway walls at x = -1/2 and nx - 1/2,
+// likewise in y and z; a population leaving through an edge of two walled
+// sides takes the first of x, y, z): with b the opposite of a,
+// f_b = f*_a - 2 (odd part of f^eq_a at the node's rho and theta and the
+// wall velocity); h on an isothermal wall h_b = h^eq_b(ghost) +
+// (h*_b - h^eq_b), the ghost one spacing outside at u_g = 2 u_w - u,
+// theta_g = max(2 theta_w - theta, theta_w / 2), rho_g theta_g =
+// rho (theta - 3 g n_z) (the node's pressure carried across by hydrostatic
+// balance, n_z the z component of the outward normal); h on an adiabatic
+// wall h_b = h*_a - 2 (odd part of h^eq_a at (rho, u_w, theta)), for total
+// energy plus the wall's work on the pair u_w . (f_b e_b - f*_a e_a) =
+// -(e_a . u_w)(f_b + f*_a) (no heat crosses a moving adiabatic wall; its
+// work does).  Each goes to the slot from which the node pulls b:
+// x - e_b = x + e_a, a ghost slot.  Sides and directions are compile-time
+// after unrolling, so every index into the parameters is a constant.
+__device__ __forceinline__ int axis_coord3(int ax, int x, int y, int z) {
+  return ax == 0 ? x : (ax == 1 ? y : z);
+}
+__device__ __forceinline__ int axis_n3(const Grid3& g, int ax) {
+  return ax == 0 ? g.nx : (ax == 1 ? g.ny : g.nz);
+}
+__host__ __device__ constexpr int e3ax(int a, int ax) {
+  return ax == 0 ? e3x(a) : (ax == 1 ? e3y(a) : e3z(a));
+}
+// Side (2 axis + high end) through which population a leaves node
+// (x, y, z) if that side is a wall, x before y before z; -1 otherwise.
+__device__ __forceinline__ int wall_side3(const Grid3& g, int a, int x, int y, int z) {
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int e = e3ax(a, ax);
+    if (e == 0) continue;
+    const int c = axis_coord3(ax, x, y, z) + e;
+    const int s = 2 * ax + (e > 0 ? 1 : 0);
+    if ((e < 0 ? c < 0 : c >= axis_n3(g, ax)) && g.bc[s] != BC3_PERIODIC) return s;
+  }
+  return -1;
+}
+
+template <class S, bool TOTAL, int SIDE>
+__device__ __forceinline__ void wall_writes_side3(const Grid3& g, S* __restrict__ dst, int x,
+                                                  int y, int z,
+                                                  const typename Io<S>::C v[NP3],
+                                                  const typename Io<S>::C heq[Q19],
+                                                  typename Io<S>::C rho, typename Io<S>::C ux,
+                                                  typename Io<S>::C uy, typename Io<S>::C uz,
+                                                  typename Io<S>::C th) {
   using C = typename Io<S>::C;
+  constexpr int AX = SIDE >> 1, DIR = (SIDE & 1) ? 1 : -1;
   const Phys3<C>& k = phys3<C>(g);
+  const int c = axis_coord3(AX, x, y, z);
+  if (g.bc[SIDE] == BC3_PERIODIC || c != (DIR > 0 ? axis_n3(g, AX) - 1 : 0)) return;
 #pragma unroll
   for (int a = 1; a < Q19; ++a) {
-    if (e3z(a) == 0) continue;
-    const int side = e3z(a) < 0 ? 0 : 1;
-    if ((side == 0 ? z != 0 : z != g.nz - 1) || g.bc_z[side] == BC3_PERIODIC) continue;
+    if (e3ax(a, AX) != DIR) continue;
+    // an earlier axis's wall takes the populations leaving through an edge
+    bool earlier = false;
+#pragma unroll
+    for (int ax = 0; ax < AX; ++ax) {
+      const int e = e3ax(a, ax);
+      if (e == 0) continue;
+      const int ce = axis_coord3(ax, x, y, z) + e;
+      if ((e < 0 ? ce < 0 : ce >= axis_n3(g, ax)) && g.bc[2 * ax + (e > 0 ? 1 : 0)] != BC3_PERIODIC)
+        earlier = true;
+    }
+    if (earlier) continue;
     const int b = (a & 1) ? a + 1 : a - 1;  // opposite
-    const C uwx = k.uw[side][0], uwy = k.uw[side][1], uwz = k.uw[side][2];
+    const C uwx = k.uw[SIDE][0], uwy = k.uw[SIDE][1], uwz = k.uw[SIDE][2];
     const C euw = C(e3x(a)) * uwx + C(e3y(a)) * uwy + C(e3z(a)) * uwz;
     const bool axis = e3sq(a) == 1;
     const C w = axis ? w3<C>(1) : w3<C>(7);
@@ -279,13 +320,18 @@ __device__ __forceinline__ void zwall_writes3(const Grid3& g, S* __restrict__ ds
     const C fb = v[a] - C(2) * fodd;
     dst[o + (long long)b * g.pitch] = Io<S>::from(fb);
     C hin;
-    if (g.bc_z[side] == BC3_ISO) {
-      const C thg = fmax(C(2) * k.thw[side] - th, C(0.5) * k.thw[side]);
+    if (g.bc[SIDE] == BC3_ISO) {
+      const C thg = fmax(C(2) * k.thw[SIDE] - th, C(0.5) * k.thw[SIDE]);
       const C ugx = C(2) * uwx - ux, ugy = C(2) * uwy - uy, ugz = C(2) * uwz - uz;
       const C esg = TOTAL ? k.b6 * thg + C(0.5) * (ugx * ugx + ugy * ugy + ugz * ugz) : k.b6 * thg;
       // the node's pressure carried to the ghost by hydrostatic balance:
-      // rho_g theta_g = rho (theta - 3 g n_z), n_z the outward normal
-      const C rg = rho * (th - C(3) * k.g * C(side == 0 ? -1 : 1)) / thg;
+      // rho_g theta_g = rho (theta - 3 g n_z), n_z the outward normal's z
+      // component (gravity acts along -z)
+      C rg;
+      if constexpr (AX == 2)
+        rg = rho * (th - C(3) * k.g * C(DIR)) / thg;
+      else
+        rg = rho * th / thg;
       C fg, hg;
       eq_one3<C, TOTAL>(b, rg, ugx, ugy, ugz, thg, esg, fg, hg);
       hin = hg + (v[Q19 + b] - heq[b]);
@@ -305,6 +351,21 @@ __device__ __forceinline__ void zwall_writes3(const Grid3& g, S* __restrict__ ds
   }
 }
 
+template <class S, bool TOTAL>
+__device__ __forceinline__ void wall_writes3(const Grid3& g, S* __restrict__ dst, int x, int y,
+                                             int z, const typename Io<S>::C v[NP3],
+                                             const typename Io<S>::C heq[Q19],
+                                             typename Io<S>::C rho, typename Io<S>::C ux,
+                                             typename Io<S>::C uy, typename Io<S>::C uz,
+                                             typename Io<S>::C th) {
+  wall_writes_side3<S, TOTAL, 0>(g, dst, x, y, z, v, heq, rho, ux, uy, uz, th);
+  wall_writes_side3<S, TOTAL, 1>(g, dst, x, y, z, v, heq, rho, ux, uy, uz, th);
+  wall_writes_side3<S, TOTAL, 2>(g, dst, x, y, z, v, heq, rho, ux, uy, uz, th);
+  wall_writes_side3<S, TOTAL, 3>(g, dst, x, y, z, v, heq, rho, ux, uy, uz, th);
+  wall_writes_side3<S, TOTAL, 4>(g, dst, x, y, z, v, heq, rho, ux, uy, uz, th);
+  wall_writes_side3<S, TOTAL, 5>(g, dst, x, y, z, v, heq, rho, ux, uy, uz, th);
+}
+
 // Store of the 38 post-collision values of node (x, y, z) at its own slots,
 // and for a node on a face the periodic copies into the ghost slots: the
 // node at w = wrap(x + e_a) pulls population a from w - e_a.
@@ -320,14 +381,23 @@ __device__ __forceinline__ void store3(const Grid3& g, S* __restrict__ dst, int 
   for (int q = 1; q < Q19; ++q) {
     const int dx = x + e3x(q), dy = y + e3y(q), dz = z + e3z(q);
     if (dx >= 0 && dx < g.nx && dy >= 0 && dy < g.ny && dz >= 0 && dz < g.nz) continue;
-    // through a z wall: zwall_writes3 takes it
-    if ((dz < 0 && g.bc_z[0] != BC3_PERIODIC) || (dz >= g.nz && g.bc_z[1] != BC3_PERIODIC))
-      continue;
+    // through a wall: wall_writes3 takes it
+    if (wall_side3(g, q, x, y, z) >= 0) continue;
     const int sx = wrap3(dx, g.nx) - e3x(q), sy = wrap3(dy, g.ny) - e3y(q),
               sz = wrap3(dz, g.nz) - e3z(q);
     dst[slot3(g, q, sx, sy, sz)] = Io<S>::from(v[q]);
     dst[slot3(g, Q19 + q, sx, sy, sz)] = Io<S>::from(v[Q19 + q]);
   }
+}
+
+// The mirror ghost of Eq. 50 across wall side SIDE of a node with rho and
+// theta: component j of 2 Q_w - q0, Q_w = rho u_w (1 - theta_w), theta_w
+// the wall's on an isothermal wall and the node's own on an adiabatic one.
+template <class C, int SIDE>
+__device__ __forceinline__ C mirror_q3(const Grid3& g, C rho, C th, int j, C q0) {
+  const Phys3<C>& k = phys3<C>(g);
+  const C thw = g.bc[SIDE] == BC3_ISO ? k.thw[SIDE] : th;
+  return C(2) * rho * k.uw[SIDE][j] * (C(1) - thw) - q0;
 }
 
 constexpr int TX3 = 32;
@@ -398,6 +468,10 @@ __global__ void __launch_bounds__(threads3<TY, SPLIT>(), (step3d_min_blocks<S, T
   const int x = x0 + tx, y = y0 + ty;
   const bool mine = interior && x < nx && y < ny;
   const int wx = wrap3(x % nx, nx), wy = wrap3(y % ny, ny);  // wrapped (ragged tiles)
+  // this thread's node on a walled x or y side
+  const bool wxl = x == 0 && g.bc[0] != BC3_PERIODIC, wxh = x == nx - 1 && g.bc[1] != BC3_PERIODIC;
+  const bool wyl = y == 0 && g.bc[2] != BC3_PERIODIC, wyh = y == ny - 1 && g.bc[3] != BC3_PERIODIC;
+  const bool wxy = wxl || wxh || wyl || wyh;
   // halo cell of this thread: the ring around the tile
   int hcell = -1, hx = 0, hy = 0;
   if (hk >= 0 && hk < NHALO) {
@@ -450,28 +524,27 @@ __global__ void __launch_bounds__(threads3<TY, SPLIT>(), (step3d_min_blocks<S, T
     if (zc >= z0 && mine) {
       const int sm = (s + 2) & 3, s0 = (s + 3) & 3;  // planes r - 2 and r - 1
       C dq[3][3];  // dq[k][j] = dQ_j / dx_k
-      // across a z wall Eq. 50 takes the mirror ghost 2 Q_w - Q(node),
+      // across a wall Eq. 50 takes the mirror ghost 2 Q_w - Q(node),
       // Q_w = rho u_w (1 - theta_w) (theta_w: the node's own on an adiabatic
       // wall)
-      const bool wb = zc == 0 && g.bc_z[0] != BC3_PERIODIC;
-      const bool wt = zc == nz - 1 && g.bc_z[1] != BC3_PERIODIC;
+      const bool wb = zc == 0 && g.bc[4] != BC3_PERIODIC;
+      const bool wt = zc == nz - 1 && g.bc[5] != BC3_PERIODIC;
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        dq[0][j] = C(0.5) * (qs[s0][j][cell + 1] - qs[s0][j][cell - 1]);
-        dq[1][j] = C(0.5) * (qs[s0][j][cell + HX] - qs[s0][j][cell - HX]);
+        C xp = qs[s0][j][cell + 1], xm = qs[s0][j][cell - 1];
+        C yp = qs[s0][j][cell + HX], ym = qs[s0][j][cell - HX];
         C up = qs[s][j][cell], dn = qs[sm][j][cell];
-        if (wb || wt) {
-          const Phys3<C>& k = phys3<C>(g);
+        if (wxy || wb || wt) {
           const C q0 = qs[s0][j][cell];
-          if (wt) {
-            const C thw = g.bc_z[1] == BC3_ISO ? k.thw[1] : pth;
-            up = C(2) * prho * k.uw[1][j] * (C(1) - thw) - q0;
-          }
-          if (wb) {
-            const C thw = g.bc_z[0] == BC3_ISO ? k.thw[0] : pth;
-            dn = C(2) * prho * k.uw[0][j] * (C(1) - thw) - q0;
-          }
+          if (wxl) xm = mirror_q3<C, 0>(g, prho, pth, j, q0);
+          if (wxh) xp = mirror_q3<C, 1>(g, prho, pth, j, q0);
+          if (wyl) ym = mirror_q3<C, 2>(g, prho, pth, j, q0);
+          if (wyh) yp = mirror_q3<C, 3>(g, prho, pth, j, q0);
+          if (wb) dn = mirror_q3<C, 4>(g, prho, pth, j, q0);
+          if (wt) up = mirror_q3<C, 5>(g, prho, pth, j, q0);
         }
+        dq[0][j] = C(0.5) * (xp - xm);
+        dq[1][j] = C(0.5) * (yp - ym);
         dq[2][j] = C(0.5) * (up - dn);
       }
       C cc[Q19];
@@ -514,8 +587,8 @@ __global__ void __launch_bounds__(threads3<TY, SPLIT>(), (step3d_min_blocks<S, T
         v[Q19 + a] = hs;
       }
       store3<S>(g, dst, x, y, zc, v);
-      if ((zc == 0 && g.bc_z[0] != BC3_PERIODIC) || (zc == nz - 1 && g.bc_z[1] != BC3_PERIODIC))
-        zwall_writes3<S, (M & M3_TOTAL) != 0>(g, dst, x, y, zc, v, heq, prho, pux, puy, puz, pth);
+      if (wxy || wb || wt)
+        wall_writes3<S, (M & M3_TOTAL) != 0>(g, dst, x, y, zc, v, heq, prho, pux, puy, puz, pth);
     }
     prho = crho;
     pux = cux;

@@ -50,6 +50,17 @@ int cuda_fail3(lbm3d_handle* h, cudaError_t e, const char* what) {
   return fail3(h, LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Side s = 2 axis + (0: low end, 1: high end) of the box.
+int side_bc3(const lbm3d_params* p, int s) {
+  return s < 2 ? p->bc_x[s] : (s < 4 ? p->bc_y[s - 2] : p->bc_z[s - 4]);
+}
+const double* side_uw3(const lbm3d_params* p, int s) {
+  return s < 2 ? p->u_wall_x[s] : (s < 4 ? p->u_wall_y[s - 2] : p->u_wall_z[s - 4]);
+}
+double side_Tw3(const lbm3d_params* p, int s) {
+  return s < 2 ? p->T_wall_x[s] : (s < 4 ? p->T_wall_y[s - 2] : p->T_wall_z[s - 4]);
+}
+
 int validate3(const lbm3d_params* p, std::string& why) {
   if (!p) {
     why = "params is NULL";
@@ -88,25 +99,29 @@ int validate3(const lbm3d_params* p, std::string& why) {
     why = "precision must be LBM_P_FP64 or LBM_P_FP32";
     return LBM_ERR_PARAM;
   }
-  for (int k = 0; k < 2; ++k) {
-    if (p->bc_z[k] != LBM_BC_PERIODIC && p->bc_z[k] != LBM_BC_WALL_ISOTHERMAL &&
-        p->bc_z[k] != LBM_BC_WALL_ADIABATIC) {
-      why = "bc_z must be LBM_BC_PERIODIC or a wall";
+  for (int s = 0; s < 6; ++s) {
+    const char* ax = s < 2 ? "x" : (s < 4 ? "y" : "z");
+    const int bc = side_bc3(p, s);
+    if (bc != LBM_BC_PERIODIC && bc != LBM_BC_WALL_ISOTHERMAL && bc != LBM_BC_WALL_ADIABATIC) {
+      why = std::string("bc_") + ax + " must be LBM_BC_PERIODIC or a wall";
       return LBM_ERR_PARAM;
     }
     for (int d = 0; d < 3; ++d)
-      if (!std::isfinite(p->u_wall_z[k][d])) {
-        why = "u_wall_z must be finite";
+      if (!std::isfinite(side_uw3(p, s)[d])) {
+        why = std::string("u_wall_") + ax + " must be finite";
         return LBM_ERR_PARAM;
       }
-    if (!(p->T_wall_z[k] > 0.0) || !std::isfinite(p->T_wall_z[k])) {
-      why = "T_wall_z must be finite and > 0";
+    // the z sides' temperatures always (as before the x and y sides
+    // existed); those of x and y where they are used
+    const double Tw = side_Tw3(p, s);
+    if ((s >= 4 || bc == LBM_BC_WALL_ISOTHERMAL) && (!(Tw > 0.0) || !std::isfinite(Tw))) {
+      why = std::string("T_wall_") + ax + " must be finite and > 0";
       return LBM_ERR_PARAM;
     }
-  }
-  if ((p->bc_z[0] == LBM_BC_PERIODIC) != (p->bc_z[1] == LBM_BC_PERIODIC)) {
-    why = "the z sides are both periodic or both walls";
-    return LBM_ERR_PARAM;
+    if ((s & 1) && (side_bc3(p, s - 1) == LBM_BC_PERIODIC) != (bc == LBM_BC_PERIODIC)) {
+      why = std::string("the ") + ax + " sides are both periodic or both walls";
+      return LBM_ERR_PARAM;
+    }
   }
   if (!std::isfinite(p->g) || (p->g != 0.0 && p->energy_model != LBM_E_INTERNAL)) {
     why = "g must be finite, and 0 unless energy_model is LBM_E_INTERNAL";
@@ -148,13 +163,13 @@ void fill_grid3(const lbm3d_params* p, Grid3& g) {
   g.pf.six_b = (float)(6.0 / p->b);
   g.pd.g = p->g;
   g.pf.g = (float)p->g;
-  for (int k = 0; k < 2; ++k) {
-    g.bc_z[k] = p->bc_z[k];
-    g.pd.thw[k] = p->T_wall_z[k] / p->T0;
+  for (int k = 0; k < 6; ++k) {
+    g.bc[k] = side_bc3(p, k);
+    g.pd.thw[k] = side_Tw3(p, k) / p->T0;
     g.pf.thw[k] = (float)g.pd.thw[k];
     for (int d = 0; d < 3; ++d) {
-      g.pd.uw[k][d] = p->u_wall_z[k][d];
-      g.pf.uw[k][d] = (float)p->u_wall_z[k][d];
+      g.pd.uw[k][d] = side_uw3(p, k)[d];
+      g.pf.uw[k][d] = (float)side_uw3(p, k)[d];
     }
   }
 }

@@ -25,6 +25,9 @@ class lbm3d_params(ctypes.Structure):
         ("z_full", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("bc_z", ctypes.c_int32 * 2), ("u_wall_z", (ctypes.c_double * 3) * 2),
         ("T_wall_z", ctypes.c_double * 2), ("g", ctypes.c_double),
+        ("bc_x", ctypes.c_int32 * 2), ("bc_y", ctypes.c_int32 * 2),
+        ("u_wall_x", (ctypes.c_double * 3) * 2), ("u_wall_y", (ctypes.c_double * 3) * 2),
+        ("T_wall_x", ctypes.c_double * 2), ("T_wall_y", ctypes.c_double * 2),
     ]
 
 
@@ -72,12 +75,15 @@ def make_params(p: dict) -> lbm3d_params:
     o.z_full = int(p.get("z_full", 1))
     o.precision = int(p.get("precision", LBM_P_FP64))
     o.g = float(p.get("g", 0.0))
-    for k in range(2):
-        o.bc_z[k] = int(p.get("bc_z", [0, 0])[k])
-        o.T_wall_z[k] = float(p.get("T_wall_z", [1.0, 1.0])[k])
-        uw = p.get("u_wall_z", [[0.0] * 3] * 2)[k]
-        for d in range(3):
-            o.u_wall_z[k][d] = float(uw[d])
+    for ax in "xyz":
+        bc, tw, uwall = (getattr(o, "bc_" + ax), getattr(o, "T_wall_" + ax),
+                         getattr(o, "u_wall_" + ax))
+        for k in range(2):
+            bc[k] = int(p.get("bc_" + ax, [0, 0])[k])
+            tw[k] = float(p.get("T_wall_" + ax, [1.0, 1.0])[k])
+            uw = p.get("u_wall_" + ax, [[0.0] * 3] * 2)[k]
+            for d in range(3):
+                uwall[k][d] = float(uw[d])
     return o
 
 

@@ -292,3 +292,99 @@ def test_rayleigh_benard_onset_3d_gpu():
     r = sorted(rates)
     slope, icpt = np.polyfit(r, [rates[k] for k in r], 1)
     assert slope > 0 and abs(-icpt / slope - 1.0) < 0.015, rates
+
+
+# walls on the x and y sides too (a population leaving through an edge of
+# two walled sides takes the first of x, y, z, as in the oracle)
+WALLS_XY = {
+    "x_iso_moving": dict(bc_x=[1, 1], T_wall_x=[1.03, 0.98],
+                         u_wall_x=[[0.0, 0.02, 0.0], [0.0, -0.01, 0.03]]),
+    "y_adiabatic": dict(bc_y=[2, 2], u_wall_y=[[0.01, 0.0, 0.0], [0.0, 0.0, 0.02]]),
+    "x_y_mixed": dict(bc_x=[2, 2], bc_y=[1, 1], T_wall_y=[1.04, 0.99],
+                      u_wall_y=[[0.0, 0.0, 0.0], [0.03, 0.0, 0.0]]),
+    "box": dict(bc_x=[1, 2], T_wall_x=[1.03, 1.0], bc_y=[2, 1], T_wall_y=[1.0, 0.97],
+                bc_z=[1, 1], T_wall_z=[1.02, 0.99],
+                u_wall_z=[[0.0, 0.0, 0.0], [0.04, -0.02, 0.0]]),
+}
+
+
+@pytest.mark.parametrize("walls", list(WALLS_XY))
+@pytest.mark.parametrize("mode", ["total_zfull_corr", "internal_corr", "total"])
+@pytest.mark.parametrize("shape", [(4, 3, 5), (37, 11, 9), (33, 9, 12)],
+                         ids=["4x3x5", "37x11x9", "33x9x12"])
+def test_fp64_parity_3d_walls_xy(shape, mode, walls):
+    p, f = _case(shape, mode, lbm.LBM_P_FP64)
+    p.update(WALLS_XY[walls])
+    o = o3.Oracle3d(p).init(*f).step(30)
+    g = Lbm3d(p).init(*f).step(30)
+    assert _rel(g.pops(), o.pops()) <= 1e-12
+    for got, want in zip(g.moments(), o.moments()):
+        assert np.abs(got - want).max() <= 1e-12 * max(np.abs(want).max(), 1e-3)
+    g.close()
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=[f"{a}x{b}" for a, b in SHAPES])
+@pytest.mark.parametrize("walls", ["box", "x_y_mixed"])
+def test_fp32_parity_3d_walls_xy(shape, walls):
+    """Every FP32 launch shape with walls on the tile edges: 37 x 21 leaves
+    ragged tiles on the x+ and y+ sides."""
+    p, f = _case((37, 21, 9), "total_zfull_corr", lbm.LBM_P_FP32)
+    p.update(WALLS_XY[walls])
+    o = o3.Oracle3d(dict(p, precision=lbm.LBM_P_FP64)).init(*f).step(30)
+    g = Lbm3d(p).set_launch(*shape).init(*f).step(30)
+    assert _rel(g.pops(), o.pops()) <= 2e-5
+    g.close()
+
+
+@pytest.mark.parametrize("shape", [(4, 3, 5), (37, 11, 9)], ids=["4x3x5", "37x11x9"])
+def test_fp64_parity_3d_gravity_box(shape):
+    """Gravity along -z in a box walled on every side (the isothermal x and y
+    walls carry no hydrostatic drop: their normal is horizontal)."""
+    p, f = _case(shape, "internal", lbm.LBM_P_FP64)
+    p.update(GRAVITY["iso_walls_corr"])
+    p.update(bc_x=[1, 1], T_wall_x=[1.02, 0.99], bc_y=[2, 2])
+    o = o3.Oracle3d(p).init(*f).step(30)
+    g = Lbm3d(p).init(*f).step(30)
+    assert _rel(g.pops(), o.pops()) <= 1e-12
+    g.close()
+
+
+def test_fp64_parity_3d_box_long():
+    """400 steps in a box walled on every side with a fast lid and several z
+    ranges per column of blocks (the walls meet the blocks' edges in x, y
+    and z)."""
+    p, f = _case((33, 9, 40), "total_zfull_corr", lbm.LBM_P_FP64)
+    p.update(b=5.0, bc_x=[1, 2], T_wall_x=[1.04, 1.0], bc_y=[2, 2],
+             bc_z=[1, 2], u_wall_z=[[0.0, 0.0, 0.0], [0.2, 0.1, 0.0]], T_wall_z=[1.05, 1.0])
+    o = o3.Oracle3d(p).init(*f).step(400, threads=8)
+    g = Lbm3d(p).init(*f).step(400)
+    assert _rel(g.pops(), o.pops()) <= 1e-11
+    g.close()
+
+
+@pytest.mark.parametrize("precision", [lbm.LBM_P_FP64, lbm.LBM_P_FP32], ids=["fp64", "fp32"])
+def test_closed_adiabatic_box_conserves_3d_gpu(precision):
+    """Six adiabatic walls at rest: no mass and no energy cross them, so the
+    sums of rho and of hbar stay at their initial values (FP64 to rounding;
+    FP32 storage to its rounding over the grid)."""
+    p, f = _case((37, 21, 9), "total_zfull_corr", precision)
+    p.update(bc_x=[2, 2], bc_y=[2, 2], bc_z=[2, 2])
+    g = Lbm3d(p).init(*f)
+    c0 = g.conserved()
+    g.step(300)
+    c1 = g.conserved()
+    tol = 1e-12 if precision == lbm.LBM_P_FP64 else 2e-6
+    assert abs(c1[0] - c0[0]) <= tol * c0[0]
+    assert abs(c1[4] - c0[4]) <= tol * c0[4]
+    g.close()
+
+
+def test_side_validation_3d():
+    p, f = _case((8, 8, 8), "total", lbm.LBM_P_FP64)
+    for bad in (dict(bc_x=[1, 0]), dict(bc_y=[0, 2]), dict(bc_x=[3, 3]),
+                dict(bc_y=[1, 1], T_wall_y=[1.0, 0.0]),
+                dict(bc_x=[2, 2], u_wall_x=[[0.0, float("inf"), 0.0], [0.0, 0.0, 0.0]])):
+        with pytest.raises(lbm.LbmError):
+            Lbm3d(dict(p, **bad))
+    # an adiabatic side needs no temperature
+    Lbm3d(dict(p, bc_x=[2, 2], T_wall_x=[0.0, 0.0])).close()
