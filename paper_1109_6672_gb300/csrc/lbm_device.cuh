@@ -173,6 +173,15 @@ struct Io<__half> {
   __device__ static __half from_sr(float v, unsigned r) {
     return in_range(v) ? from_sr_in_range(v, r) : __float2half_rn(v * 256.0f);
   }
+  // two values in one stochastically rounding conversion (cvt.rs, sm_100
+  // family): the random word r supplies the bits of both; non-finite
+  // values stay non-finite (no saturation)
+  __device__ static void from_sr2(float va, float vb, unsigned r, __half& sa, __half& sb) {
+    unsigned d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(va * 256.0f), "f"(vb * 256.0f), "r"(r));
+    sa = __ushort_as_half((unsigned short)(d >> 16));
+    sb = __ushort_as_half((unsigned short)(d & 0xFFFFu));
+  }
 };
 template <>
 struct Io<__nv_bfloat16> {
@@ -191,6 +200,15 @@ struct Io<__nv_bfloat16> {
   }
   __device__ static __nv_bfloat16 from_sr(float v, unsigned r) {
     return in_range(v) ? from_sr_in_range(v, r) : __float2bfloat16_rn(v);
+  }
+  // two values in one stochastically rounding conversion (cvt.rs, sm_100
+  // family), as for FP16
+  __device__ static void from_sr2(float va, float vb, unsigned r, __nv_bfloat16& sa,
+                                  __nv_bfloat16& sb) {
+    unsigned d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(va), "f"(vb), "r"(r));
+    sa = __ushort_as_bfloat16((unsigned short)(d >> 16));
+    sb = __ushort_as_bfloat16((unsigned short)(d & 0xFFFFu));
   }
 };
 
@@ -216,10 +234,13 @@ __device__ __forceinline__ unsigned sr_hash(const Grid& g, int x, int y) {
 // Random words of a node: the linear congruential sequence
 // x -> 1664525 x + 1013904223 (mod 2^32) started at the node's hash h (the
 // 32-bit generator published in Press et al., Numerical Recipes, ch. 7).
-// Word k + 1 rounds stream k: population k (0..17) of the node's own stores;
-// 18 + a / 27 + a: wall values of f_a / h_a that the node writes into ghost
-// slots.  The node's own stores walk the sequence one multiply-add per value;
-// the rare ghost-slot writes step to word k + 1 directly.
+// Words 18 + a / 27 + a round the wall values of f_a / h_a that the node
+// writes into ghost slots (stepping there directly); the node's own 18
+// stores walk the sequence one multiply-add per word: in the pulled-row
+// kernels word j + 1 rounds the pair of populations 2j, 2j + 1 in one
+// hardware conversion (its two 16-bit halves: over the ensemble of nodes
+// the word is uniform, the sequence being a bijection of the hash, so each
+// half is too), in the register-pull kernel word k + 1 rounds population k.
 __device__ __forceinline__ unsigned lcg_next(unsigned r) { return r * 1664525u + 1013904223u; }
 __device__ __forceinline__ unsigned sr_bits(unsigned h, int k) {
   unsigned r = h;

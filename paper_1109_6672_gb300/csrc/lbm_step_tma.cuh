@@ -199,27 +199,21 @@ __device__ __forceinline__ void collide_m(const Grid& g, S* __restrict__ p, int 
     v[9 + a] = hs;
     v[18 + a] = heq[a];
   }
-  unsigned r = Io<S>::sr ? sr_hash(g, x, y) : 0u;
   if constexpr (Io<S>::sr) {
-    // one range test for the node's 18 values, then the rounding without
-    // the per-value test (same results; a node with a value out of range
-    // takes the per-value stores below)
-    bool in_range = true;
+    // stochastic rounding in hardware, two populations per conversion and
+    // one random word per pair (non-finite values pass through unchanged)
+    unsigned r = sr_hash(g, x, y);
 #pragma unroll
-    for (int a = 0; a < NPOP; ++a) in_range = in_range && Io<S>::in_range(v[a]);
-    if (in_range) {
-#pragma unroll
-      for (int a = 0; a < NPOP; ++a) {
-        r = lcg_next(r);
-        p[plane(a) * pitch] = Io<S>::from_sr_in_range(v[a], r);
-      }
-      return;
+    for (int a = 0; a < NPOP; a += 2) {
+      r = lcg_next(r);
+      S sa, sb;
+      Io<S>::from_sr2(v[a], v[a + 1], r, sa, sb);
+      p[plane(a) * pitch] = sa;
+      p[plane(a + 1) * pitch] = sb;
     }
-  }
+  } else {
 #pragma unroll
-  for (int a = 0; a < NPOP; ++a) {
-    if constexpr (Io<S>::sr) r = lcg_next(r);
-    p[plane(a) * pitch] = store_val<S>(v[a], r);
+    for (int a = 0; a < NPOP; ++a) p[plane(a) * pitch] = Io<S>::from(v[a]);
   }
 }
 
