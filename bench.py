@@ -36,8 +36,9 @@ UNIT = "GLUPS"
 # reports null until it is captured again.
 KERNEL_SOURCES = ("lbm_device.cuh", "lbm_step_tma.cuh", "lbm_step_pr.cuh")
 MEASURED_TRAFFIC = {
-    ("d521cd8addf12c82", "f32"): 2302.793728e6,
-    ("d521cd8addf12c82", "bf16"): 1087.173632e6,
+    ("4c9d4a9d20c10b09", "f32"): 2301.39392e6,
+    ("4c9d4a9d20c10b09", "bf16"): 1091.98848e6,
+    ("4c9d4a9d20c10b09", "f16"): 1095.580672e6,
 }
 
 
