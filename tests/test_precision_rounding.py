@@ -6,9 +6,11 @@
   rounding back would: the exact difference is an FP64 number when the
   exponents differ by at most 28, and otherwise lies within 2^-28 of the
   larger operand, far from any FP32 rounding tie.
-* The per-node range tests of the stochastic rounding select exactly the
-  values the per-value tests did: FP16 |v| < 255.875 <=> |256 v| < 65504,
-  BF16 |v| <= FLT_MAX <=> v finite.
+* The range tests of the software stochastic rounding (the register-pull
+  kernel and the wall values written into ghost slots; the pulled-row
+  kernels round in hardware and test nothing) select the values they are
+  meant to: FP16 |v| < 255.875 <=> |256 v| < 65504, BF16 |v| <= FLT_MAX <=>
+  v finite.
 """
 import numpy as np
 
