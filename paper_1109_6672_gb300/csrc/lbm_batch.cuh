@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(PR_THREADS, (batch_min_blocks<S>()))
     __syncthreads();
     const int par = (int)((bg.t0 + j) & 1);
     int pre_out = 0;
-    const int st = pr_block<S, 1, M, DD>(s_grid, &bg.maps[par], bg.buf[par], bg.buf[par ^ 1], w.x0,
+    const int st = pr_block<S, 1, M, DD, 1>(s_grid, &bg.maps[par], bg.buf[par], bg.buf[par ^ 1], w.x0,
                                      w.y0, w.rows, smem, kbase, pre, next, &pre_out);
     if (st) return;  // timeout recorded in the grid's status word
     kbase += pr_staged_rows(s_grid, w.y0, w.rows);

@@ -89,7 +89,7 @@ template <class S, int M>
 cudaError_t batch_one(const BatchGrid* grids, const WorkItem* items, BatchCtl* ctl, int j,
                       int blocks, cudaStream_t stream, int* occ) {
   static bool configured = false;
-  const size_t smem = PrGeom<S, 1, batch_depth<S>()>::smem_bytes();
+  const size_t smem = PrGeom<S, 1, batch_depth<S>(), 1>::smem_bytes();
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(batch_step_kernel<S, M>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -27,8 +27,9 @@ namespace lbm {
 constexpr int PR_COMPUTE = 128;              // compute threads per block
 constexpr int PR_THREADS = PR_COMPUTE + 32;  // plus the helper warp
 
-// DD: ring depth (0: 3 slots for FP64 storage, else 4).
-template <class S, int NPT, int DD = 0>
+// DD: ring depth (0: 3 slots for FP64 storage, else 4).  XD: the walled x
+// sides' ghost-slot writes are deferred (batched kernel, below).
+template <class S, int NPT, int DD = 0, int XD = 0>
 struct PrGeom {
   static constexpr int TWC = PR_COMPUTE * NPT;  // output columns per block
   static constexpr int NB = NPT == 1 ? 1 : 2;   // boxes per plane group
@@ -38,8 +39,14 @@ struct PrGeom {
   static constexpr int SLOT = 3 * NB * GB;  // elements per pulled row
   static constexpr int D = DD ? DD : (sizeof(S) == 8 ? 3 : 4);
   static constexpr unsigned BOX_BYTES = 6 * BW * sizeof(S);
+  // x-edge records (XD, one thread per node): the walled x sides'
+  // ghost-slot writes of XREC_ROWS rows are deferred and done together
+  // (pr_block), in two banks of 2 XREC_ROWS records of XREC_VALS values
+  static constexpr int XREC_ROWS = (XD && NPT == 1) ? 8 : 0;
+  static constexpr int XREC_VALS = 16;
   static constexpr size_t smem_bytes() {
-    return (size_t)D * SLOT * sizeof(S) + 2 * (TWC + 2) * sizeof(typename Io<S>::C) + D * 8;
+    return (size_t)D * SLOT * sizeof(S) + 2 * (TWC + 2) * sizeof(typename Io<S>::C) + D * 8 +
+           (size_t)4 * XREC_ROWS * XREC_VALS * sizeof(typename Io<S>::C);
   }
   static_assert(BW % 8 == 0, "box starts must stay 16-byte aligned");
   static_assert((GB * sizeof(S)) % 128 == 0, "boxes must start on 128-byte boundaries");
@@ -65,11 +72,12 @@ __device__ __forceinline__ void pull_pr(const S* slot, const int co[3],
   }
 }
 
-// Shared-memory layout of a block: ring slots, Q_x rows, mbarriers.
-template <class S, int NPT, int DD = 0>
+// Shared-memory layout of a block: ring slots, Q_x rows, mbarriers, x-edge
+// records (XD).
+template <class S, int NPT, int DD = 0, int XD = 0>
 struct PrSmem {
   using C = typename Io<S>::C;
-  using G = PrGeom<S, NPT, DD>;
+  using G = PrGeom<S, NPT, DD, XD>;
   __device__ static S* ring(unsigned char* smem) { return reinterpret_cast<S*>(smem); }
   __device__ static C* qxs(unsigned char* smem) {
     return reinterpret_cast<C*>(smem + (size_t)G::D * G::SLOT * sizeof(S));
@@ -77,7 +85,51 @@ struct PrSmem {
   __device__ static unsigned bars(unsigned char* smem) {
     return smem_u32(qxs(smem) + 2 * (G::TWC + 2));
   }
+  __device__ static C* xrec(unsigned char* smem) {
+    return reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(qxs(smem) + 2 * (G::TWC + 2)) +
+                                G::D * 8);
+  }
 };
+
+// The values the x-edge writes of side XS (xedge_writes) read from a node:
+// for each population A leaving through the side (B its opposite) f*_A,
+// h*_A, h*_B and h^eq_B, then rho, u_x, u_y, theta.
+template <int XS>
+__host__ __device__ constexpr int xrec_pop(int k) {
+  return XS == 0 ? (k == 0 ? 3 : (k == 1 ? 6 : 7)) : (k == 0 ? 1 : (k == 1 ? 5 : 8));
+}
+template <class C, int XS>
+__device__ __forceinline__ void xrec_put(C* r, const C* v, C rho, C ux, C uy, C th) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int A = xrec_pop<XS>(k), B = opp(A);
+    r[4 * k] = v[A];
+    r[4 * k + 1] = v[9 + A];
+    r[4 * k + 2] = v[9 + B];
+    r[4 * k + 3] = v[18 + B];
+  }
+  r[12] = rho;
+  r[13] = ux;
+  r[14] = uy;
+  r[15] = th;
+}
+template <class S, int XS>
+__device__ __forceinline__ void xrec_flush(const Grid& g, S* __restrict__ dst, int x, int y,
+                                           const typename Io<S>::C* r) {
+  using C = typename Io<S>::C;
+  C v[27];
+#pragma unroll
+  for (int a = 0; a < 27; ++a) v[a] = C(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int A = xrec_pop<XS>(k), B = opp(A);
+    v[A] = r[4 * k];
+    v[9 + A] = r[4 * k + 1];
+    v[9 + B] = r[4 * k + 2];
+    v[18 + B] = r[4 * k + 3];
+  }
+  xedge_writes<S, XS>(g, dst, x, y, v, r[12], r[13], r[14], r[15]);
+}
 
 // Initialise the ring's mbarriers (once per kernel, all threads call).
 template <class S, int NPT, int DD = 0>
@@ -122,26 +174,30 @@ struct PrNext {
 // Only helper lane 0 issues copies, so pre / *pre_out matter in that thread
 // alone.  Returns 0, or 1 if a staged row never arrived (after draining its own
 // copies).
-template <class S, int NPT, int M, int DD = 0>
+template <class S, int NPT, int M, int DD = 0, int XD = 0>
 __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, const void* src_v,
                                         void* dst_v, int x0, int y0, int rows, unsigned char* smem,
                                         int kbase, int pre = 0,
                                         PrNext next = PrNext{nullptr, 0, 0, 0, 0},
                                         int* pre_out = nullptr) {
   using C = typename Io<S>::C;
-  using G = PrGeom<S, NPT, DD>;
-  using SM = PrSmem<S, NPT, DD>;
+  using G = PrGeom<S, NPT, DD, XD>;
+  using SM = PrSmem<S, NPT, DD, XD>;
   constexpr bool DEV = Io<S>::dev;  // moments carried as deviations (moments_m)
   constexpr int D = G::D, TWC = G::TWC;
   constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
   S* ring = SM::ring(smem);
   C* qxs = SM::qxs(smem);
+  constexpr int XR = G::XREC_ROWS, XV = G::XREC_VALS;
+  C* xrec = SM::xrec(smem);
   const unsigned ring_s = smem_u32(ring), bar_s = SM::bars(smem);
 
   const int t = threadIdx.x, nx = g.nx, ny = g.ny;
   const int y1 = min(y0 + rows, ny);
   const bool wall_l = g.bc[0] != BC_PERIODIC, wall_r = g.bc[1] != BC_PERIODIC;
   const bool wall_b = g.bc[2] != BC_PERIODIC, wall_t = g.bc[3] != BC_PERIODIC;
+  // this share holds a node of a walled x side (recorded x-edge writes)
+  const bool xl = wall_l && x0 == 0, xr = wall_r && x0 <= nx - 1 && nx - 1 < x0 + G::TWC;
   // staged pulled rows rs .. re (halo rows only where they hold nodes)
   const int rs = (y0 >= 1 || !wall_b) ? y0 - 1 : y0;
   const int re = (y1 < ny || !wall_t) ? y1 : y1 - 1;
@@ -297,8 +353,27 @@ __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, c
 #pragma unroll
             for (int a = 0; a < 27; ++a) v[a] += pref<S>(g, a < 18 ? a : a - 9);
           }
-          if (c == 0) xedge_writes<S, 0>(g, dst, c, ro, v, rho_n, pux[i], puy[i], th_n);
-          if (c == nx - 1) xedge_writes<S, 1>(g, dst, c, ro, v, rho_n, pux[i], puy[i], th_n);
+          // a walled x side's writes are recorded and done XREC_ROWS rows at
+          // a time by a whole warp (below), so that the row barrier does not
+          // wait on one lane's wall rules; periodic copies are cheap inline
+          if constexpr (XR > 0) {
+            C* rec = xrec + (((ro - y0) / XR) & 1) * (2 * XR * XV) + ((ro - y0) % XR) * 2 * XV;
+            if (c == 0) {
+              if (wall_l)
+                xrec_put<C, 0>(rec, v, rho_n, pux[i], puy[i], th_n);
+              else
+                xedge_writes<S, 0>(g, dst, c, ro, v, rho_n, pux[i], puy[i], th_n);
+            }
+            if (c == nx - 1) {
+              if (wall_r)
+                xrec_put<C, 1>(rec + XV, v, rho_n, pux[i], puy[i], th_n);
+              else
+                xedge_writes<S, 1>(g, dst, c, ro, v, rho_n, pux[i], puy[i], th_n);
+            }
+          } else {
+            if (c == 0) xedge_writes<S, 0>(g, dst, c, ro, v, rho_n, pux[i], puy[i], th_n);
+            if (c == nx - 1) xedge_writes<S, 1>(g, dst, c, ro, v, rho_n, pux[i], puy[i], th_n);
+          }
           if (yedge) {
             C tmp[27];
 #pragma unroll
@@ -324,6 +399,21 @@ __device__ __forceinline__ int pr_block(const Grid& g, const CUtensorMap* map, c
     }
     // everyone is done with pulled row r - 1: refill its slot
     if (helper && hl == 0) issue_upto(k + D - 1);
+    // the recorded x-edge writes of the chunk that row ro completes: lane l
+    // of warp 0 takes side l & 1 of chunk row l >> 1.  The other bank fills
+    // meanwhile; this one is refilled only after the next chunk's last
+    // barrier, which warp 0 reaches after this.
+    if constexpr (XR > 0) {
+      if (ro >= y0 && (xl || xr) && t < 2 * XR && ((ro - y0 + 1) % XR == 0 || ro == y1 - 1)) {
+        const int c0 = ((ro - y0) / XR) * XR;  // first row of the chunk, from y0
+        const int row = y0 + c0 + (t >> 1);
+        const C* rec = xrec + ((c0 / XR) & 1) * (2 * XR * XV) + (t >> 1) * 2 * XV;
+        if (row <= ro) {
+          if ((t & 1) == 0 && xl) xrec_flush<S, 0>(g, dst, 0, row, rec);
+          if ((t & 1) == 1 && xr) xrec_flush<S, 1>(g, dst, nx - 1, row, rec + XV);
+        }
+      }
+    }
 #pragma unroll
     for (int i = 0; i < NPT; ++i) {
       qymm[i] = pqy[i];
