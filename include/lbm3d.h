@@ -81,7 +81,7 @@ typedef struct {
                         /* LBM_BC_WALL_ADIABATIC (halfway walls, see above);  */
                         /* both periodic or both walls                        */
   double u_wall_z[2][3];  /* wall velocities of the z sides                   */
-  double T_wall_z[2];     /* wall temperatures (isothermal walls), > 0        */
+  double T_wall_z[2];     /* wall temperatures, > 0 on an isothermal wall      */
   double g;               /* gravity along -z, a = (0, 0, -rho g): Guo's force */
                           /* term beside C_a (Eq. 51 with D = 3) and the half- */
                           /* force velocity shift; LBM_E_INTERNAL only, else 0 */
@@ -104,7 +104,7 @@ int64_t lbm3d_state_bytes(const lbm3d_params* p);
  * cuda_stream (NULL: the legacy default stream).  Errors: LBM_ERR_PARAM
  * (nx, ny or nz < 1, tau <= 0, R T0 != 1/3, b < 3, an unknown model,
  * precision or side kind, one side of an axis periodic and the other a
- * wall, a non-finite wall velocity, a wall temperature <= 0,
+ * wall, a non-finite wall velocity, an isothermal wall's temperature <= 0,
  * a non-finite g or g != 0 with total energy, 2^31 nodes or more),
  * LBM_ERR_OOM, LBM_ERR_CUDA.  *out is NULL
  * on error. */

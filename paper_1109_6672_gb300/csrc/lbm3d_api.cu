@@ -111,10 +111,9 @@ int validate3(const lbm3d_params* p, std::string& why) {
         why = std::string("u_wall_") + ax + " must be finite";
         return LBM_ERR_PARAM;
       }
-    // the z sides' temperatures always (as before the x and y sides
-    // existed); those of x and y where they are used
+    // a wall temperature is read on isothermal walls only
     const double Tw = side_Tw3(p, s);
-    if ((s >= 4 || bc == LBM_BC_WALL_ISOTHERMAL) && (!(Tw > 0.0) || !std::isfinite(Tw))) {
+    if (bc == LBM_BC_WALL_ISOTHERMAL && (!(Tw > 0.0) || !std::isfinite(Tw))) {
       why = std::string("T_wall_") + ax + " must be finite and > 0";
       return LBM_ERR_PARAM;
     }

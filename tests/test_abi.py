@@ -152,7 +152,14 @@ def test_3d_state_bytes_and_validation_without_gpu(lib):
                 dict(p, precision=lbm.LBM_P_FP32_BF16), dict(p, energy_model=3),
                 dict(p, correction=2), dict(p, nx=2048, ny=2048, nz=1024),
                 dict(p, bc_z=[1, 0]), dict(p, bc_z=[3, 3]), dict(p, bc_z=[1, 1], T_wall_z=[0.0, 1.0]),
-                dict(p, bc_z=[1, 1], u_wall_z=[[float("nan"), 0, 0], [0, 0, 0]])):
+                dict(p, bc_z=[1, 1], u_wall_z=[[float("nan"), 0, 0], [0, 0, 0]]),
+                dict(p, bc_x=[1, 0]), dict(p, bc_y=[0, 2]), dict(p, bc_x=[4, 4]),
+                dict(p, bc_y=[1, 1], T_wall_y=[1.0, 0.0]),
+                dict(p, bc_x=[2, 2], u_wall_x=[[0, float("inf"), 0], [0, 0, 0]])):
         with pytest.raises(lbm.LbmError) as e:
             lbm3d.lbm3d_state_bytes(bad)
         assert e.value.status == lbm.LBM_ERR_PARAM
+    # a wall temperature is read on isothermal walls only
+    for good in (dict(p, bc_x=[2, 2], T_wall_x=[0.0, 0.0]), dict(p, T_wall_z=[0.0, 0.0]),
+                 dict(p, bc_x=[1, 2], T_wall_x=[1.1, 0.0], bc_y=[2, 2], bc_z=[2, 1])):
+        assert lbm3d.lbm3d_state_bytes(good) == n
