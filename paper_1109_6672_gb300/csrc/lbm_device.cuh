@@ -174,8 +174,11 @@ struct Io<__half> {
     return in_range(v) ? from_sr_in_range(v, r) : __float2half_rn(v * 256.0f);
   }
   // two values in one stochastically rounding conversion (cvt.rs, sm_100
-  // family): the random word r supplies the bits of both; non-finite
-  // values stay non-finite (no saturation)
+  // family): the random word r supplies the bits of both (bits 28-16 the
+  // first value's, 12-0 the second's).  No saturation: non-finite values
+  // stay non-finite, and a finite 256 v at or above 65536 becomes infinite
+  // (in the last spacing below it, infinite or 65504 at random), so a
+  // diverging state is still flagged
   __device__ static void from_sr2(float va, float vb, unsigned r, __half& sa, __half& sb) {
     unsigned d;
     asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(va * 256.0f), "f"(vb * 256.0f), "r"(r));
@@ -202,7 +205,8 @@ struct Io<__nv_bfloat16> {
     return in_range(v) ? from_sr_in_range(v, r) : __float2bfloat16_rn(v);
   }
   // two values in one stochastically rounding conversion (cvt.rs, sm_100
-  // family), as for FP16
+  // family), as for FP16 (bits 31-16 round the first value, 15-0 the
+  // second; a value rounded up past the largest finite one is infinite)
   __device__ static void from_sr2(float va, float vb, unsigned r, __nv_bfloat16& sa,
                                   __nv_bfloat16& sb) {
     unsigned d;
