@@ -388,3 +388,21 @@ def test_side_validation_3d():
             Lbm3d(dict(p, **bad))
     # an adiabatic side needs no temperature
     Lbm3d(dict(p, bc_x=[2, 2], T_wall_x=[0.0, 0.0])).close()
+
+
+DEGENERATE = [(1, 4, 3), (3, 1, 4), (2, 3, 1), (1, 1, 1), (1, 1, 5)]
+
+
+@pytest.mark.parametrize("walls", ["box", "x_y_mixed"])
+@pytest.mark.parametrize("mode", ["total_zfull_corr", "internal_corr"])
+@pytest.mark.parametrize("shape", DEGENERATE, ids=["x".join(map(str, s)) for s in DEGENERATE])
+def test_fp64_parity_3d_walls_degenerate(shape, mode, walls):
+    """Axes one node thick: both walls of an axis act on the same node (its
+    leaving populations bounce off either side, Eq. 50 takes both mirror
+    ghosts), and a one-plane periodic axis wraps onto itself."""
+    p, f = _case(shape, mode, lbm.LBM_P_FP64)
+    p.update(WALLS_XY[walls])
+    o = o3.Oracle3d(p).init(*f).step(30)
+    g = Lbm3d(p).init(*f).step(30)
+    assert _rel(g.pops(), o.pops()) <= 1e-12
+    g.close()
