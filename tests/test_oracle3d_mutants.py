@@ -54,6 +54,13 @@ MUTANTS = [
      "Dg[m] = -s->D[27 * i + m];", "Eq. 50 across a wall: the mirror without D_w", WALL_PINS),
     ("ghost_theta_at_wall", "double thg = 2.0 * thw - th;", "double thg = thw;",
      "isothermal wall: the ghost at the wall temperature, not extrapolated", WALL_PINS),
+    ("side_walls_velocity_swapped",
+     "return s < 2 ? p->u_wall_x[s] : (s < 4 ? p->u_wall_y[s - 2] : p->u_wall_z[s - 4]);",
+     "return s < 2 ? p->u_wall_y[s] : (s < 4 ? p->u_wall_x[s - 2] : p->u_wall_z[s - 4]);",
+     "walls on every side: the x and y sides' wall velocities swapped", WALL_PINS),
+    ("ghost_high_side_state_of_low", "wall_ghost_D(s, i, 2 * k + 1, gp);",
+     "wall_ghost_D(s, i, 2 * k, gp);",
+     "Eq. 50 across the high wall of an axis with the low wall's state", WALL_PINS),
 ]
 
 
